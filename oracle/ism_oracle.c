@@ -1,0 +1,431 @@
+/*
+ * ism_oracle.c -- TEST INFRASTRUCTURE ONLY.
+ *
+ * The plain, slow, sequential CPU oracle of the interpolated stencil
+ * multigrid (ISM) pressure solve and of the projection time step it sits in
+ * (Tegze & Toth, "A GPU cluster optimized multigrid scheme for computing
+ * unsteady incompressible fluid flow").  Only the test suite, the smoke check
+ * and the CPU-baseline leg of the benchmark load this file; the product path
+ * (the CUDA library) never does, and the two share no code.
+ *
+ * Every loop runs over cells in a fixed order (rows j = 0..ny-1 outer,
+ * columns i = 0..nx-1 inner) in IEEE double, except the *_f32 variants, which
+ * emulate the single-precision inner solver of the mixed path with float
+ * loops.  Build with -ffp-contract=off so that no multiply-add is fused on
+ * any host.
+ *
+ * Conventions (Sec. 2.3, Sec. 3.3):
+ *   cell-centred field p[j*nx + i], cell (i, j), i along x, j along y;
+ *   face order bc[0..3] = west, east, south, north;
+ *   bc = 0: homogeneous Neumann wall (no flux through the face);
+ *   bc = 1: Dirichlet p = 0 on the face (ghost value -p_c).
+ *   The fine operator is the finite-volume flux sum of the five-point
+ *   Laplacian (Sec. 3.3: the Gauss theorem turns the cell integral into face
+ *   fluxes), in units where a face flux is (p_neighbour - p_cell):
+ *       (A_f p)_c = sum over faces of flux,
+ *   a Neumann face contributing 0 and a Dirichlet-0 face (-p_c - p_c).
+ *   The equation solved is A_f p = b.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define F_W 0
+#define F_E 1
+#define F_S 2
+#define F_N 3
+
+#define AT(a, i, j) (a)[(size_t)(j) * (size_t)nx + (size_t)(i)]
+
+/* ------------------------------------------------------------------------ */
+/* Fine operator, Sec. 2.3 / Sec. 3.3: five-point flux sum.                  */
+/* ------------------------------------------------------------------------ */
+
+static double cell_flux_sum(int nx, int ny, const int *bc, const double *p,
+                            int i, int j)
+{
+    double pc = AT(p, i, j);
+    double s = 0.0;
+    if (i > 0) s += AT(p, i - 1, j) - pc; else if (bc[F_W]) s += -pc - pc;
+    if (i < nx - 1) s += AT(p, i + 1, j) - pc; else if (bc[F_E]) s += -pc - pc;
+    if (j > 0) s += AT(p, i, j - 1) - pc; else if (bc[F_S]) s += -pc - pc;
+    if (j < ny - 1) s += AT(p, i, j + 1) - pc; else if (bc[F_N]) s += -pc - pc;
+    return s;
+}
+
+/* out = A_f p */
+void or_apply_af(int nx, int ny, const int *bc, const double *p, double *out)
+{
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            AT(out, i, j) = cell_flux_sum(nx, ny, bc, p, i, j);
+}
+
+/* r = b - A_f p */
+void or_residual(int nx, int ny, const int *bc, const double *p,
+                 const double *b, double *r)
+{
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            AT(r, i, j) = AT(b, i, j) - cell_flux_sum(nx, ny, bc, p, i, j);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Red-black Gauss-Seidel sweep, Sec. 3.1: the point update solves the cell's */
+/* own equation for p_c with the neighbours held fixed:                       */
+/*   p_c = (sum of interior neighbours - b_c) / d_c,                          */
+/*   d_c = (#interior neighbours) + 2 (#Dirichlet-0 faces).                   */
+/* Red cells ((i + j) even) are updated first, then black.                    */
+/* ------------------------------------------------------------------------ */
+
+static void gs_colour(int nx, int ny, const int *bc, double *p, const double *b,
+                      int colour)
+{
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            if (((i + j) & 1) != colour) continue;
+            double s = 0.0;
+            int d = 0;
+            if (i > 0) { s += AT(p, i - 1, j); d += 1; } else if (bc[F_W]) d += 2;
+            if (i < nx - 1) { s += AT(p, i + 1, j); d += 1; } else if (bc[F_E]) d += 2;
+            if (j > 0) { s += AT(p, i, j - 1); d += 1; } else if (bc[F_S]) d += 2;
+            if (j < ny - 1) { s += AT(p, i, j + 1); d += 1; } else if (bc[F_N]) d += 2;
+            AT(p, i, j) = (s - AT(b, i, j)) / (double)d;
+        }
+    }
+}
+
+void or_rbgs_sweep(int nx, int ny, const int *bc, double *p, const double *b)
+{
+    gs_colour(nx, ny, bc, p, b, 0);
+    gs_colour(nx, ny, bc, p, b, 1);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Restriction, Sec. 3.2-3.3: the coarse right-hand side is the sum of the    */
+/* fine equations over the m x m block (agglomeration, as in ACM).            */
+/* ------------------------------------------------------------------------ */
+
+void or_restrict(int nx, int ny, int m, const double *r, double *rc)
+{
+    int ncx = nx / m, ncy = ny / m;
+    for (int J = 0; J < ncy; ++J)
+        for (int I = 0; I < ncx; ++I) {
+            double s = 0.0;
+            for (int j = J * m; j < (J + 1) * m; ++j)
+                for (int i = I * m; i < (I + 1) * m; ++i)
+                    s += AT(r, i, j);
+            rc[(size_t)J * ncx + I] = s;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Bilinear interpolation from coarse centres, Eq. 5.                          */
+/* Q11, Q21, Q12, Q22 are the corner values of the interpolation rectangle    */
+/* (Delta_x = Delta_y = m fine cells), (x, y) the fine-cell centre measured   */
+/* from Q11.  Outside the hull of coarse centres the rule near the boundary is */
+/* a mirror ghost centre at distance m beyond the edge centre (the paper      */
+/* leaves this rule open): even (Q_ghost = Q_edge) at a Neumann face, odd      */
+/* (Q_ghost = -Q_edge) at a Dirichlet-0 face.                                 */
+/* ------------------------------------------------------------------------ */
+
+static double coarse_or_ghost(int ncx, int ncy, const int *bc, const double *q,
+                              int I, int J)
+{
+    double sgn = 1.0;
+    if (I < 0) { I = 0; if (bc[F_W]) sgn = -sgn; }
+    if (I >= ncx) { I = ncx - 1; if (bc[F_E]) sgn = -sgn; }
+    if (J < 0) { J = 0; if (bc[F_S]) sgn = -sgn; }
+    if (J >= ncy) { J = ncy - 1; if (bc[F_N]) sgn = -sgn; }
+    return sgn * q[(size_t)J * ncx + I];
+}
+
+/* value of the interpolant P q at fine cell (i, j) */
+static double bilinear_at(int nx, int ny, int m, const int *bc, const double *q,
+                          int i, int j)
+{
+    int ncx = nx / m, ncy = ny / m;
+    /* lower-left corner of the interpolation rectangle: the coarse centre at
+       or left of / below the fine centre; coarse centre I sits at fine
+       coordinate (I + 1/2) m. */
+    int I0 = (int)floor(((double)i + 0.5) / m - 0.5);
+    int J0 = (int)floor(((double)j + 0.5) / m - 0.5);
+    double Dx = (double)m, Dy = (double)m;
+    double x = ((double)i + 0.5) - ((double)I0 + 0.5) * m;
+    double y = ((double)j + 0.5) - ((double)J0 + 0.5) * m;
+    double Q11 = coarse_or_ghost(ncx, ncy, bc, q, I0, J0);
+    double Q21 = coarse_or_ghost(ncx, ncy, bc, q, I0 + 1, J0);
+    double Q12 = coarse_or_ghost(ncx, ncy, bc, q, I0, J0 + 1);
+    double Q22 = coarse_or_ghost(ncx, ncy, bc, q, I0 + 1, J0 + 1);
+    return (Q11 * (Dx - x) * (Dy - y) + Q21 * x * (Dy - y)
+            + Q12 * (Dx - x) * y + Q22 * x * y) / (Dx * Dy);
+}
+
+/* p += P q (bilinear prolongation with the same rule, Sec. 3.3) */
+void or_prolong_add(int nx, int ny, int m, const int *bc, const double *q, double *p)
+{
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            AT(p, i, j) += bilinear_at(nx, ny, m, bc, q, i, j);
+}
+
+/* p += q[block] (piecewise-constant correction of ACM, Sec. 3.2) */
+void or_prolong_const_add(int nx, int ny, int m, const double *q, double *p)
+{
+    int ncx = nx / m;
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            AT(p, i, j) += q[(size_t)(j / m) * ncx + (i / m)];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Coarse operator, Sec. 3.3 (Eq. 5-7, Fig. 1).                                */
+/* Column J of A_c is obtained by interpolating the unit coarse vector e_J to */
+/* the fine grid and summing, for every coarse cell K, the fine face fluxes    */
+/* (p_out - p_in) that cross the boundary of K; fluxes inside K cancel.  With */
+/* kind = 0 (ISM) the fine values come from the bilinear rule above; with      */
+/* kind = 1 (ACM) p is constant inside each coarse cell, which reproduces the  */
+/* summation of the fine equations.  The result is dense row-major nc x nc,    */
+/* row K = coarse equation, column J = coarse unknown.                         */
+/* ------------------------------------------------------------------------ */
+
+static double face_sums(int nx, int ny, int m, const int *bc, const double *p,
+                        int KI, int KJ)
+{
+    int x0 = KI * m, x1 = x0 + m, y0 = KJ * m, y1 = y0 + m;
+    double s = 0.0;
+    for (int j = y0; j < y1; ++j) {                     /* west face */
+        if (x0 > 0) s += AT(p, x0 - 1, j) - AT(p, x0, j);
+        else if (bc[F_W]) s += -AT(p, x0, j) - AT(p, x0, j);
+    }
+    for (int j = y0; j < y1; ++j) {                     /* east face */
+        if (x1 < nx) s += AT(p, x1, j) - AT(p, x1 - 1, j);
+        else if (bc[F_E]) s += -AT(p, x1 - 1, j) - AT(p, x1 - 1, j);
+    }
+    for (int i = x0; i < x1; ++i) {                     /* south face */
+        if (y0 > 0) s += AT(p, i, y0 - 1) - AT(p, i, y0);
+        else if (bc[F_S]) s += -AT(p, i, y0) - AT(p, i, y0);
+    }
+    for (int i = x0; i < x1; ++i) {                     /* north face */
+        if (y1 < ny) s += AT(p, i, y1) - AT(p, i, y1 - 1);
+        else if (bc[F_N]) s += -AT(p, i, y1 - 1) - AT(p, i, y1 - 1);
+    }
+    return s;
+}
+
+int or_coarse_operator(int nx, int ny, int m, const int *bc, int kind, double *Ac)
+{
+    int ncx = nx / m, ncy = ny / m, nc = ncx * ncy;
+    double *p = (double *)calloc((size_t)nx * ny, sizeof(double));
+    double *q = (double *)calloc((size_t)nc, sizeof(double));
+    if (!p || !q) { free(p); free(q); return -1; }
+    memset(Ac, 0, sizeof(double) * (size_t)nc * nc);
+    for (int JJ = 0; JJ < ncy; ++JJ) {
+        for (int JI = 0; JI < ncx; ++JI) {
+            int col = JJ * ncx + JI;
+            q[col] = 1.0;
+            /* the interpolant of e_J vanishes outside coarse cells JI-1..JI+1,
+               JJ-1..JJ+1 (the hat spans from centre to neighbouring centre) */
+            int bi0 = JI - 1 < 0 ? 0 : JI - 1, bi1 = JI + 1 >= ncx ? ncx - 1 : JI + 1;
+            int bj0 = JJ - 1 < 0 ? 0 : JJ - 1, bj1 = JJ + 1 >= ncy ? ncy - 1 : JJ + 1;
+            for (int j = bj0 * m; j < (bj1 + 1) * m; ++j)
+                for (int i = bi0 * m; i < (bi1 + 1) * m; ++i)
+                    AT(p, i, j) = (kind == 0) ? bilinear_at(nx, ny, m, bc, q, i, j)
+                                              : q[(size_t)(j / m) * ncx + (i / m)];
+            for (int KJ = bj0; KJ <= bj1; ++KJ)
+                for (int KI = bi0; KI <= bi1; ++KI)
+                    Ac[(size_t)(KJ * ncx + KI) * nc + col] =
+                        face_sums(nx, ny, m, bc, p, KI, KJ);
+            for (int j = bj0 * m; j < (bj1 + 1) * m; ++j)
+                for (int i = bi0 * m; i < (bi1 + 1) * m; ++i)
+                    AT(p, i, j) = 0.0;
+            q[col] = 0.0;
+        }
+    }
+    free(p);
+    free(q);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Single-precision emulation of the inner solver of the mixed path.          */
+/* Same steps as above in float arithmetic; sums of the restriction and of    */
+/* norms are accumulated in double.                                           */
+/* ------------------------------------------------------------------------ */
+
+static float cell_flux_sum_f(int nx, int ny, const int *bc, const float *p,
+                             int i, int j)
+{
+    float pc = AT(p, i, j);
+    float s = 0.0f;
+    if (i > 0) s += AT(p, i - 1, j) - pc; else if (bc[F_W]) s += -pc - pc;
+    if (i < nx - 1) s += AT(p, i + 1, j) - pc; else if (bc[F_E]) s += -pc - pc;
+    if (j > 0) s += AT(p, i, j - 1) - pc; else if (bc[F_S]) s += -pc - pc;
+    if (j < ny - 1) s += AT(p, i, j + 1) - pc; else if (bc[F_N]) s += -pc - pc;
+    return s;
+}
+
+void or_residual_f32(int nx, int ny, const int *bc, const float *p,
+                     const float *b, float *r)
+{
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            AT(r, i, j) = AT(b, i, j) - cell_flux_sum_f(nx, ny, bc, p, i, j);
+}
+
+static void gs_colour_f(int nx, int ny, const int *bc, float *p, const float *b,
+                        int colour)
+{
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            if (((i + j) & 1) != colour) continue;
+            float s = 0.0f;
+            int d = 0;
+            if (i > 0) { s += AT(p, i - 1, j); d += 1; } else if (bc[F_W]) d += 2;
+            if (i < nx - 1) { s += AT(p, i + 1, j); d += 1; } else if (bc[F_E]) d += 2;
+            if (j > 0) { s += AT(p, i, j - 1); d += 1; } else if (bc[F_S]) d += 2;
+            if (j < ny - 1) { s += AT(p, i, j + 1); d += 1; } else if (bc[F_N]) d += 2;
+            AT(p, i, j) = (s - AT(b, i, j)) / (float)d;
+        }
+    }
+}
+
+void or_rbgs_sweep_f32(int nx, int ny, const int *bc, float *p, const float *b)
+{
+    gs_colour_f(nx, ny, bc, p, b, 0);
+    gs_colour_f(nx, ny, bc, p, b, 1);
+}
+
+void or_restrict_f32(int nx, int ny, int m, const float *r, double *rc)
+{
+    int ncx = nx / m, ncy = ny / m;
+    for (int J = 0; J < ncy; ++J)
+        for (int I = 0; I < ncx; ++I) {
+            double s = 0.0;
+            for (int j = J * m; j < (J + 1) * m; ++j)
+                for (int i = I * m; i < (I + 1) * m; ++i)
+                    s += (double)AT(r, i, j);
+            rc[(size_t)J * ncx + I] = s;
+        }
+}
+
+void or_prolong_add_f32(int nx, int ny, int m, const int *bc, const double *q, float *p)
+{
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            AT(p, i, j) = AT(p, i, j) + (float)bilinear_at(nx, ny, m, bc, q, i, j);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Projection time step, Sec. 2.2-2.3 (Eq. 3-4), physical signs:              */
+/*   v* = v^n + dt [ -(v.grad) v + nu lap v - grad p^n ]     (forward Euler)  */
+/*   A_f dp = h (div_flux v*) / dt                                            */
+/*   v^{n+1} = v* - dt grad dp,   p^{n+1} = p^n + dp                          */
+/* on the staggered (MAC) grid: u[j*(nx+1) + i] on x-faces (i = 0..nx),       */
+/* v[j*nx + i] on y-faces (j = 0..ny).  Second-order central differences,     */
+/* advective form, face-averaged transverse velocity.                          */
+/*                                                                             */
+/* Face kinds (vel_bc[face]): 0 no-slip wall moving tangentially with          */
+/* wall_u[face]; 1 free-slip wall; 2 inflow (west face only, profile u_in[j]); */
+/* 3 convective outflow (east face only, speed conv_u).  The pressure is      */
+/* Dirichlet-0 on outflow faces and Neumann elsewhere.                         */
+/* ------------------------------------------------------------------------ */
+
+#define UU(i, j) u[(size_t)(j) * (size_t)(nx + 1) + (size_t)(i)]
+#define VV(i, j) v[(size_t)(j) * (size_t)nx + (size_t)(i)]
+#define US(i, j) us[(size_t)(j) * (size_t)(nx + 1) + (size_t)(i)]
+#define VS(i, j) vs[(size_t)(j) * (size_t)nx + (size_t)(i)]
+#define PP(i, j) p[(size_t)(j) * (size_t)nx + (size_t)(i)]
+
+/* ghost value of a tangential velocity component beyond a face */
+static double tangential_ghost(int kind, double wall_u, double inner)
+{
+    switch (kind) {
+    case 0: return 2.0 * wall_u - inner;   /* no-slip: mean of inner and ghost = wall speed */
+    case 1: return inner;                  /* free slip: zero normal gradient */
+    case 2: return -inner;                 /* inflow: no tangential velocity at the inlet */
+    default: return inner;                 /* outflow: zero normal gradient */
+    }
+}
+
+void or_predictor(int nx, int ny, double h, double dt, double nu,
+                  const int *vel_bc, const double *wall_u, const double *u_in,
+                  double conv_u, const double *u, const double *v,
+                  const double *p, double *us, double *vs)
+{
+    double ih = 1.0 / h, ih2 = 1.0 / (h * h);
+    /* x-faces */
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 0; i <= nx; ++i) {
+            double uc = UU(i, j);
+            if (i == 0) {
+                US(i, j) = (vel_bc[F_W] == 2) ? u_in[j] : 0.0;
+                continue;
+            }
+            if (i == nx) {
+                if (vel_bc[F_E] == 3) {
+                    double pin = PP(nx - 1, j);
+                    double gp = (-pin - pin) * ih;                /* ghost -p: Dirichlet 0 */
+                    US(i, j) = uc + dt * (-conv_u * (uc - UU(nx - 1, j)) * ih - gp);
+                } else {
+                    US(i, j) = 0.0;
+                }
+                continue;
+            }
+            double uw = UU(i - 1, j), ue = UU(i + 1, j);
+            double usx = (j > 0) ? UU(i, j - 1) : tangential_ghost(vel_bc[F_S], wall_u[F_S], uc);
+            double unx = (j < ny - 1) ? UU(i, j + 1) : tangential_ghost(vel_bc[F_N], wall_u[F_N], uc);
+            double vbar = 0.25 * (VV(i - 1, j) + VV(i, j) + VV(i - 1, j + 1) + VV(i, j + 1));
+            double adv = uc * (ue - uw) * (0.5 * ih) + vbar * (unx - usx) * (0.5 * ih);
+            double lap = (ue + uw + unx + usx - 4.0 * uc) * ih2;
+            double gp = (PP(i, j) - PP(i - 1, j)) * ih;
+            US(i, j) = uc + dt * (-adv + nu * lap - gp);
+        }
+    }
+    /* y-faces: south and north are walls (zero normal velocity) */
+    for (int j = 0; j <= ny; ++j) {
+        for (int i = 0; i < nx; ++i) {
+            double vc = VV(i, j);
+            if (j == 0 || j == ny) { VS(i, j) = 0.0; continue; }
+            double vsy = VV(i, j - 1), vny = VV(i, j + 1);
+            double vw = (i > 0) ? VV(i - 1, j) : tangential_ghost(vel_bc[F_W], wall_u[F_W], vc);
+            double ve = (i < nx - 1) ? VV(i + 1, j) : tangential_ghost(vel_bc[F_E], wall_u[F_E], vc);
+            double ubar = 0.25 * (UU(i, j - 1) + UU(i + 1, j - 1) + UU(i, j) + UU(i + 1, j));
+            double adv = ubar * (ve - vw) * (0.5 * ih) + vc * (vny - vsy) * (0.5 * ih);
+            double lap = (ve + vw + vny + vsy - 4.0 * vc) * ih2;
+            double gp = (PP(i, j) - PP(i, j - 1)) * ih;
+            VS(i, j) = vc + dt * (-adv + nu * lap - gp);
+        }
+    }
+}
+
+/* b = h (u_e - u_w + v_n - v_s) / dt : right-hand side of A_f dp = b (Eq. 4) */
+void or_divergence(int nx, int ny, double h, double dt, const double *u,
+                   const double *v, double *b)
+{
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            b[(size_t)j * nx + i] = h * ((UU(i + 1, j) - UU(i, j))
+                                         + (VV(i, j + 1) - VV(i, j))) / dt;
+}
+
+/* v^{n+1} = v* - dt grad dp on every face whose normal velocity is not
+   prescribed; p += dp */
+void or_correct(int nx, int ny, double h, double dt, const int *vel_bc,
+                const double *dp, double *u, double *v, double *p)
+{
+    double s = dt / h;
+    for (int j = 0; j < ny; ++j) {
+        for (int i = 1; i < nx; ++i)
+            UU(i, j) -= s * (dp[(size_t)j * nx + i] - dp[(size_t)j * nx + i - 1]);
+        if (vel_bc[F_E] == 3) {
+            double pin = dp[(size_t)j * nx + nx - 1];
+            UU(nx, j) -= s * (-pin - pin);
+        }
+    }
+    for (int j = 1; j < ny; ++j)
+        for (int i = 0; i < nx; ++i)
+            VV(i, j) -= s * (dp[(size_t)j * nx + i] - dp[(size_t)(j - 1) * nx + i]);
+    for (size_t k = 0; k < (size_t)nx * ny; ++k) p[k] += dp[k];
+}

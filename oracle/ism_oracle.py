@@ -1,0 +1,338 @@
+"""TEST INFRASTRUCTURE ONLY: the CPU oracle of the ISM pressure solve.
+
+Plain, slow and sequential.  The per-cell loops live in ``ism_oracle.c``
+(IEEE double, fixed loop order, no fused multiply-add); this module builds it,
+wraps it with ctypes and drives the multigrid cycle in the paper's order.  The
+exact coarse solve uses a dense LU factorisation from LAPACK (scipy) of the
+assembled coarse operator, a library primitive standing in for the paper's
+iterative coarse solve (Sec. 4: block Gauss-Seidel to a coarse tolerance).
+
+Readings of points the paper leaves open (each one is restated where it is
+used):
+* cycle: correction scheme, r = b - A_f p, r_c = R r, e_c = A_c^+ r_c exactly,
+  p += P e_c, then nu red-black Gauss-Seidel sweeps (no pre-smoothing), mean
+  of p removed when every face is Neumann, stop on the relative L2 residual
+  ||b - A_f p|| / ||b|| <= tol (the paper's accommodative cycle, Sec. 4.3.1,
+  with an exact coarse solve);
+* the cycle count is the number of coarse corrections applied;
+* Neumann compatibility: the mean of b is removed before the solve.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg use this module.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+import scipy.linalg
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ism_oracle.c")
+_SO = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+VEL_NOSLIP, VEL_FREESLIP, VEL_INFLOW, VEL_OUTFLOW = 0, 1, 2, 3
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_fp = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
+_ip = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C part in place (gcc, no fused multiply-add)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-std=c99", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            i, d = C.c_int, C.c_double
+            sig = {
+                "or_apply_af": [i, i, _ip, _dp, _dp],
+                "or_residual": [i, i, _ip, _dp, _dp, _dp],
+                "or_rbgs_sweep": [i, i, _ip, _dp, _dp],
+                "or_restrict": [i, i, i, _dp, _dp],
+                "or_prolong_add": [i, i, i, _ip, _dp, _dp],
+                "or_prolong_const_add": [i, i, i, _dp, _dp],
+                "or_coarse_operator": [i, i, i, _ip, i, _dp],
+                "or_residual_f32": [i, i, _ip, _fp, _fp, _fp],
+                "or_rbgs_sweep_f32": [i, i, _ip, _fp, _fp],
+                "or_restrict_f32": [i, i, i, _fp, _dp],
+                "or_prolong_add_f32": [i, i, i, _ip, _dp, _fp],
+                "or_predictor": [i, i, d, d, d, _ip, _dp, _dp, d, _dp, _dp, _dp, _dp, _dp],
+                "or_divergence": [i, i, d, d, _dp, _dp, _dp],
+                "or_correct": [i, i, d, d, _ip, _dp, _dp, _dp, _dp],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = C.c_int if name == "or_coarse_operator" else None
+            _lib = L
+    return _lib
+
+
+def _bc(bc):
+    a = np.ascontiguousarray(np.asarray(bc, dtype=np.int32).reshape(4))
+    return a
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# thin wrappers (fields are (ny, nx) float64 arrays)
+# --------------------------------------------------------------------------
+
+def apply_af(p, bc):
+    ny, nx = p.shape
+    out = np.empty_like(p, dtype=np.float64)
+    lib().or_apply_af(nx, ny, _bc(bc), _c64(p), out)
+    return out
+
+
+def residual(p, b, bc):
+    ny, nx = p.shape
+    r = np.empty((ny, nx), dtype=np.float64)
+    lib().or_residual(nx, ny, _bc(bc), _c64(p), _c64(b), r)
+    return r
+
+
+def rbgs_sweep(p, b, bc):
+    """One red-black Gauss-Seidel sweep in place (Sec. 3.1)."""
+    ny, nx = p.shape
+    assert p.dtype == np.float64 and p.flags.c_contiguous
+    lib().or_rbgs_sweep(nx, ny, _bc(bc), p, _c64(b))
+
+
+def restrict(r, m):
+    ny, nx = r.shape
+    rc = np.empty((ny // m, nx // m), dtype=np.float64)
+    lib().or_restrict(nx, ny, m, _c64(r), rc)
+    return rc
+
+
+def prolong_add(p, q, m, bc):
+    ny, nx = p.shape
+    assert p.dtype == np.float64 and p.flags.c_contiguous
+    lib().or_prolong_add(nx, ny, m, _bc(bc), _c64(q), p)
+
+
+def prolong_const_add(p, q, m):
+    ny, nx = p.shape
+    assert p.dtype == np.float64 and p.flags.c_contiguous
+    lib().or_prolong_const_add(nx, ny, m, _c64(q), p)
+
+
+def coarse_operator(nx, ny, m, bc, kind="ism"):
+    """Dense coarse operator A_c (Sec. 3.3); kind 'ism' or 'acm'."""
+    nc = (nx // m) * (ny // m)
+    Ac = np.empty((nc, nc), dtype=np.float64)
+    rc = lib().or_coarse_operator(nx, ny, m, _bc(bc), 0 if kind == "ism" else 1, Ac)
+    if rc != 0:
+        raise MemoryError("oracle coarse operator allocation failed")
+    return Ac
+
+
+# --------------------------------------------------------------------------
+# the two-level solver
+# --------------------------------------------------------------------------
+
+class OracleISM:
+    """Two-level ISM (kind='ism') or two-level ACM (kind='acm') solver.
+
+    Sec. 3.3-3.4: aggressive m x m coarsening (16h / 32h), interpolated
+    nine-point coarse stencil (ISM) or summed five-point coarse equations with
+    piecewise-constant correction (ACM), red-black Gauss-Seidel smoothing.
+    """
+
+    def __init__(self, nx, ny, m, bc=(0, 0, 0, 0), kind="ism", nu=8):
+        if nx % m or ny % m:
+            raise ValueError("grid must be a multiple of the coarsening factor")
+        self.nx, self.ny, self.m = nx, ny, m
+        self.bc = _bc(bc)
+        self.kind = kind
+        self.nu = nu
+        self.singular = not np.any(self.bc)
+        self.Ac = coarse_operator(nx, ny, m, self.bc, kind)
+        nc = self.Ac.shape[0]
+        M = -self.Ac
+        if self.singular:
+            # all-Neumann: A_c 1 = 0.  (-A_c + 1 1^T / nc) is nonsingular and,
+            # for a right-hand side with zero sum, returns minus the mean-free
+            # solution of A_c e = r_c.
+            M = M + np.full((nc, nc), 1.0 / nc)
+        self._lu = scipy.linalg.lu_factor(M, check_finite=False)
+
+    # e_c = A_c^+ r_c (exact coarse solve)
+    def coarse_solve(self, rc):
+        x = scipy.linalg.lu_solve(self._lu, rc.reshape(-1), check_finite=False)
+        return (-x).reshape(rc.shape)
+
+    def _correct(self, p, ec):
+        if self.kind == "ism":
+            prolong_add(p, ec, self.m, self.bc)
+        else:
+            prolong_const_add(p, ec, self.m)
+
+    def cycle(self, p, b):
+        """One cycle (reading: correction scheme, exact coarse solve, then nu
+        post-smoothing sweeps, no pre-smoothing; mean of p removed when all
+        faces are Neumann)."""
+        r = residual(p, b, self.bc)
+        rc = restrict(r, self.m)
+        ec = self.coarse_solve(rc)
+        self._correct(p, ec)
+        for _ in range(self.nu):
+            rbgs_sweep(p, b, self.bc)
+        if self.singular:
+            p -= p.mean()
+
+    def prepare_rhs(self, b):
+        b = np.array(b, dtype=np.float64, order="C", copy=True)
+        if self.singular:
+            b -= b.mean()
+        return b
+
+    def solve(self, b, p0=None, tol=1e-8, max_cycles=10000):
+        """FP64 solve.  Returns (p, cycles, relres_history)."""
+        b = self.prepare_rhs(b)
+        p = np.zeros_like(b) if p0 is None else np.array(p0, dtype=np.float64, order="C", copy=True)
+        if self.singular:
+            p -= p.mean()
+        bn = np.linalg.norm(b)
+        if bn == 0.0:
+            return np.zeros_like(b), 0, [0.0]
+        hist = [np.linalg.norm(residual(p, b, self.bc)) / bn]
+        cycles = 0
+        while hist[-1] > tol and cycles < max_cycles:
+            self.cycle(p, b)
+            cycles += 1
+            hist.append(np.linalg.norm(residual(p, b, self.bc)) / bn)
+        return p, cycles, hist
+
+    # ---------------- mixed precision (emulated single-precision inner) ----
+
+    def inner_cycle_f32(self, e, r32):
+        """One inner cycle on A_f e = r32 with float loops; the exact coarse
+        solve runs in double and is rounded to float by the prolongation."""
+        L = lib()
+        nx, ny, m = self.nx, self.ny, self.m
+        rin = np.empty_like(e)
+        L.or_residual_f32(nx, ny, self.bc, e, r32, rin)
+        rc = np.empty((ny // m, nx // m), dtype=np.float64)
+        L.or_restrict_f32(nx, ny, m, rin, rc)
+        ec = self.coarse_solve(rc)
+        L.or_prolong_add_f32(nx, ny, m, self.bc, np.ascontiguousarray(ec), e)
+        for _ in range(self.nu):
+            L.or_rbgs_sweep_f32(nx, ny, self.bc, e, r32)
+        if self.singular:
+            e -= np.float32(e.astype(np.float64).mean())
+
+    def inner_residual_norm_f32(self, e, r32):
+        rin = np.empty_like(e)
+        lib().or_residual_f32(self.nx, self.ny, self.bc, e, r32, rin)
+        return float(np.linalg.norm(rin.astype(np.float64)))
+
+    # Single-precision rounding floor of the inner residual: every Gauss-Seidel
+    # update rounds e to float (relative error up to 2^-24), and the five-point
+    # stencil maps that noise to a residual of about 1.5e-7 ||e||.  The inner
+    # solve stops once it is within FLOOR_MULT * 2^-23 ||e|| of that floor.
+    FLOOR_UNIT = 2.0 ** -23
+    FLOOR_MULT = 4.0
+
+    def solve_mixed(self, b, p0=None, tol=1e-8, max_outer=50, inner_tol=1e-3,
+                    inner_max=10000):
+        """FP64 iterative refinement around single-precision inner cycles.
+
+        Outer step (FP64): r = b - A_f p, relres = ||r|| / ||b||.  Inner solve
+        (float): cycles on A_f e = r (e_0 = 0) until the float residual is
+        below max(inner_tol ||r||, FLOOR_MULT 2^-23 ||e||) or ``inner_max``
+        cycles.  Then p += e (FP64) and the mean of p is removed (all-Neumann).
+        Returns (p, outer_iterations, inner_cycles_total, relres_history).
+        """
+        b = self.prepare_rhs(b)
+        p = np.zeros_like(b) if p0 is None else np.array(p0, dtype=np.float64, order="C", copy=True)
+        if self.singular:
+            p -= p.mean()
+        bn = np.linalg.norm(b)
+        if bn == 0.0:
+            return np.zeros_like(b), 0, 0, [0.0]
+        r = residual(p, b, self.bc)
+        hist = [np.linalg.norm(r) / bn]
+        outer = inner_total = 0
+        while hist[-1] > tol and outer < max_outer:
+            r32 = np.ascontiguousarray(r, dtype=np.float32)
+            r32n = float(np.linalg.norm(r32.astype(np.float64)))
+            e = np.zeros_like(r32)
+            for _ in range(inner_max):
+                self.inner_cycle_f32(e, r32)
+                inner_total += 1
+                en = float(np.linalg.norm(e.astype(np.float64)))
+                lim = max(inner_tol * r32n, self.FLOOR_MULT * self.FLOOR_UNIT * en)
+                if self.inner_residual_norm_f32(e, r32) <= lim:
+                    break
+            p += e.astype(np.float64)
+            if self.singular:
+                p -= p.mean()
+            outer += 1
+            r = residual(p, b, self.bc)
+            hist.append(np.linalg.norm(r) / bn)
+        return p, outer, inner_total, hist
+
+
+# --------------------------------------------------------------------------
+# projection time step (Sec. 2.2-2.3, Eq. 3-4)
+# --------------------------------------------------------------------------
+
+def predictor(u, v, p, h, dt, nu, vel_bc, wall_u=(0, 0, 0, 0), u_in=None, conv_u=1.0):
+    ny, nx = p.shape
+    us = np.empty((ny, nx + 1)); vs = np.empty((ny + 1, nx))
+    uin = np.zeros(ny) if u_in is None else _c64(u_in)
+    lib().or_predictor(nx, ny, h, dt, nu, _bc(vel_bc), _c64(np.asarray(wall_u, float)),
+                       uin, conv_u, _c64(u), _c64(v), _c64(p), us, vs)
+    return us, vs
+
+
+def divergence(u, v, h, dt):
+    ny, nx = v.shape[0] - 1, u.shape[1] - 1
+    b = np.empty((ny, nx))
+    lib().or_divergence(nx, ny, h, dt, _c64(u), _c64(v), b)
+    return b
+
+
+def correct(u, v, p, dp, h, dt, vel_bc):
+    ny, nx = p.shape
+    for a in (u, v, p):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    lib().or_correct(nx, ny, h, dt, _bc(vel_bc), _c64(dp), u, v, p)
+
+
+def pressure_bc(vel_bc):
+    """Dirichlet-0 pressure on outflow faces, Neumann elsewhere."""
+    return tuple(1 if k == VEL_OUTFLOW else 0 for k in vel_bc)
+
+
+def proj_step(u, v, p, h, dt, nu, vel_bc, solver: OracleISM, wall_u=(0, 0, 0, 0),
+              u_in=None, conv_u=1.0, tol=1e-8, max_cycles=10000, dp0=None):
+    """One Goda incremental pressure-correction step (Sec. 2.2) in place on
+    (u, v, p).  Returns (dp, cycles, relres_history)."""
+    us, vs = predictor(u, v, p, h, dt, nu, vel_bc, wall_u, u_in, conv_u)
+    b = divergence(us, vs, h, dt)
+    dp, cycles, hist = solver.solve(b, p0=dp0, tol=tol, max_cycles=max_cycles)
+    u[...] = us
+    v[...] = vs
+    correct(u, v, p, dp, h, dt, vel_bc)
+    return dp, cycles, hist

@@ -1,0 +1,316 @@
+"""Pins of the CPU oracle against facts fixed by the paper and the mathematics.
+
+None of these compares the oracle with itself: each checks a textbook
+identity (Kronecker-sum Laplacian, DCT/DST diagonalisation), a closed form
+derived from Eq. 5-7, an exactness property of an operator, brute force on a
+tiny grid, or a convergence rate.
+"""
+import numpy as np
+import pytest
+import scipy.fft
+
+import oracle as O
+from synth.inputs import random_field, smooth_rhs
+from tests.conftest import ALL_BCS
+
+
+# ---------------------------------------------------------------- helpers
+
+def second_difference(n, lo, hi):
+    """1-D cell-centred second difference with ghost rules: Neumann ghost
+    = inner value (end diagonal -1), Dirichlet-0 ghost = -inner (end -3)."""
+    T = np.diag(np.full(n, -2.0)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)
+    T[0, 0] = -1.0 if lo == 0 else -3.0
+    T[-1, -1] = -1.0 if hi == 0 else -3.0
+    return T
+
+
+def dense_laplacian(nx, ny, bc):
+    """Five-point operator as the Kronecker sum of 1-D second differences."""
+    return (np.kron(np.eye(ny), second_difference(nx, bc[0], bc[1]))
+            + np.kron(second_difference(ny, bc[2], bc[3]), np.eye(nx)))
+
+
+def spectral_solve(b, bc):
+    """Exact solve of A_f p = b for uniform face types per axis using the
+    DCT-II (Neumann-Neumann) or DST-II (Dirichlet-Dirichlet) bases, whose
+    eigenvalues are -4 sin^2(pi k / 2n) and -4 sin^2(pi (k+1) / 2n)."""
+    ny, nx = b.shape
+    assert bc[0] == bc[1] and bc[2] == bc[3]
+    tx = "dct" if bc[0] == 0 else "dst"
+    ty = "dct" if bc[2] == 0 else "dst"
+    kx = np.arange(nx) + (0 if tx == "dct" else 1)
+    ky = np.arange(ny) + (0 if ty == "dct" else 1)
+    lam = (-4 * np.sin(np.pi * kx / (2 * nx)) ** 2)[None, :] + \
+          (-4 * np.sin(np.pi * ky / (2 * ny)) ** 2)[:, None]
+    bh = b.copy()
+    bh = (scipy.fft.dct if tx == "dct" else scipy.fft.dst)(bh, type=2, axis=1, norm="ortho")
+    bh = (scipy.fft.dct if ty == "dct" else scipy.fft.dst)(bh, type=2, axis=0, norm="ortho")
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ph = np.where(lam == 0.0, 0.0, bh / lam)
+    ph = (scipy.fft.idct if ty == "dct" else scipy.fft.idst)(ph, type=2, axis=0, norm="ortho")
+    ph = (scipy.fft.idct if tx == "dct" else scipy.fft.idst)(ph, type=2, axis=1, norm="ortho")
+    return ph
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def S1(n, lo, hi):
+    """tridiag(1, 2, 1) with end diagonal 3 at a Neumann end, 1 at a
+    Dirichlet-0 end: the 1-D factor of the ISM coarse operator."""
+    S = np.diag(np.full(n, 2.0)) + np.diag(np.ones(n - 1), 1) + np.diag(np.ones(n - 1), -1)
+    S[0, 0] = 3.0 if lo == 0 else 1.0
+    S[-1, -1] = 3.0 if hi == 0 else 1.0
+    return S
+
+
+# ---------------------------------------------------------------- fine operator
+
+@pytest.mark.parametrize("bc", ALL_BCS)
+def test_fine_operator_is_kronecker_sum(bc):
+    nx, ny = 12, 8
+    eye = np.eye(nx * ny)
+    A = np.column_stack([O.apply_af(eye[k].reshape(ny, nx), bc).ravel() for k in range(nx * ny)])
+    assert np.array_equal(A, dense_laplacian(nx, ny, bc))
+    assert np.array_equal(A, A.T)                       # symmetric
+    assert np.linalg.eigvalsh(A).max() <= 1e-12         # negative semi-definite
+    if not any(bc):
+        assert np.abs(A.sum(axis=1)).max() == 0.0       # Neumann: row sums vanish
+
+
+def test_fine_operator_dct_spectrum():
+    """All-Neumann: the DCT-II modes are eigenvectors with eigenvalues
+    -4 sin^2(pi k/2nx) - 4 sin^2(pi l/2ny)."""
+    nx, ny = 24, 16
+    for (k, l) in [(0, 0), (1, 0), (3, 5), (23, 15), (7, 2)]:
+        mode = np.outer(np.cos(np.pi * l * (np.arange(ny) + 0.5) / ny),
+                        np.cos(np.pi * k * (np.arange(nx) + 0.5) / nx))
+        lam = -4 * np.sin(np.pi * k / (2 * nx)) ** 2 - 4 * np.sin(np.pi * l / (2 * ny)) ** 2
+        np.testing.assert_allclose(O.apply_af(mode, (0, 0, 0, 0)), lam * mode, atol=1e-12)
+
+
+def test_residual_definition():
+    p = random_field(20, 12, 1)
+    b = random_field(20, 12, 2)
+    bc = (1, 0, 0, 1)
+    np.testing.assert_allclose(O.residual(p, b, bc), b - dense_laplacian(20, 12, bc).dot(p.ravel()).reshape(12, 20),
+                               atol=1e-12)
+
+
+# ---------------------------------------------------------------- smoother
+
+@pytest.mark.parametrize("bc", ALL_BCS)
+def test_rbgs_leaves_black_residual_zero(bc):
+    """Red cells first, then black: after one sweep each black cell has just
+    solved its own equation with its (red) neighbours fixed, so its residual
+    vanishes; red residuals do not."""
+    nx, ny = 18, 14
+    p = random_field(nx, ny, 3)
+    b = random_field(nx, ny, 4)
+    O.rbgs_sweep(p, b, bc)
+    r = O.residual(p, b, bc)
+    jj, ii = np.mgrid[0:ny, 0:nx]
+    black = (ii + jj) % 2 == 1
+    assert np.abs(r[black]).max() <= 1e-13
+    assert np.abs(r[~black]).max() > 1e-3
+
+
+def test_rbgs_fixed_point_is_exact_solution():
+    nx, ny = 64, 32
+    b = smooth_rhs(nx, ny, 5)
+    b -= b.mean()
+    pe = spectral_solve(b, (0, 0, 0, 0))
+    p = pe.copy()
+    O.rbgs_sweep(p, b, (0, 0, 0, 0))
+    assert np.abs(p - pe).max() <= 1e-12 * np.abs(pe).max()
+
+
+# ---------------------------------------------------------------- transfer operators
+
+def test_restriction_is_block_sum():
+    r = random_field(64, 32, 6)
+    rc = O.restrict(r, 16)
+    assert rc.shape == (2, 4)
+    np.testing.assert_allclose(rc, r.reshape(2, 16, 4, 16).sum(axis=(1, 3)), rtol=1e-13)
+
+
+def test_prolongation_reproduces_linear_functions():
+    """Eq. 5 is exact for bilinear functions: inside the hull of coarse
+    centres the interpolant of a + b X + c Y + d X Y is that function."""
+    m, ncx, ncy = 16, 5, 4
+    nx, ny = m * ncx, m * ncy
+    Xc = (np.arange(ncx) + 0.5) * m
+    Yc = (np.arange(ncy) + 0.5) * m
+    f = lambda X, Y: 0.3 + 1.7 * X - 0.4 * Y + 0.01 * X * Y
+    q = f(Xc[None, :], Yc[:, None])
+    p = np.zeros((ny, nx))
+    O.prolong_add(p, q, m, (0, 0, 0, 0))
+    x = np.arange(nx) + 0.5
+    y = np.arange(ny) + 0.5
+    inside_x = (x >= Xc[0]) & (x <= Xc[-1])
+    inside_y = (y >= Yc[0]) & (y <= Yc[-1])
+    ex = f(x[None, :], y[:, None])
+    np.testing.assert_allclose(p[np.ix_(inside_y, inside_x)], ex[np.ix_(inside_y, inside_x)], rtol=1e-13)
+
+
+def test_prolongation_boundary_rules():
+    """Mirror ghosts: a constant coarse field interpolates to the same
+    constant up to a Neumann wall, and to a linear ramp that vanishes on a
+    Dirichlet-0 wall (fine cell k from the wall gets (2k+1)/m)."""
+    m = 16
+    q = np.ones((3, 4))
+    p = np.zeros((3 * m, 4 * m))
+    O.prolong_add(p, q, m, (0, 0, 0, 0))
+    np.testing.assert_allclose(p, 1.0, rtol=1e-14)
+    p = np.zeros((3 * m, 4 * m))
+    O.prolong_add(p, q, m, (1, 0, 0, 0))
+    k = np.arange(m // 2)
+    np.testing.assert_allclose(p[m:2 * m, :m // 2], np.tile((2 * k + 1) / m, (m, 1)), rtol=1e-13)
+    np.testing.assert_allclose(p[:, m // 2:], 1.0, rtol=1e-14)
+
+
+# ---------------------------------------------------------------- coarse operator
+
+@pytest.mark.parametrize("bc", ALL_BCS)
+@pytest.mark.parametrize("m", [8, 16, 32])
+def test_ism_coarse_operator_closed_form(bc, m):
+    """Summing the fluxes of Eq. 6-7 over the coarse faces gives
+    A_c = 1/4 (S_y kron S_x) - 4 I (derived by summing the bilinear weights
+    1/8, 3/4, 1/8 along each coarse face), independent of m."""
+    ncx, ncy = 5, 4
+    Ac = O.coarse_operator(ncx * m, ncy * m, m, bc, "ism")
+    cf = 0.25 * np.kron(S1(ncy, bc[2], bc[3]), S1(ncx, bc[0], bc[1])) - 4.0 * np.eye(ncx * ncy)
+    np.testing.assert_allclose(Ac, cf, atol=1e-12)
+
+
+def test_ism_coarse_stencil_is_nine_point():
+    """Sec. 3.3: the five-point fine stencil becomes a nine-point coarse
+    stencil; interior weights: corners 1/4, edges 1/2, centre -3."""
+    m, ncx, ncy = 16, 6, 5
+    Ac = O.coarse_operator(ncx * m, ncy * m, m, (0, 0, 0, 0), "ism")
+    assert (np.abs(Ac) > 1e-14).sum(axis=1).max() == 9
+    K = 2 * ncx + 3
+    row = Ac[K].reshape(ncy, ncx)[1:4, 2:5]
+    np.testing.assert_allclose(row, [[0.25, 0.5, 0.25], [0.5, -3.0, 0.5], [0.25, 0.5, 0.25]], atol=1e-13)
+    np.testing.assert_allclose(Ac.sum(axis=1), 0.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("bc", ALL_BCS)
+def test_acm_coarse_operator_is_scaled_five_point(bc):
+    """ACM (Sec. 3.2): summing the fine equations with p constant per
+    coarse cell gives m times the coarse five-point operator."""
+    m, ncx, ncy = 16, 5, 3
+    Ac = O.coarse_operator(ncx * m, ncy * m, m, bc, "acm")
+    np.testing.assert_allclose(Ac, m * dense_laplacian(ncx, ncy, bc), atol=1e-12)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (0, 1, 0, 0)])
+def test_coarse_operator_equals_R_Af_P(bc):
+    """The face-flux construction equals the product R A_f P of the block-sum
+    restriction, the fine operator and the bilinear prolongation."""
+    m, ncx, ncy = 8, 4, 3
+    nx, ny = m * ncx, m * ncy
+    nc, N = ncx * ncy, nx * ny
+    P = np.zeros((N, nc))
+    for k in range(nc):
+        q = np.zeros(nc)
+        q[k] = 1.0
+        p = np.zeros((ny, nx))
+        O.prolong_add(p, q.reshape(ncy, ncx), m, bc)
+        P[:, k] = p.ravel()
+    R = np.zeros((nc, N))
+    for k in range(N):
+        r = np.zeros(N)
+        r[k] = 1.0
+        R[:, k] = O.restrict(r.reshape(ny, nx), m).ravel()
+    RAP = R @ dense_laplacian(nx, ny, bc) @ P
+    np.testing.assert_allclose(O.coarse_operator(nx, ny, m, bc, "ism"), RAP, atol=1e-12)
+
+
+@pytest.mark.parametrize("bc", ALL_BCS)
+def test_coarse_correction_annihilates_restricted_residual(bc):
+    """Petrov-Galerkin: with A_c = R A_f P and an exact coarse solve, the
+    restricted residual right after the correction is zero."""
+    m, nx, ny = 16, 96, 64
+    s = O.OracleISM(nx, ny, m, bc)
+    b = s.prepare_rhs(smooth_rhs(nx, ny, 7))
+    p = random_field(nx, ny, 8)
+    rc = O.restrict(O.residual(p, b, bc), m)
+    ec = s.coarse_solve(rc)
+    O.prolong_add(p, ec, m, bc)
+    after = O.restrict(O.residual(p, b, bc), m)
+    assert np.abs(after).max() <= 1e-11 * np.abs(rc).max()
+
+
+# ---------------------------------------------------------------- solver
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (1, 1, 1, 1)])
+def test_solve_matches_spectral_exact_solution(bc):
+    nx, ny, m = 128, 64, 16
+    b = smooth_rhs(nx, ny, 9) + (0 if not any(bc) else 1e-5)
+    s = O.OracleISM(nx, ny, m, bc)
+    p, cycles, hist = s.solve(b, tol=1e-11)
+    assert hist[-1] <= 1e-11
+    pe = spectral_solve(s.prepare_rhs(b), bc)
+    assert rel(p, pe) <= 1e-10
+
+
+@pytest.mark.parametrize("bc", ALL_BCS)
+@pytest.mark.parametrize("m", [4, 8])
+def test_solve_matches_dense_pseudo_inverse_16x16(bc, m):
+    n = 16
+    b = random_field(n, n, 10)
+    A = dense_laplacian(n, n, bc)
+    if not any(bc):
+        b = b - b.mean()
+        x = np.linalg.pinv(A, rcond=1e-10) @ b.ravel()   # cut the null mode
+    else:
+        x = np.linalg.solve(A, b.ravel())
+    s = O.OracleISM(n, n, m, bc, nu=2)
+    p, cycles, hist = s.solve(b, tol=1e-12, max_cycles=5000)
+    assert hist[-1] <= 1e-12
+    assert rel(p.ravel(), x) <= 1e-10
+
+
+def test_manufactured_solution_second_order():
+    """p = cos(pi x) cos(pi y) with Neumann walls: lap p = -2 pi^2 p.  The
+    cell-centred scheme converges with order 2."""
+    errs = []
+    for n in (32, 64, 128, 256):
+        h = 1.0 / n
+        xc = (np.arange(n) + 0.5) * h
+        pe = np.outer(np.cos(np.pi * xc), np.cos(np.pi * xc))
+        b = h * h * (-2 * np.pi ** 2) * pe
+        s = O.OracleISM(n, n, 16 if n >= 64 else 8)
+        p, cycles, hist = s.solve(b, tol=1e-10)
+        errs.append(np.abs(p - (pe - pe.mean())).max())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > 1.9) and np.all(orders < 2.1), (errs, orders)
+
+
+def test_neumann_solution_has_zero_mean():
+    s = O.OracleISM(64, 64, 16)
+    p, c, h = s.solve(smooth_rhs(64, 64, 11) + 0.3, tol=1e-9)
+    assert abs(p.mean()) <= 1e-15 * np.abs(p).max()
+
+
+def test_ism_converges_in_fewer_cycles_than_acm():
+    """Sec. 4.3: the interpolated stencil needs fewer cycles than ACM with
+    the same restriction length (256^2, 16h, nu = 8, to 1e-8)."""
+    b = smooth_rhs(256, 256, 0)
+    ism = O.OracleISM(256, 256, 16, kind="ism", nu=8).solve(b, tol=1e-8)[1]
+    acm = O.OracleISM(256, 256, 16, kind="acm", nu=8).solve(b, tol=1e-8)[1]
+    assert ism < acm / 2, (ism, acm)
+
+
+def test_mixed_refinement_reaches_tolerance():
+    nx = ny = 128
+    b = smooth_rhs(nx, ny, 12)
+    s = O.OracleISM(nx, ny, 16)
+    pm, outer, inner, hist = s.solve_mixed(b, tol=1e-8)
+    assert hist[-1] <= 1e-8
+    assert outer >= 2                      # one float solve cannot reach 1e-8
+    pe = spectral_solve(s.prepare_rhs(b), (0, 0, 0, 0))
+    assert rel(pm, pe) <= 1e-9
