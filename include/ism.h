@@ -1,0 +1,212 @@
+/*
+ * ism.h -- C ABI of the GB300 interpolated stencil multigrid (ISM) library.
+ *
+ * Method: Tegze & Toth, "A GPU cluster optimized multigrid scheme for
+ * computing unsteady incompressible fluid flow".  The library solves the
+ * cell-centred pressure Poisson equation of a projection time step (Sec. 2.2,
+ * Eq. 4) with a two-level multigrid: red-black Gauss-Seidel smoothing on the
+ * fine grid (Sec. 3.1), aggregating restriction over m x m blocks with
+ * m = 16 or 32 (Sec. 3.2-3.4, Fig. 2b), an exact solve on the interpolated
+ * nine-point coarse stencil (Sec. 3.3, Eq. 5-7) and bilinear prolongation
+ * with correction (Eq. 5).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Fields are row-major: cell (i, j), i along x (fastest), j along y, at
+ * element j*nx + i.  Face order for boundary arrays is west, east, south,
+ * north.  The fine operator is the finite-volume five-point flux sum
+ *     (A_f p)_c = sum over faces (p_neighbour - p_c),
+ * where a Neumann face contributes 0 and a Dirichlet-0 face -2 p_c; the
+ * equation solved is A_f p = b ("flux units": b is h^2 times the usual
+ * Laplacian right-hand side).
+ *
+ * Pointers: arrays documented "device" are CUDA device pointers (or managed
+ * memory) owned by the caller; the library never frees them.  Arrays
+ * documented "host" are ordinary host memory.  The library owns all of its
+ * workspaces; they live until ism_destroy.
+ *
+ * Streams: every call is ordered on the stream given to ism_setup.  Calls
+ * that return numbers on the host (cycles, residuals) synchronise that
+ * stream before returning.  A context must not be used from two host threads
+ * at once.
+ *
+ * Errors: every entry point returns an ism_status.  ISM_ERR_ARG leaves all
+ * caller arrays untouched.  ISM_ERR_NOT_CONVERGED leaves the last iterate in
+ * the output array and the reached residual in the *_out arguments.  No entry
+ * point aborts the process or traps on the device; device-side limits
+ * (iteration caps) end in a status code.
+ */
+#ifndef ISM_H
+#define ISM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ISM_OK = 0,
+    ISM_ERR_ARG = 1,            /* invalid argument; nothing was written */
+    ISM_ERR_NOT_CONVERGED = 2,  /* cycle or refinement cap reached before tol */
+    ISM_ERR_NONFINITE = 3,      /* NaN or Inf met in the right-hand side or iterate */
+    ISM_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+    ISM_ERR_NOMEM = 5           /* device or host allocation failed */
+} ism_status;
+
+typedef enum { ISM_BC_NEUMANN = 0, ISM_BC_DIRICHLET0 = 1 } ism_bc;
+
+typedef enum {
+    ISM_FP64 = 0,   /* every step in IEEE double */
+    ISM_MIXED = 1   /* FP64 iterative refinement around single-precision cycles */
+} ism_precision;
+
+typedef enum {
+    ISM_COARSE_ISM = 0,   /* interpolated nine-point coarse stencil, bilinear correction (Sec. 3.3) */
+    ISM_COARSE_ACM = 1    /* summed five-point coarse equations, constant correction (Sec. 3.2) */
+} ism_coarse_kind;
+
+/* Velocity boundary kinds of the projection step, per face. */
+typedef enum {
+    ISM_VEL_NOSLIP = 0,    /* wall; tangential velocity wall_u[face] */
+    ISM_VEL_FREESLIP = 1,  /* wall; zero tangential stress */
+    ISM_VEL_INFLOW = 2,    /* west face only: u = inflow profile */
+    ISM_VEL_OUTFLOW = 3    /* east face only: convective outflow, pressure Dirichlet 0 */
+} ism_vel_bc;
+
+/* Solver options (ism_get_options fills the defaults). */
+typedef struct {
+    int nu;               /* post-smoothing red-black sweeps per cycle (default 8) */
+    int sweeps_per_pass;  /* single precision: sweeps fused into one pass over memory (default 4; nu % it == 0) */
+    int kind;             /* ism_coarse_kind (default ISM_COARSE_ISM) */
+    int max_outer;        /* mixed: refinement iterations cap (default 50) */
+    int inner_max;        /* mixed: single-precision cycles per refinement iteration cap (default 10000) */
+    double inner_tol;     /* mixed: inner stop when ||r_in|| <= inner_tol ||r|| ... (default 1e-3) */
+    double floor_mult;    /* ... or ||r_in|| <= floor_mult 2^-23 ||e|| (rounding floor, default 4) */
+    int check_every;      /* cycles launched between host reads of the convergence flag (default 16) */
+    int use_graphs;       /* capture the cycle loop in CUDA graphs (default 1) */
+} ism_options;
+
+typedef struct ism_ctx ism_ctx;
+
+/* Human-readable name of a status code (static string). */
+const char *ism_status_str(ism_status s);
+
+/* ism_setup -- validate the problem and build the coarse level.
+ * Sec. 3.3-3.4 and Sec. 4 (problem statement: grid, boundary conditions,
+ * tile/coarsening size).
+ *   nx, ny   fine cells; both multiples of `coarsen`, nx*ny <= 2^31.
+ *   h        cell size (used by proj_step only; > 0).
+ *   bc       host, 4 ints (ism_bc) for the west, east, south, north faces.
+ *   coarsen  m in {8, 16, 32}: coarse cells are m x m blocks of fine cells.
+ *   prec     ism_precision.
+ *   stream   cudaStream_t to order all work on (NULL = legacy default stream).
+ *   out      host; receives the new context.
+ * Builds the coarse operator A_c = R A_f P in FP64 on the host (closed form
+ * of the face-flux sums of Eq. 6-7), its separable eigenbases, and allocates
+ * all workspaces.  Returns ISM_ERR_ARG, ISM_ERR_NOMEM or ISM_ERR_CUDA on
+ * failure (*out untouched). */
+ism_status ism_setup(int nx, int ny, double h, const int bc[4], int coarsen,
+                     ism_precision prec, void *stream, ism_ctx **out);
+
+void ism_destroy(ism_ctx *ctx);
+
+ism_status ism_get_options(const ism_ctx *ctx, ism_options *opt);
+/* Replace the options; invalid values -> ISM_ERR_ARG (nothing changed). */
+ism_status ism_set_options(ism_ctx *ctx, const ism_options *opt);
+
+/* ism_solve -- solve A_f p = rhs to ||rhs - A_f p||_2 <= tol ||rhs||_2.
+ * Sec. 3.4 (two-level sparse V cycle) with the cycle of Sec. 4.3.1
+ * restated as: r = b - A_f p, r_c = R r (block sums), e_c = A_c^+ r_c
+ * (exact), p += P e_c, nu red-black sweeps.
+ *   rhs         device, nx*ny doubles (read only).  With all faces Neumann
+ *               its mean is removed before solving (compatibility).
+ *   p           device, nx*ny doubles; in: initial guess, out: solution
+ *               (mean 0 when all faces are Neumann).
+ *   tol         relative L2 residual target (> 0).
+ *   max_cycles  cap on coarse corrections (FP64) or on single-precision
+ *               cycles over all refinement iterations (mixed).
+ *   cycles_out  host, may be NULL: cycles applied.
+ *   relres_out  host, may be NULL: final relative residual (FP64 measure).
+ * Synchronises the context's stream. */
+ism_status ism_solve(ism_ctx *ctx, const double *rhs, double *p, double tol,
+                     int max_cycles, int *cycles_out, double *relres_out);
+
+/* Relative-residual history of the last solve: one entry per cycle (FP64)
+ * or per refinement iteration (mixed), starting with the initial guess.
+ * hist: host array of cap doubles; returns the number of entries written. */
+int ism_last_history(const ism_ctx *ctx, double *hist, int cap);
+
+/* Counters of the last solve (host, any may be NULL): refinement iterations
+ * (mixed; 0 for FP64), single-precision or FP64 cycles, kernel launches. */
+ism_status ism_last_counts(const ism_ctx *ctx, int *outer, int *cycles, long long *launches);
+
+/* ---------------- kernel-level entry points (one step of the cycle) ------
+ * Device arrays in the context's precision T (double for ISM_FP64, float
+ * for ISM_MIXED); results are asynchronous on the context's stream. */
+
+/* k red-black Gauss-Seidel sweeps in place on p (Sec. 3.1): red cells
+ * ((i+j) even) first; p_c = (sum of in-domain neighbours - b_c) / d_c with
+ * d_c = in-domain neighbours + 2 per Dirichlet-0 face. */
+ism_status ism_smooth(ism_ctx *ctx, void *p, const void *b, int sweeps);
+
+/* r_c = R (b - A_f p) (block sums over m x m, Sec. 3.2-3.3); rc: device,
+ * (ny/m)*(nx/m) values of T.  norms: host, 2 doubles or NULL:
+ * ||b - A_f p||_2 and sum(p). */
+ism_status ism_residual_restrict(ism_ctx *ctx, const void *p, const void *b,
+                                 void *rc, double *norms);
+
+/* e_c = A_c^+ r_c (exact coarse solve on the mean-free subspace when all
+ * faces are Neumann); rc, ec: device, (ny/m)*(nx/m) values of T. */
+ism_status ism_coarse_solve(ism_ctx *ctx, const void *rc, void *ec);
+
+/* p += P e_c (bilinear, Eq. 5, mirror ghost centres beyond the boundary;
+ * constant per block for ISM_COARSE_ACM). */
+ism_status ism_prolong_add(ism_ctx *ctx, const void *ec, void *p);
+
+/* ---------------- projection time step (Sec. 2.2-2.3, Eq. 3-4) ---------- */
+
+/* Velocity boundary setup for proj_step.
+ *   vel_bc  host, 4 ints (ism_vel_bc).  INFLOW only on the west face,
+ *           OUTFLOW only on the east face; the pressure boundary given to
+ *           ism_setup must be Dirichlet-0 exactly on OUTFLOW faces.
+ *   wall_u  host, 4 doubles: tangential wall speed of NOSLIP faces.
+ *   u_in    device, ny floats: west inflow profile (NULL if no inflow);
+ *           read at every proj_step, so the caller may update it.
+ *   conv_u  convective outflow speed (> 0 when an OUTFLOW face exists). */
+ism_status ism_set_flow(ism_ctx *ctx, const int vel_bc[4], const double wall_u[4],
+                        const float *u_in, double conv_u);
+
+/* One Goda incremental pressure-correction step, in place:
+ *   v* = v + dt [ -(v.grad) v + nu lap v - grad p ]  (forward Euler,
+ *        second-order central differences on the MAC grid)
+ *   A_f dp = h div(v*) / dt  solved by ism_solve to tol (see ism_proj_tol)
+ *   v = v* - dt grad dp,  p = p + dp.
+ *   u  device, ny*(nx+1) floats (x-faces);  v  device, (ny+1)*nx floats
+ *   (y-faces);  p  device, nx*ny floats.  dt > 0, nu >= 0.
+ * Returns the status of the pressure solve. */
+ism_status proj_step(ism_ctx *ctx, float *u, float *v, float *p, double dt, double nu);
+
+/* Pressure-solve controls used by proj_step (defaults tol 1e-8,
+ * max_cycles 100000, warm start off). */
+ism_status ism_proj_tol(ism_ctx *ctx, double tol, int max_cycles, int warm_start);
+
+/* Last pressure increment dp of proj_step: device, nx*ny doubles owned by
+ * the context (valid until the next call on it). */
+const double *ism_last_dp(const ism_ctx *ctx);
+
+/* ---------------- batched ensemble ----------------------------------------
+ * Solve n independent problems, each described by its own context (same
+ * precision, same stream as ctxs[0]); one set of launches advances every
+ * unfinished problem by one step per launch.
+ *   ctxs   host, n contexts.  rhs, p: host arrays of n device pointers.
+ *   cycles_out: host, n ints or NULL.  relres_out: host, n doubles or NULL.
+ * Returns ISM_OK if every problem converged, else the first failing status. */
+ism_status ism_solve_batched(int n, ism_ctx *const *ctxs, const double *const *rhs,
+                             double *const *p, double tol, int max_cycles,
+                             int *cycles_out, double *relres_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISM_H */

@@ -1,0 +1,863 @@
+// ism_core.cu -- setup, control kernels and solve drivers of the ISM library.
+//
+// The two-level cycle (Sec. 3.4, Fig. 2b; cycle of Sec. 4.3.1 restated with
+// an exact coarse solve):
+//   r = b - A_f p;  r_c = R r (m x m block sums);  e_c = A_c^+ r_c;
+//   p += P e_c (bilinear, Eq. 5);  nu red-black Gauss-Seidel sweeps;
+// repeated until ||b - A_f p|| <= tol ||b||.  Convergence is decided on the
+// device by one-CTA control kernels, so a chunk of cycles runs as one CUDA
+// graph with a single host read of the state per chunk.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ism_kernels.cuh"
+#include "ism_sweep32.cuh"
+
+// ================================================================ control
+
+__global__ void __launch_bounds__(256) k_ctl(IsmState *st, const double *partials, int nblk,
+                                             int nq, int mode)
+{
+    __shared__ double S[ISM_NQ];
+    if ((mode == CTL_FP64_AFTER || mode == CTL_OUTER_AFTER) && st->done) return;
+    if (mode == CTL_INNER && st->inner_done) return;
+    ctl_reduce(partials, nblk, nq, S);
+    if (threadIdx.x == 0) ctl_decide(st, S, mode);
+}
+
+// ================================================================ rhs preparation
+
+// partial sums of x (mode 0: sum x) or of (x - mean)^2 with y = x - mean (mode 1)
+__global__ void k_rhs_stats(const double *__restrict__ x, double *__restrict__ y, long long n,
+                            const IsmState *st, int mode, int sub_mean, double *partials)
+{
+    double s = 0.0;
+    const double mu = (mode == 1 && sub_mean) ? st->mean : 0.0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double v = x[i];
+        if (mode == 0) s += v;
+        else {
+            v -= mu;
+            y[i] = v;
+            s += v * v;
+        }
+    }
+    double v1[1] = {s};
+    block_partials<1>(v1, partials, gridDim.x, blockIdx.x);
+}
+
+// ================================================================ mixed-path outer kernels
+
+// FP64 refinement step.  UPDATE: p_out = p_in + e (e = inner iterate selected
+// by st->cur); then r = b - A_f p_out in FP64, r32 = (float) r, partials
+// (||r||^2, sum p_out).  Grid (ceil(nx/256), ny).
+template <bool UPDATE>
+__global__ void k_refine(const double *__restrict__ p_in, double *__restrict__ p_out,
+                         const float *e0, const float *e1, const double *__restrict__ b,
+                         float *__restrict__ r32, double *partials, int nx, int ny, int bcmask,
+                         const IsmState *st)
+{
+    const int j = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float *__restrict__ e = (UPDATE && st->cur) ? e1 : e0;
+    double r2 = 0.0, ps = 0.0;
+    if (i < nx) {
+        const size_t idx = (size_t)j * nx + i;
+        auto P = [&](size_t k) -> double {
+            double v = p_in[k];
+            if (UPDATE) v += (double)e[k];
+            return v;
+        };
+        const double pc = P(idx);
+        double s = 0.0;
+        if (i > 0) s += P(idx - 1);
+        if (i < nx - 1) s += P(idx + 1);
+        if (j > 0) s += P(idx - nx);
+        if (j < ny - 1) s += P(idx + nx);
+        const double r = b[idx] - (s - (double)diag_count(i, j, nx, ny, bcmask) * pc);
+        if (UPDATE) p_out[idx] = pc;
+        r32[idx] = (float)r;
+        r2 = r * r;
+        ps = pc;
+    }
+    double v[2] = {r2, ps};
+    block_partials<2>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// out = in - mean (mean of the final iterate when all faces are Neumann);
+// zeros when the right-hand side vanished.
+__global__ void k_finalize(const double *__restrict__ in, double *__restrict__ out, long long n,
+                           const IsmState *st, int sub_mean)
+{
+    const double mu = sub_mean ? st->mean : 0.0;
+    const bool zero = st->zero_rhs != 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = zero ? 0.0 : in[i] - mu;
+}
+
+// ================================================================ host: setup
+
+extern "C" const char *ism_status_str(ism_status s)
+{
+    switch (s) {
+    case ISM_OK: return "ok";
+    case ISM_ERR_ARG: return "invalid argument";
+    case ISM_ERR_NOT_CONVERGED: return "not converged";
+    case ISM_ERR_NONFINITE: return "non-finite value";
+    case ISM_ERR_CUDA: return "CUDA error";
+    case ISM_ERR_NOMEM: return "out of memory";
+    }
+    return "unknown status";
+}
+
+static void default_options(ism_options *o)
+{
+    o->nu = 8;
+    o->sweeps_per_pass = 4;
+    o->kind = ISM_COARSE_ISM;
+    o->max_outer = 50;
+    o->inner_max = 10000;
+    o->inner_tol = 1e-3;
+    o->floor_mult = 4.0;
+    o->check_every = 16;
+    o->use_graphs = 1;
+}
+
+static const double kPi = 3.14159265358979323846;
+
+// Eigenbasis of S = tridiag(1, 2, 1) of size n with end diagonals 3 (Neumann)
+// or 1 (Dirichlet-0): with the ghost x_{-1} = +-x_0 and x_n = +-x_{n-1},
+// (S x)_i = x_{i-1} + 2 x_i + x_{i+1} everywhere, so the cosine/sine modes
+// below are eigenvectors with eigenvalue 2 + 2 cos(theta):
+//   N-N: cos(theta (i+1/2)), theta = pi k / n          (DCT-II)
+//   D-D: sin(theta (i+1/2)), theta = pi (k+1) / n      (DST-II)
+//   N-D: cos(theta (i+1/2)), theta = pi (k+1/2) / n    (DCT-IV)
+//   D-N: sin(theta (i+1/2)), theta = pi (k+1/2) / n    (DST-IV)
+// Q[i*n + k] is component i of unit eigenvector k.
+static void s_eigen(int n, int lo_dir, int hi_dir, std::vector<double> &Q, std::vector<double> &lam)
+{
+    Q.assign((size_t)n * n, 0.0);
+    lam.assign(n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        double th;
+        bool use_sin = lo_dir != 0;
+        if (!lo_dir && !hi_dir) th = kPi * k / n;
+        else if (lo_dir && hi_dir) th = kPi * (k + 1) / n;
+        else th = kPi * (k + 0.5) / n;
+        lam[k] = 2.0 + 2.0 * cos(th);
+        double nrm = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double v = use_sin ? sin(th * (i + 0.5)) : cos(th * (i + 0.5));
+            Q[(size_t)i * n + k] = v;
+            nrm += v * v;
+        }
+        nrm = 1.0 / sqrt(nrm);
+        for (int i = 0; i < n; ++i) Q[(size_t)i * n + k] *= nrm;
+    }
+}
+
+struct EigenHost {
+    std::vector<double> Qx, Qy, lx, ly;
+};
+
+// Eigenvalues of A_c on (Qy x Qx): ISM A_c = 1/4 (S_y x S_x) - 4 I
+// (closed form of summing the Eq. 6-7 face fluxes), ACM A_c = m (T_y (+) T_x)
+// with T = S - 4 I, the five-point coarse operator of the summed equations.
+static ism_status upload_coarse(ism_ctx *ctx, const EigenHost &E)
+{
+    const int ncx = ctx->ncx, ncy = ctx->ncy;
+    std::vector<double> QxT((size_t)ncx * ncx), QyT((size_t)ncy * ncy), Minv((size_t)ncx * ncy);
+    for (int i = 0; i < ncx; ++i)
+        for (int k = 0; k < ncx; ++k) QxT[(size_t)k * ncx + i] = E.Qx[(size_t)i * ncx + k];
+    for (int i = 0; i < ncy; ++i)
+        for (int k = 0; k < ncy; ++k) QyT[(size_t)k * ncy + i] = E.Qy[(size_t)i * ncy + k];
+    for (int l = 0; l < ncy; ++l)
+        for (int k = 0; k < ncx; ++k) {
+            double mu = (ctx->opt.kind == ISM_COARSE_ACM)
+                            ? ctx->m * ((E.lx[k] - 4.0) + (E.ly[l] - 4.0))
+                            : 0.25 * E.lx[k] * E.ly[l] - 4.0;
+            Minv[(size_t)l * ncx + k] = fabs(mu) < 1e-10 ? 0.0 : 1.0 / mu;
+        }
+    auto up = [&](double *d64, float *d32, const std::vector<double> &h) -> ism_status {
+        std::vector<float> f(h.size());
+        for (size_t i = 0; i < h.size(); ++i) f[i] = (float)h[i];
+        ISM_CUDA_TRY(cudaMemcpy(d64, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+        ISM_CUDA_TRY(cudaMemcpy(d32, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+        return ISM_OK;
+    };
+    ism_status s;
+    if ((s = up(ctx->Qx64, ctx->Qx32, E.Qx)) != ISM_OK) return s;
+    if ((s = up(ctx->QxT64, ctx->QxT32, QxT)) != ISM_OK) return s;
+    if ((s = up(ctx->Qy64, ctx->Qy32, E.Qy)) != ISM_OK) return s;
+    if ((s = up(ctx->QyT64, ctx->QyT32, QyT)) != ISM_OK) return s;
+    return up(ctx->Minv64, ctx->Minv32, Minv);
+}
+
+static void free_graphs(ism_ctx *ctx)
+{
+    if (ctx->g_fp64) cudaGraphExecDestroy(ctx->g_fp64);
+    if (ctx->g_inner) cudaGraphExecDestroy(ctx->g_inner);
+    ctx->g_fp64 = ctx->g_inner = nullptr;
+}
+
+extern "C" void ism_destroy(ism_ctx *ctx)
+{
+    if (!ctx) return;
+    if (ctx->ws) cudaStreamSynchronize(ctx->ws);
+    if (ctx->ws2) cudaStreamSynchronize(ctx->ws2);
+    free_graphs(ctx);
+    void *bufs[] = {ctx->Qx64, ctx->QxT64, ctx->Qy64, ctx->QyT64, ctx->Minv64, ctx->Qx32,
+                    ctx->QxT32, ctx->Qy32, ctx->QyT32, ctx->Minv32, ctx->b64, ctx->p64[0],
+                    ctx->p64[1], ctx->e32[0], ctx->e32[1], ctx->r32, ctx->rc64, ctx->ec64,
+                    ctx->T64, ctx->rc32, ctx->ec32, ctx->T32, ctx->partials, ctx->st,
+                    ctx->st_k, ctx->us, ctx->vs, ctx->dp, ctx->rcpart, ctx->G32};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    for (int K = 0; K <= SMAXK; ++K)
+        for (int r = 0; r < 2; ++r)
+            if (ctx->plans[K][r].edge) cudaFree(ctx->plans[K][r].edge);
+    if (ctx->st_host) cudaFreeHost(ctx->st_host);
+    if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
+    if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    if (ctx->ws2) cudaStreamDestroy(ctx->ws2);
+    if (ctx->ws) cudaStreamDestroy(ctx->ws);
+    free(ctx);
+}
+
+static ism_status make_plans(ism_ctx *ctx);
+
+static EigenHost build_eigen(const ism_ctx *ctx)
+{
+    EigenHost E;
+    s_eigen(ctx->ncx, ctx->bc[0], ctx->bc[1], E.Qx, E.lx);
+    s_eigen(ctx->ncy, ctx->bc[2], ctx->bc[3], E.Qy, E.ly);
+    return E;
+}
+
+extern "C" ism_status ism_setup(int nx, int ny, double h, const int bc[4], int coarsen,
+                                ism_precision prec, void *stream, ism_ctx **out)
+{
+    if (!out || !bc) return ISM_ERR_ARG;
+    if (coarsen != 8 && coarsen != 16 && coarsen != 32) return ISM_ERR_ARG;
+    if (nx <= 0 || ny <= 0 || nx % coarsen || ny % coarsen) return ISM_ERR_ARG;
+    if ((long long)nx * ny > (1LL << 31) || nx > (1 << 20) || ny > (1 << 20)) return ISM_ERR_ARG;
+    if (nx / coarsen > 1024 || ny / coarsen > 1024) return ISM_ERR_ARG;
+    if (!(h > 0.0) || !isfinite(h)) return ISM_ERR_ARG;
+    for (int f = 0; f < 4; ++f)
+        if (bc[f] != ISM_BC_NEUMANN && bc[f] != ISM_BC_DIRICHLET0) return ISM_ERR_ARG;
+    if (prec != ISM_FP64 && prec != ISM_MIXED) return ISM_ERR_ARG;
+
+    ism_ctx *ctx = (ism_ctx *)calloc(1, sizeof(ism_ctx));
+    if (!ctx) return ISM_ERR_NOMEM;
+    ctx->nx = nx;
+    ctx->ny = ny;
+    ctx->m = coarsen;
+    ctx->ncx = nx / coarsen;
+    ctx->ncy = ny / coarsen;
+    ctx->n = (long long)nx * ny;
+    ctx->h = h;
+    ctx->bcmask = 0;
+    for (int f = 0; f < 4; ++f) {
+        ctx->bc[f] = bc[f];
+        if (bc[f]) ctx->bcmask |= 1 << f;
+    }
+    ctx->singular = ctx->bcmask == 0;
+    ctx->prec = prec;
+    ctx->user_stream = (cudaStream_t)stream;
+    default_options(&ctx->opt);
+    ctx->proj_tol = 1e-8;
+    ctx->proj_max_cycles = 100000;
+    ctx->conv_u = 1.0;
+
+    const size_t N = (size_t)ctx->n, nc = (size_t)ctx->ncx * ctx->ncy;
+    const int tiles = ((nx + sweep_tile_w(SMAXK, true) - 1) / sweep_tile_w(SMAXK, true)) *
+                      ((ny + sweep_tile_h(SMAXK, true) - 1) / sweep_tile_h(SMAXK, true));   // largest tile grid
+    ctx->max_blocks = std::max({(int)nc, tiles, ((nx + 255) / 256) * ny, 1024});
+
+#define ALLOC(ptr, bytes)                                                        \
+    do {                                                                         \
+        if (cudaMalloc((void **)&(ptr), (bytes)) != cudaSuccess) {               \
+            cudaGetLastError();                                                  \
+            ism_destroy(ctx);                                                    \
+            return ISM_ERR_NOMEM;                                                \
+        }                                                                        \
+    } while (0)
+    const size_t ncx2 = (size_t)ctx->ncx * ctx->ncx, ncy2 = (size_t)ctx->ncy * ctx->ncy;
+    ALLOC(ctx->Qx64, ncx2 * 8); ALLOC(ctx->QxT64, ncx2 * 8);
+    ALLOC(ctx->Qy64, ncy2 * 8); ALLOC(ctx->QyT64, ncy2 * 8);
+    ALLOC(ctx->Minv64, nc * 8);
+    ALLOC(ctx->Qx32, ncx2 * 4); ALLOC(ctx->QxT32, ncx2 * 4);
+    ALLOC(ctx->Qy32, ncy2 * 4); ALLOC(ctx->QyT32, ncy2 * 4);
+    ALLOC(ctx->Minv32, nc * 4);
+    ALLOC(ctx->b64, N * 8);
+    ALLOC(ctx->p64[0], N * 8);
+    ALLOC(ctx->rc64, nc * 8); ALLOC(ctx->ec64, nc * 8); ALLOC(ctx->T64, nc * 8);
+    ALLOC(ctx->rc32, nc * 4); ALLOC(ctx->ec32, nc * 4); ALLOC(ctx->T32, nc * 4);
+    ALLOC(ctx->rcpart, nc * 4 * 4);
+    ALLOC(ctx->G32, (size_t)ctx->ncy * nx * 4);
+    if (prec == ISM_MIXED) {
+        ALLOC(ctx->p64[1], N * 8);
+        ALLOC(ctx->e32[0], N * 4);
+        ALLOC(ctx->e32[1], N * 4);
+        ALLOC(ctx->r32, N * 4);
+    }
+    ALLOC(ctx->partials, (size_t)ISM_NQ * ctx->max_blocks * 8);
+    ALLOC(ctx->st, sizeof(IsmState));
+    ALLOC(ctx->st_k, sizeof(IsmState));
+#undef ALLOC
+    if (cudaMallocHost((void **)&ctx->st_host, sizeof(IsmState)) != cudaSuccess) {
+        cudaGetLastError();
+        ism_destroy(ctx);
+        return ISM_ERR_NOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->ws, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->ws2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        ism_destroy(ctx);
+        return ISM_ERR_CUDA;
+    }
+    if (cudaMemset(ctx->st, 0, sizeof(IsmState)) != cudaSuccess ||
+        cudaMemset(ctx->st_k, 0, sizeof(IsmState)) != cudaSuccess) {
+        ism_destroy(ctx);
+        return ISM_ERR_CUDA;
+    }
+    ism_status s = upload_coarse(ctx, build_eigen(ctx));
+    if (s != ISM_OK) {
+        ism_destroy(ctx);
+        return s;
+    }
+    // the fused sweep pass uses 80 KB of dynamic shared memory
+    const int smb = (int)sweep_smem_bytes();
+    cudaFuncSetAttribute(k_sweep32<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    if ((s = make_plans(ctx)) != ISM_OK) {
+        ism_destroy(ctx);
+        return s;
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        ism_destroy(ctx);
+        return ISM_ERR_CUDA;
+    }
+    *out = ctx;
+    return ISM_OK;
+}
+
+extern "C" ism_status ism_get_options(const ism_ctx *ctx, ism_options *opt)
+{
+    if (!ctx || !opt) return ISM_ERR_ARG;
+    *opt = ctx->opt;
+    return ISM_OK;
+}
+
+extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
+{
+    if (!ctx || !o) return ISM_ERR_ARG;
+    if (o->nu < 1 || o->nu > 256) return ISM_ERR_ARG;
+    if (o->sweeps_per_pass < 1 || o->sweeps_per_pass > SMAXK || o->nu % o->sweeps_per_pass) return ISM_ERR_ARG;
+    if (o->kind != ISM_COARSE_ISM && o->kind != ISM_COARSE_ACM) return ISM_ERR_ARG;
+    if (o->max_outer < 1 || o->inner_max < 1 || o->check_every < 1 || o->check_every > 4096) return ISM_ERR_ARG;
+    if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
+    const int kind_changed = o->kind != ctx->opt.kind;
+    cudaStreamSynchronize(ctx->ws);
+    ctx->opt = *o;
+    free_graphs(ctx);
+    if (kind_changed) return upload_coarse(ctx, build_eigen(ctx));
+    return ISM_OK;
+}
+
+ism_status ism_enter(ism_ctx *ctx)
+{
+    ISM_CUDA_TRY(cudaEventRecord(ctx->ev_in, ctx->user_stream));
+    ISM_CUDA_TRY(cudaStreamWaitEvent(ctx->ws, ctx->ev_in, 0));
+    return ISM_OK;
+}
+
+ism_status ism_leave(ism_ctx *ctx)
+{
+    ISM_CUDA_TRY(cudaEventRecord(ctx->ev_out, ctx->ws));
+    ISM_CUDA_TRY(cudaStreamWaitEvent(ctx->user_stream, ctx->ev_out, 0));
+    return ISM_OK;
+}
+
+// ================================================================ host: launch helpers
+
+static inline dim3 row_grid(int nx, int ny, int threads) { return dim3((nx + threads - 1) / threads, ny); }
+
+static inline int coarse_threads(int ncx) { return std::min(256, ((ncx + 31) / 32) * 32); }
+
+// e_c = A_c^+ r_c.  FUSED (single precision inside the cycle): r_c is read as
+// the sum of the 4 partial block sums and the x-interpolated rows G are made.
+template <typename T, bool FUSED>
+static ism_status launch_coarse(ism_ctx *ctx, const T *rc, T *ec, T *Tm, const int *skip)
+{
+    const T *Qx, *QxT, *Qy, *QyT, *Minv;
+    if (sizeof(T) == 8) {
+        Qx = (const T *)ctx->Qx64; QxT = (const T *)ctx->QxT64;
+        Qy = (const T *)ctx->Qy64; QyT = (const T *)ctx->QyT64; Minv = (const T *)ctx->Minv64;
+    } else {
+        Qx = (const T *)ctx->Qx32; QxT = (const T *)ctx->QxT32;
+        Qy = (const T *)ctx->Qy32; QyT = (const T *)ctx->QyT32; Minv = (const T *)ctx->Minv32;
+    }
+    const int th = 256;
+    const int JS = ctx->ncx >= th ? 1 : th / ctx->ncx;
+    const size_t sm = (size_t)(JS + 2) * ctx->ncx * sizeof(T);
+    k_coarse1<T, FUSED><<<ctx->ncy, th, sm, ctx->ws>>>(rc, QyT, Qx, Minv, Tm, ctx->ncx, ctx->ncy, skip);
+    ISM_LAUNCH_CHECK(ctx);
+    k_coarse2<T, FUSED><<<ctx->ncy, th, sm, ctx->ws>>>(
+        Tm, Qy, QxT, ec, ctx->ncx, ctx->ncy, skip, (T *)(FUSED ? (void *)ctx->G32 : nullptr), ctx->nx,
+        ctx->m, ctx->bcmask, ctx->opt.kind, (T *)(FUSED ? (void *)ctx->rcpart : nullptr));
+    ISM_LAUNCH_CHECK(ctx);
+    return ISM_OK;
+}
+
+template <typename T>
+static ism_status launch_resid(ism_ctx *ctx, const T *p, const T *b, T *rc, const int *skip,
+                               int ctl_mode = -1)
+{
+    const int th = std::min(256, ctx->m * ctx->m);
+    k_resid<T><<<dim3(ctx->ncx, ctx->ncy), th, 0, ctx->ws>>>(p, b, rc, ctx->partials, ctx->nx,
+                                                                ctx->ny, ctx->m, ctx->bcmask, skip,
+                                                                ctx->st, ctl_mode);
+    ISM_LAUNCH_CHECK(ctx);
+    return ISM_OK;
+}
+
+static ism_status launch_ctl(ism_ctx *ctx, IsmState *st, int nblk, int nq, int mode)
+{
+    k_ctl<<<1, 256, 0, ctx->ws>>>(st, ctx->partials, nblk, nq, mode);
+    ISM_LAUNCH_CHECK(ctx);
+    return ISM_OK;
+}
+
+template <typename T>
+static ism_status launch_sweeps(ism_ctx *ctx, T *p, const T *b, int sweeps, const int *skip)
+{
+    const int hx = (ctx->nx + 1) / 2;
+    const dim3 g = row_grid(hx, ctx->ny, 128);
+    for (int s = 0; s < sweeps; ++s)
+        for (int col = 0; col < 2; ++col) {
+            k_rbgs_colour<T><<<g, 128, 0, ctx->ws>>>(p, b, ctx->nx, ctx->ny, ctx->bcmask, col, skip);
+            ISM_LAUNCH_CHECK(ctx);
+        }
+    return ISM_OK;
+}
+
+// Tile grid of a pass and its split into an interior rectangle (regions
+// strictly inside the domain) and the list of edge tiles.
+using SweepPlan = ism_ctx::SweepPlan;
+
+static SweepPlan &sweep_plan(ism_ctx *ctx, int K, bool resid)
+{
+    return ctx->plans[K][resid ? 1 : 0];
+}
+
+static ism_status make_plans(ism_ctx *ctx)
+{
+    for (int K = 0; K <= SMAXK; ++K)
+        for (int r = 0; r < 2; ++r) {
+            SweepPlan &P = ctx->plans[K][r];
+            const int tw = sweep_tile_w(K, r), th = sweep_tile_h(K, r);
+            const int Hc = sweep_halo_cols(K, r), H = sweep_halo(K, r);
+            P.gx = (ctx->nx + tw - 1) / tw;
+            P.gy = (ctx->ny + th - 1) / th;
+            // interior: region [bx*tw - Hc, +SRW) inside [1, nx-2], same in y
+            auto lo = [](int t, int h) { int b = 0; while (b * t - h < 1) ++b; return b; };
+            P.ix0 = lo(tw, Hc);
+            P.iy0 = lo(th, H);
+            P.ix1 = P.ix0; while (P.ix1 < P.gx && P.ix1 * tw - Hc + SRW <= ctx->nx - 1) ++P.ix1;
+            P.iy1 = P.iy0; while (P.iy1 < P.gy && P.iy1 * th - H + SRH <= ctx->ny - 1) ++P.iy1;
+            if (P.ix1 <= P.ix0 || P.iy1 <= P.iy0) { P.ix1 = P.ix0; P.iy1 = P.iy0; }
+            std::vector<int2> e;
+            for (int by = 0; by < P.gy; ++by)
+                for (int bx = 0; bx < P.gx; ++bx)
+                    if (!(bx >= P.ix0 && bx < P.ix1 && by >= P.iy0 && by < P.iy1)) e.push_back(make_int2(bx, by));
+            P.nedge = (int)e.size();
+            if (cudaMalloc((void **)&P.edge, e.size() * sizeof(int2)) != cudaSuccess) {
+                cudaGetLastError();
+                return ISM_ERR_NOMEM;
+            }
+            ISM_CUDA_TRY(cudaMemcpy(P.edge, e.data(), e.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        }
+    return ISM_OK;
+}
+
+static inline int sweep_nblk(ism_ctx *ctx, int K, bool resid)
+{
+    const SweepPlan &P = sweep_plan(ctx, K, resid);
+    return P.gx * P.gy;
+}
+
+// Interior and edge launches of one pass run concurrently: the edge launch
+// goes to a forked stream joined back before the next kernel.
+template <bool PR, bool RE>
+static ism_status launch_sweep_pair(ism_ctx *ctx, const SweepArgs &a, const SweepPlan &P)
+{
+    const size_t sm = sweep_smem_bytes();
+    const bool both = P.ix1 > P.ix0 && P.nedge > 0;
+    if (both) {
+        ISM_CUDA_TRY(cudaEventRecord(ctx->ev_fork, ctx->ws));
+        ISM_CUDA_TRY(cudaStreamWaitEvent(ctx->ws2, ctx->ev_fork, 0));
+        k_sweep32<PR, RE, true><<<P.nedge, STHREADS, sm, ctx->ws2>>>(a);
+        k_sweep32<PR, RE, false><<<dim3(P.ix1 - P.ix0, P.iy1 - P.iy0), STHREADS, sm, ctx->ws>>>(a);
+        ISM_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->ws2));
+        ISM_CUDA_TRY(cudaStreamWaitEvent(ctx->ws, ctx->ev_join, 0));
+    } else if (P.ix1 > P.ix0) {
+        k_sweep32<PR, RE, false><<<dim3(P.ix1 - P.ix0, P.iy1 - P.iy0), STHREADS, sm, ctx->ws>>>(a);
+    } else {
+        k_sweep32<PR, RE, true><<<P.nedge, STHREADS, sm, ctx->ws>>>(a);
+    }
+    return ISM_OK;
+}
+
+static ism_status launch_sweep32(ism_ctx *ctx, SweepArgs a, bool prolong, bool resid)
+{
+    const SweepPlan &P = sweep_plan(ctx, a.K, resid);
+    a.H = sweep_halo(a.K, resid);
+    a.Hc = sweep_halo_cols(a.K, resid);
+    a.TW = sweep_tile_w(a.K, resid);
+    a.TH = sweep_tile_h(a.K, resid);
+    a.gx = P.gx; a.gy = P.gy; a.ix0 = P.ix0; a.iy0 = P.iy0; a.edge_tiles = P.edge;
+    if (!resid) a.ctl_mode = -1;
+    ism_status st;
+    if (prolong && resid) st = launch_sweep_pair<true, true>(ctx, a, P);
+    else if (prolong) st = launch_sweep_pair<true, false>(ctx, a, P);
+    else if (resid) st = launch_sweep_pair<false, true>(ctx, a, P);
+    else st = launch_sweep_pair<false, false>(ctx, a, P);
+    if (st != ISM_OK) return st;
+    ctx->launches += (P.ix1 > P.ix0) + (P.nedge > 0);
+    if (cudaGetLastError() != cudaSuccess) return ISM_ERR_CUDA;
+    return ISM_OK;
+}
+
+#define TRY(x)                                                                   \
+    do {                                                                         \
+        ism_status _s = (x);                                                     \
+        if (_s != ISM_OK) return _s;                                             \
+    } while (0)
+
+// ================================================================ host: cycles
+
+// One FP64 cycle; every kernel returns at once when st->done is set.
+static ism_status fp64_cycle(ism_ctx *ctx)
+{
+    const int *skip = &ctx->st->done;
+    TRY((launch_coarse<double, false>(ctx, ctx->rc64, ctx->ec64, ctx->T64, skip)));
+    k_prolong<double><<<row_grid(ctx->nx, ctx->ny, 128), 128, 0, ctx->ws>>>(
+        ctx->p64[0], ctx->ec64, ctx->nx, ctx->ny, ctx->m, ctx->ncx, ctx->ncy, ctx->bcmask,
+        ctx->opt.kind, ctx->st, ctx->singular, skip);
+    ISM_LAUNCH_CHECK(ctx);
+    TRY(launch_sweeps<double>(ctx, ctx->p64[0], ctx->b64, ctx->opt.nu, skip));
+    return launch_resid<double>(ctx, ctx->p64[0], ctx->b64, ctx->rc64, skip, CTL_FP64_AFTER);
+}
+
+static SweepArgs inner_args(ism_ctx *ctx, IsmState *st, float *e0, float *e1, const float *b,
+                            const int *skip, const int *curp)
+{
+    SweepArgs a;
+    a.e0 = e0; a.e1 = e1; a.b = b; a.G = ctx->G32; a.rcpart = ctx->rcpart;
+    a.partials = ctx->partials; a.st = st; a.skip = skip; a.curp = curp;
+    a.nx = ctx->nx; a.ny = ctx->ny; a.m = ctx->m; a.ncx = ctx->ncx; a.ncy = ctx->ncy;
+    a.lm = ctx->m == 8 ? 3 : ctx->m == 16 ? 4 : 5;
+    a.bcmask = ctx->bcmask; a.kind = ctx->opt.kind; a.K = ctx->opt.sweeps_per_pass;
+    a.q = 0; a.use_mean = ctx->singular; a.ctl_mode = -1;
+    a.H = a.Hc = a.TW = a.TH = 0;
+    return a;
+}
+
+// One single-precision inner cycle; kernels return at once when st->inner_done:
+// coarse solve (from the partial block sums of the previous pass), then nu/K
+// fused passes (the first adds the prolongation, the last computes the
+// residual and its restriction), then the control kernel.
+static ism_status inner_cycle(ism_ctx *ctx)
+{
+    const int *skip = &ctx->st->inner_done;
+    TRY((launch_coarse<float, true>(ctx, ctx->rcpart, ctx->ec32, ctx->T32, skip)));
+    const int npass = ctx->opt.nu / ctx->opt.sweeps_per_pass;
+    SweepArgs a = inner_args(ctx, ctx->st, ctx->e32[0], ctx->e32[1], ctx->r32, skip, &ctx->st->cur);
+    a.ctl_mode = CTL_INNER;
+    for (int q = 0; q < npass; ++q) {
+        a.q = q;
+        TRY(launch_sweep32(ctx, a, q == 0, q == npass - 1));
+    }
+    return ISM_OK;
+}
+
+// Run chunks of `check_every` cycles (as a CUDA graph when enabled) until the
+// flag at `flag_off` in the state becomes nonzero.
+static ism_status run_chunks(ism_ctx *ctx, bool inner, int max_chunks)
+{
+    const int C = ctx->opt.check_every;
+    cudaGraphExec_t *gx = inner ? &ctx->g_inner : &ctx->g_fp64;
+    int *glen = inner ? &ctx->g_inner_len : &ctx->g_fp64_len;
+    for (int it = 0; it < max_chunks; ++it) {
+        if (ctx->opt.use_graphs) {
+            if (!*gx) {
+                cudaGraph_t g;
+                const long long l0 = ctx->launches;
+                ISM_CUDA_TRY(cudaStreamBeginCapture(ctx->ws, cudaStreamCaptureModeThreadLocal));
+                ism_status s = ISM_OK;
+                for (int c = 0; c < C && s == ISM_OK; ++c) s = inner ? inner_cycle(ctx) : fp64_cycle(ctx);
+                cudaError_t e = cudaStreamEndCapture(ctx->ws, &g);
+                if (s != ISM_OK || e != cudaSuccess) return s != ISM_OK ? s : ISM_ERR_CUDA;
+                e = cudaGraphInstantiate(gx, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) { *gx = nullptr; return ISM_ERR_CUDA; }
+                *glen = (int)(ctx->launches - l0);
+                ctx->launches = l0;
+            }
+            ISM_CUDA_TRY(cudaGraphLaunch(*gx, ctx->ws));
+            ctx->launches += *glen;
+        } else {
+            for (int c = 0; c < C; ++c) TRY(inner ? inner_cycle(ctx) : fp64_cycle(ctx));
+        }
+        ISM_CUDA_TRY(cudaMemcpyAsync(ctx->st_host, ctx->st, offsetof(IsmState, hist),
+                                     cudaMemcpyDeviceToHost, ctx->ws));
+        ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+        if (inner ? (ctx->st_host->inner_done || ctx->st_host->done) : ctx->st_host->done) return ISM_OK;
+    }
+    return ISM_OK;
+}
+
+// ================================================================ host: solve
+
+static void init_state(ism_ctx *ctx, IsmState *h, double tol, int max_cycles)
+{
+    memset(h, 0, offsetof(IsmState, hist));
+    h->max_cycles = max_cycles;
+    h->max_outer = ctx->opt.max_outer;
+    h->inner_max = ctx->opt.inner_max;
+    h->npass = ctx->opt.nu / ctx->opt.sweeps_per_pass;
+    h->tol = tol;
+    h->inner_tol = ctx->opt.inner_tol;
+    h->floor_mult = ctx->opt.floor_mult;
+    h->inv_n = 1.0 / (double)ctx->n;
+}
+
+ism_status ism_prepare_rhs(ism_ctx *ctx, const double *rhs)
+{
+    const int G = 4 * 152;
+    k_rhs_stats<<<G, 256, 0, ctx->ws>>>(rhs, nullptr, ctx->n, ctx->st, 0, 0, ctx->partials);
+    ISM_LAUNCH_CHECK(ctx);
+    TRY(launch_ctl(ctx, ctx->st, G, 1, CTL_RHS_MEAN));
+    k_rhs_stats<<<G, 256, 0, ctx->ws>>>(rhs, ctx->b64, ctx->n, ctx->st, 1, ctx->singular, ctx->partials);
+    ISM_LAUNCH_CHECK(ctx);
+    return launch_ctl(ctx, ctx->st, G, 1, CTL_RHS_NORM);
+}
+
+static ism_status read_state(ism_ctx *ctx)
+{
+    ISM_CUDA_TRY(cudaMemcpyAsync(ctx->st_host, ctx->st, offsetof(IsmState, hist),
+                                 cudaMemcpyDeviceToHost, ctx->ws));
+    ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+    return ISM_OK;
+}
+
+static ism_status solve_fp64(ism_ctx *ctx)
+{
+    TRY(launch_resid<double>(ctx, ctx->p64[0], ctx->b64, ctx->rc64, nullptr, CTL_FP64_INIT));
+    TRY(read_state(ctx));
+    const int C = ctx->opt.check_every;
+    const int max_chunks = ctx->st_host->max_cycles / C + 2;
+    if (!ctx->st_host->done) TRY(run_chunks(ctx, false, max_chunks));
+    k_finalize<<<4 * 152, 256, 0, ctx->ws>>>(ctx->p64[0], ctx->p64[0], ctx->n, ctx->st, ctx->singular);
+    ISM_LAUNCH_CHECK(ctx);
+    return read_state(ctx);
+}
+
+static ism_status solve_mixed(ism_ctx *ctx)
+{
+    const dim3 rg = row_grid(ctx->nx, ctx->ny, 256);
+    const int nrb = rg.x * rg.y;
+    int c64 = 0;
+    k_refine<false><<<rg, 256, 0, ctx->ws>>>(ctx->p64[0], nullptr, ctx->e32[0], ctx->e32[1],
+                                             ctx->b64, ctx->r32, ctx->partials, ctx->nx, ctx->ny,
+                                             ctx->bcmask, ctx->st);
+    ISM_LAUNCH_CHECK(ctx);
+    TRY(launch_ctl(ctx, ctx->st, nrb, 2, CTL_OUTER_INIT));
+    const int C = ctx->opt.check_every;
+    for (;;) {
+        TRY(read_state(ctx));
+        if (ctx->st_host->done) break;
+        // inner solve of A e = r32 from e = 0
+        ISM_CUDA_TRY(cudaMemsetAsync(ctx->e32[0], 0, (size_t)ctx->n * sizeof(float), ctx->ws));
+        ISM_CUDA_TRY(cudaMemsetAsync(ctx->rcpart, 0, (size_t)ctx->ncx * ctx->ncy * 16, ctx->ws));
+        {   // restriction of r (the residual of e = 0): a pass with no sweeps
+            SweepArgs a = inner_args(ctx, ctx->st, ctx->e32[0], ctx->e32[1], ctx->r32, nullptr, nullptr);
+            a.K = 0;
+            TRY(launch_sweep32(ctx, a, false, true));
+        }
+        const int max_chunks = std::min(ctx->opt.inner_max, ctx->st_host->max_cycles) / C + 2;
+        TRY(run_chunks(ctx, true, max_chunks));
+        // p <- p + e, r = b - A p (FP64)
+        k_refine<true><<<rg, 256, 0, ctx->ws>>>(ctx->p64[c64], ctx->p64[c64 ^ 1], ctx->e32[0],
+                                                ctx->e32[1], ctx->b64, ctx->r32, ctx->partials,
+                                                ctx->nx, ctx->ny, ctx->bcmask, ctx->st);
+        ISM_LAUNCH_CHECK(ctx);
+        c64 ^= 1;
+        TRY(launch_ctl(ctx, ctx->st, nrb, 2, CTL_OUTER_AFTER));
+    }
+    k_finalize<<<4 * 152, 256, 0, ctx->ws>>>(ctx->p64[c64], ctx->p64[0], ctx->n, ctx->st, ctx->singular);
+    ISM_LAUNCH_CHECK(ctx);
+    return read_state(ctx);
+}
+
+ism_status ism_solve_internal(ism_ctx *ctx, double tol, int max_cycles)
+{
+    // keep rhs-preparation results (bnorm, zero_rhs, status) and reset the rest
+    TRY(read_state(ctx));
+    IsmState h = *ctx->st_host;
+    const double bn = h.bnorm;
+    const int zr = h.zero_rhs, stt = h.status, dn = h.done;
+    init_state(ctx, &h, tol, max_cycles);
+    h.bnorm = bn;
+    h.zero_rhs = zr;
+    h.status = stt;
+    h.done = dn;
+    ISM_CUDA_TRY(cudaMemcpyAsync(ctx->st, &h, offsetof(IsmState, hist), cudaMemcpyHostToDevice, ctx->ws));
+    if (dn) {                      // right-hand side already rejected (non-finite)
+        ctx->last_cycles = ctx->last_outer = 0;
+        ctx->last_relres = NAN;
+        ctx->last_status = stt;
+        ctx->last_nhist = 0;
+        return (ism_status)stt;
+    }
+    ism_status s = ctx->prec == ISM_FP64 ? solve_fp64(ctx) : solve_mixed(ctx);
+    if (s != ISM_OK) return s;
+    const IsmState *hs = ctx->st_host;
+    ctx->last_cycles = hs->cycles;
+    ctx->last_outer = hs->outer;
+    ctx->last_relres = hs->relres;
+    ctx->last_status = hs->status;
+    ctx->last_nhist = std::min(ISM_HMAX, (ctx->prec == ISM_FP64 ? hs->cycles : hs->outer) + 1);
+    return (ism_status)hs->status;
+}
+
+extern "C" ism_status ism_solve(ism_ctx *ctx, const double *rhs, double *p, double tol,
+                                int max_cycles, int *cycles_out, double *relres_out)
+{
+    if (!ctx || !rhs || !p || !(tol > 0.0) || max_cycles < 0) return ISM_ERR_ARG;
+    TRY(ism_enter(ctx));
+    // reset the state, then prepare the rhs
+    IsmState h;
+    memset(&h, 0, offsetof(IsmState, hist));
+    h.inv_n = 1.0 / (double)ctx->n;
+    ISM_CUDA_TRY(cudaMemcpyAsync(ctx->st, &h, offsetof(IsmState, hist), cudaMemcpyHostToDevice, ctx->ws));
+    TRY(ism_prepare_rhs(ctx, rhs));
+    ISM_CUDA_TRY(cudaMemcpyAsync(ctx->p64[0], p, (size_t)ctx->n * 8, cudaMemcpyDeviceToDevice, ctx->ws));
+    ism_status s = ism_solve_internal(ctx, tol, max_cycles);
+    if (s == ISM_OK || s == ISM_ERR_NOT_CONVERGED || s == ISM_ERR_NONFINITE) {
+        ISM_CUDA_TRY(cudaMemcpyAsync(p, ctx->p64[0], (size_t)ctx->n * 8, cudaMemcpyDeviceToDevice, ctx->ws));
+    }
+    ism_status s2 = ism_leave(ctx);
+    ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+    if (cycles_out) *cycles_out = ctx->last_cycles;
+    if (relres_out) *relres_out = ctx->last_relres;
+    return s != ISM_OK ? s : s2;
+}
+
+extern "C" int ism_last_history(const ism_ctx *ctx, double *hist, int cap)
+{
+    if (!ctx || !hist || cap <= 0) return 0;
+    const int n = std::min(cap, ctx->last_nhist);
+    if (cudaMemcpy(hist, ctx->st->hist, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+extern "C" ism_status ism_last_counts(const ism_ctx *ctx, int *outer, int *cycles, long long *launches)
+{
+    if (!ctx) return ISM_ERR_ARG;
+    if (outer) *outer = ctx->last_outer;
+    if (cycles) *cycles = ctx->last_cycles;
+    if (launches) *launches = ctx->launches;
+    return ISM_OK;
+}
+
+// ================================================================ kernel-level entry points
+
+extern "C" ism_status ism_smooth(ism_ctx *ctx, void *p, const void *b, int sweeps)
+{
+    if (!ctx || !p || !b || sweeps < 0) return ISM_ERR_ARG;
+    if (sweeps == 0) return ISM_OK;
+    TRY(ism_enter(ctx));
+    if (ctx->prec == ISM_FP64) {
+        TRY(launch_sweeps<double>(ctx, (double *)p, (const double *)b, sweeps, nullptr));
+    } else {
+        // fused passes of up to K sweeps, ping-pong between p and e32[1]
+        float *buf[2] = {(float *)p, ctx->e32[1]};
+        SweepArgs a = inner_args(ctx, ctx->st_k, buf[0], buf[1], (const float *)b, nullptr, nullptr);
+        a.use_mean = 0;
+        int cur = 0, left = sweeps;
+        while (left > 0) {
+            a.K = std::min(left, SMAXK);
+            a.q = cur;
+            TRY(launch_sweep32(ctx, a, false, false));
+            cur ^= 1;
+            left -= a.K;
+        }
+        if (cur) ISM_CUDA_TRY(cudaMemcpyAsync(p, buf[1], (size_t)ctx->n * 4, cudaMemcpyDeviceToDevice, ctx->ws));
+    }
+    return ism_leave(ctx);
+}
+
+extern "C" ism_status ism_residual_restrict(ism_ctx *ctx, const void *p, const void *b, void *rc,
+                                            double *norms)
+{
+    if (!ctx || !p || !b || !rc) return ISM_ERR_ARG;
+    TRY(ism_enter(ctx));
+    if (ctx->prec == ISM_FP64) TRY(launch_resid<double>(ctx, (const double *)p, (const double *)b, (double *)rc, nullptr));
+    else TRY(launch_resid<float>(ctx, (const float *)p, (const float *)b, (float *)rc, nullptr));
+    if (norms) {
+        std::vector<double> part((size_t)3 * ctx->ncx * ctx->ncy);
+        ISM_CUDA_TRY(cudaMemcpyAsync(part.data(), ctx->partials, part.size() * 8, cudaMemcpyDeviceToHost, ctx->ws));
+        ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+        const int nb = ctx->ncx * ctx->ncy;
+        double r2 = 0, ps = 0;
+        for (int k = 0; k < nb; ++k) { r2 += part[k]; ps += part[nb + k]; }
+        norms[0] = sqrt(r2);
+        norms[1] = ps;
+    }
+    return ism_leave(ctx);
+}
+
+extern "C" ism_status ism_coarse_solve(ism_ctx *ctx, const void *rc, void *ec)
+{
+    if (!ctx || !rc || !ec) return ISM_ERR_ARG;
+    TRY(ism_enter(ctx));
+    if (ctx->prec == ISM_FP64) TRY((launch_coarse<double, false>(ctx, (const double *)rc, (double *)ec, ctx->T64, nullptr)));
+    else TRY((launch_coarse<float, false>(ctx, (const float *)rc, (float *)ec, ctx->T32, nullptr)));
+    return ism_leave(ctx);
+}
+
+extern "C" ism_status ism_prolong_add(ism_ctx *ctx, const void *ec, void *p)
+{
+    if (!ctx || !ec || !p) return ISM_ERR_ARG;
+    TRY(ism_enter(ctx));
+    const dim3 g = row_grid(ctx->nx, ctx->ny, 128);
+    if (ctx->prec == ISM_FP64)
+        k_prolong<double><<<g, 128, 0, ctx->ws>>>((double *)p, (const double *)ec, ctx->nx, ctx->ny, ctx->m,
+                                                  ctx->ncx, ctx->ncy, ctx->bcmask, ctx->opt.kind, nullptr, 0, nullptr);
+    else
+        k_prolong<float><<<g, 128, 0, ctx->ws>>>((float *)p, (const float *)ec, ctx->nx, ctx->ny, ctx->m,
+                                                 ctx->ncx, ctx->ncy, ctx->bcmask, ctx->opt.kind, nullptr, 0, nullptr);
+    ISM_LAUNCH_CHECK(ctx);
+    return ism_leave(ctx);
+}

@@ -1,0 +1,121 @@
+// ism_internal.cuh -- shared declarations of the ISM library (not installed).
+//
+// Layout of everything the library owns on the device, the control block
+// that the kernels use to decide convergence without host round trips, and
+// the launch helpers shared by the solver, the projection step and the
+// batched ensemble.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ism.h"
+
+#define ISM_HMAX 4096          // residual-history entries kept on the device
+#define ISM_NQ 4               // partial sums per CTA (q-major)
+
+// Device control block.  Written by the one-CTA control kernels, read by
+// every cycle kernel (which returns at once when its phase is finished).
+struct IsmState {
+    int done;          // FP64 path / outer refinement finished
+    int status;        // ism_status of the finished solve
+    int cycles;        // FP64: coarse corrections; mixed: single-precision cycles (all outer iterations)
+    int outer;         // mixed: refinement iterations applied
+    int inner_done;    // mixed: current inner solve finished
+    int inner_cycles;  // mixed: cycles in the current inner solve
+    int cur;           // mixed: which ping-pong buffer holds the inner iterate
+    int zero_rhs;      // ||b|| == 0: the solution is p = 0
+    int max_cycles, max_outer, inner_max, npass;
+    double tol, inner_tol, floor_mult, inv_n;
+    double bnorm;      // ||b - mean(b)||_2
+    double relres;     // latest relative residual (FP64 measure)
+    double mean;       // mean to subtract from the iterate (all-Neumann), FP64 path / outer p
+    double mean_e;     // mixed: mean of the inner iterate
+    double r32norm;    // mixed: ||r|| of the current inner right-hand side
+    double rin, enorm; // mixed: latest inner residual and iterate norms
+    unsigned int ticket; // CTAs finished in the current fused-control kernel
+    double hist[ISM_HMAX];
+};
+
+struct ism_ctx {
+    int nx, ny, m, ncx, ncy;
+    long long n;               // nx * ny
+    double h;
+    int bc[4];
+    int bcmask;                // bit f set: face f is Dirichlet-0
+    int singular;              // all faces Neumann
+    int prec;
+    ism_options opt;
+    cudaStream_t user_stream;  // ordering stream given by the caller
+    cudaStream_t ws;           // private work stream (graph capture needs a non-legacy stream)
+    cudaStream_t ws2;          // forked stream for concurrent launches within a step
+    cudaEvent_t ev_in, ev_out, ev_fork, ev_join;
+
+    // coarse level: separable eigenbases of A_c = (Qy x Qx) diag(mu) (Qy x Qx)^T
+    double *Qx64, *QxT64, *Qy64, *QyT64, *Minv64;
+    float *Qx32, *QxT32, *Qy32, *QyT32, *Minv32;
+
+    // work buffers
+    double *b64;               // right-hand side with the mean removed
+    double *p64[2];            // FP64 iterate (ping-pong for the mixed refinement update)
+    float *e32[2];             // mixed: single-precision inner iterate (ping-pong)
+    float *r32;                // mixed: inner right-hand side
+    double *rc64, *ec64, *T64; // coarse residual, correction, intermediate
+    float *rc32, *ec32, *T32;
+    float *rcpart;             // 4 partial block sums per coarse cell (fused restriction)
+    float *G32;                // x-interpolated coarse correction rows, ncy x nx
+    double *partials;          // ISM_NQ * max_blocks
+    int max_blocks;
+    IsmState *st;              // device control block
+    IsmState *st_k;            // device control block for kernel-level entry points
+    IsmState *st_host;         // pinned host copy (selected fields are read back)
+
+    // tile plans of the fused sweep pass, per (sweeps K, residual fused)
+    struct SweepPlan { int gx, gy, ix0, ix1, iy0, iy1, nedge; int2 *edge; } plans[9][2];
+
+    // CUDA graphs of a chunk of cycles
+    cudaGraphExec_t g_fp64, g_inner;
+    int g_fp64_len, g_inner_len;
+
+    // last solve
+    int last_cycles, last_outer, last_status, last_nhist;
+    double last_relres;
+    long long launches;
+
+    // projection step
+    int vel_bc[4];
+    double wall_u[4];
+    const float *u_in;
+    double conv_u;
+    int flow_set;
+    float *us, *vs;            // predicted velocities
+    double *dp;                // pressure increment
+    double proj_tol;
+    int proj_max_cycles, proj_warm;
+};
+
+// ------------------------------------------------------------------ helpers
+
+#define ISM_CUDA_TRY(call)                                                    \
+    do {                                                                      \
+        cudaError_t _e = (call);                                              \
+        if (_e != cudaSuccess) return ISM_ERR_CUDA;                           \
+    } while (0)
+
+#define ISM_LAUNCH_CHECK(ctx)                                                 \
+    do {                                                                      \
+        (ctx)->launches++;                                                    \
+        if (cudaGetLastError() != cudaSuccess) return ISM_ERR_CUDA;           \
+    } while (0)
+
+// Order ctx->ws after the caller's stream, and the caller's stream after ws.
+ism_status ism_enter(ism_ctx *ctx);
+ism_status ism_leave(ism_ctx *ctx);
+
+// Solve on internal buffers: b64 holds the right-hand side (mean removed),
+// p64[0] the initial guess; on return p64[0] holds the solution.
+ism_status ism_solve_internal(ism_ctx *ctx, double tol, int max_cycles);
+// Copy user rhs into b64 (removing the mean when singular) and compute ||b||.
+ism_status ism_prepare_rhs(ism_ctx *ctx, const double *rhs);
+
+// Projection-step kernels (ism_proj.cu) need the residual solver above.

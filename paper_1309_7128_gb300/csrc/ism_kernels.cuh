@@ -1,0 +1,408 @@
+// ism_kernels.cuh -- device kernels of the ISM solve (included by ism_core.cu
+// and ism_batched.cu; everything here is internal).
+//
+// Fine-grid conventions: row-major (i fastest), face order W, E, S, N,
+// bcmask bit f set when face f is Dirichlet-0.  The five-point flux sum is
+//   (A_f p)_c = sum_nb p_nb - d_c p_c,
+//   d_c = (#in-domain neighbours) + 2 (#Dirichlet-0 faces of the cell),
+// so the Gauss-Seidel point update is p_c = (sum_nb p_nb - b_c) / d_c.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ism_internal.cuh"
+
+#define FULLMASK 0xffffffffu
+
+// 1/d for d = 0..8 (d = 4 for interior cells, 2..8 on the boundary)
+__constant__ double c_invd64[9] = {0.0, 1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4,
+                                   1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8};
+__constant__ float c_invd32[9] = {0.0f, 1.0f, 1.0f / 2, 1.0f / 3, 1.0f / 4,
+                                  1.0f / 5, 1.0f / 6, 1.0f / 7, 1.0f / 8};
+
+template <typename T> __device__ __forceinline__ T inv_diag(int d);
+template <> __device__ __forceinline__ double inv_diag<double>(int d) { return c_invd64[d]; }
+template <> __device__ __forceinline__ float inv_diag<float>(int d) { return c_invd32[d]; }
+
+// d_c: each boundary face of the cell removes its neighbour (-1) and, when
+// Dirichlet-0, adds the ghost's 2 p_c (+2): net +1 (Dirichlet) or -1 (Neumann).
+__device__ __forceinline__ int diag_count(int x, int y, int nx, int ny, int bcmask)
+{
+    int d = 4;
+    if (x == 0) d += (bcmask & 1) ? 1 : -1;
+    if (x == nx - 1) d += (bcmask & 2) ? 1 : -1;
+    if (y == 0) d += (bcmask & 4) ? 1 : -1;
+    if (y == ny - 1) d += (bcmask & 8) ? 1 : -1;
+    return d;
+}
+
+// ----------------------------------------------------------------- reductions
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULLMASK, v, o);
+    return v;
+}
+
+// Deterministic block reduction of NQ doubles; thread 0 of the block writes
+// partials[q * nblk + bid].  blockDim.x must be a multiple of 32, <= 1024.
+template <int NQ>
+__device__ __forceinline__ void block_partials(double (&v)[NQ], double *partials,
+                                               int nblk, int bid)
+{
+    __shared__ double red[NQ][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) v[q] = warp_sum(v[q]);
+    __syncthreads();   // red[] may still be read by a previous call
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) red[q][w] = v[q];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            double t = lane < nw ? red[q][lane] : 0.0;
+            t = warp_sum(t);
+            if (lane == 0) partials[(size_t)q * nblk + bid] = t;
+        }
+    }
+}
+
+// ----------------------------------------------------------------- convergence control
+
+enum CtlMode {
+    CTL_RHS_MEAN = 0,   // S0 = sum b                  -> st->mean
+    CTL_RHS_NORM = 1,   // S0 = ||b - mean||^2          -> bnorm, zero_rhs, status
+    CTL_FP64_INIT = 2,  // S0 = ||r||^2, S1 = sum p    -> hist[0], done?
+    CTL_FP64_AFTER = 3, // same after one cycle         -> cycles++, hist, done?
+    CTL_OUTER_INIT = 4, // S0 = ||r64||^2, S1 = sum p   -> hist[0], done?, inner reset
+    CTL_OUTER_AFTER = 5,
+    CTL_INNER = 6       // S0 = ||r_in||^2, S1 = sum e, S2 = ||e||^2
+};
+
+// Fixed-order reduction of nq partial-sum columns (q-major, nblk entries
+// each) by one CTA (blockDim a multiple of 32); S[q] valid after return.
+__device__ __forceinline__ void ctl_reduce(const double *partials, int nblk, int nq, double *S)
+{
+    __shared__ double wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+    for (int q = 0; q < nq; ++q) {
+        double s = 0.0;
+        for (int b = t; b < nblk; b += blockDim.x) s += __ldcg(partials + (size_t)q * nblk + b);
+        s = warp_sum(s);
+        if (lane == 0) wsum[w] = s;
+        __syncthreads();
+        if (t == 0) {
+            double u = 0.0;
+            for (int k = 0; k < nw; ++k) u += wsum[k];
+            S[q] = u;
+        }
+        __syncthreads();
+    }
+}
+
+// Convergence bookkeeping of one control point (one thread).
+__device__ __forceinline__ void ctl_decide(IsmState *st, const double *S, int mode)
+{
+    switch (mode) {
+    case CTL_RHS_MEAN:
+        st->mean = S[0] * st->inv_n;
+        break;
+    case CTL_RHS_NORM: {
+        const double bn = sqrt(S[0]);
+        st->bnorm = bn;
+        st->zero_rhs = (bn == 0.0);
+        if (!isfinite(bn)) { st->status = ISM_ERR_NONFINITE; st->done = 1; }
+        break;
+    }
+    case CTL_FP64_INIT:
+    case CTL_FP64_AFTER:
+    case CTL_OUTER_INIT:
+    case CTL_OUTER_AFTER: {
+        const bool fp64 = (mode == CTL_FP64_INIT || mode == CTL_FP64_AFTER);
+        const bool after = (mode == CTL_FP64_AFTER || mode == CTL_OUTER_AFTER);
+        int k;
+        if (fp64) { if (after) st->cycles++; k = st->cycles; }
+        else { if (after) st->outer++; k = st->outer; }
+        const double rel = st->bnorm > 0.0 ? sqrt(S[0]) / st->bnorm : 0.0;
+        st->relres = rel;
+        st->mean = S[1] * st->inv_n;
+        if (k < ISM_HMAX) st->hist[k] = rel;
+        if (!isfinite(rel)) { st->status = ISM_ERR_NONFINITE; st->done = 1; }
+        else if (rel <= st->tol || st->zero_rhs) { st->status = ISM_OK; st->done = 1; }
+        else if (fp64 ? (st->cycles >= st->max_cycles)
+                      : (st->outer >= st->max_outer || st->cycles >= st->max_cycles)) {
+            st->status = ISM_ERR_NOT_CONVERGED;
+            st->done = 1;
+        }
+        if (!fp64 && !st->done) {      // start a new inner solve on r = b - A p
+            st->inner_done = 0;
+            st->inner_cycles = 0;
+            st->cur = 0;
+            st->mean_e = 0.0;
+            st->r32norm = sqrt(S[0]);
+        }
+        break;
+    }
+    case CTL_INNER: {
+        st->inner_cycles++;
+        st->cycles++;
+        st->cur = (st->cur + st->npass) & 1;
+        const double rin = sqrt(S[0]), en = sqrt(S[2]);
+        st->rin = rin;
+        st->enorm = en;
+        st->mean_e = S[1] * st->inv_n;
+        const double lim = fmax(st->inner_tol * st->r32norm, st->floor_mult * 0x1p-23 * en);
+        if (!isfinite(rin)) st->inner_done = 1;
+        else if (rin <= lim || st->inner_cycles >= st->inner_max || st->cycles >= st->max_cycles)
+            st->inner_done = 1;
+        break;
+    }
+    }
+}
+
+// Last-CTA-done control: every CTA has written its partial sums; the CTA
+// that finishes last reduces them in fixed order and applies the control
+// decision, then re-arms the ticket.  No CTA waits for another.
+__device__ __forceinline__ void ctl_last_block(IsmState *st, const double *partials, int nblk,
+                                               int nq, int mode)
+{
+    __shared__ int am_last;
+    __shared__ double S[ISM_NQ];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(&st->ticket, 1u) == (unsigned)(nblk - 1));
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    ctl_reduce(partials, nblk, nq, S);
+    if (threadIdx.x == 0) {
+        ctl_decide(st, S, mode);
+        st->ticket = 0;
+    }
+}
+
+// ----------------------------------------------------------------- interpolation
+
+// Bilinear prolongation value (Eq. 5) at fine cell (x, y) from coarse values
+// q (ncy x ncx), coarse centre I at fine coordinate (I + 1/2) m.  Beyond the
+// outermost centres the ghost centre mirrors the edge value: even at a
+// Neumann face, odd (sign flip) at a Dirichlet-0 face.
+template <typename T>
+__device__ __forceinline__ T coarse_ghost(const T *__restrict__ q, int I, int J, int ncx,
+                                          int ncy, int bcmask)
+{
+    bool neg = false;
+    if (I < 0) { I = 0; neg ^= (bcmask & 1) != 0; }
+    if (I >= ncx) { I = ncx - 1; neg ^= (bcmask & 2) != 0; }
+    if (J < 0) { J = 0; neg ^= (bcmask & 4) != 0; }
+    if (J >= ncy) { J = ncy - 1; neg ^= (bcmask & 8) != 0; }
+    T v = q[(size_t)J * ncx + I];
+    return neg ? -v : v;
+}
+
+template <typename T>
+__device__ __forceinline__ T prolong_value(const T *__restrict__ q, int x, int y, int m,
+                                           int ncx, int ncy, int bcmask, int kind)
+{
+    if (kind == ISM_COARSE_ACM) return q[(size_t)(y / m) * ncx + (x / m)];
+    const int hm = m >> 1;
+    const int I0 = (x - hm + m) / m - 1;   // floor((x + 1/2)/m - 1/2), x >= 0
+    const int J0 = (y - hm + m) / m - 1;
+    const T invm = (T)1 / (T)m;            // m is a power of two: exact
+    const T tx = ((T)(x - I0 * m - hm) + (T)0.5) * invm;
+    const T ty = ((T)(y - J0 * m - hm) + (T)0.5) * invm;
+    const T q11 = coarse_ghost(q, I0, J0, ncx, ncy, bcmask);
+    const T q21 = coarse_ghost(q, I0 + 1, J0, ncx, ncy, bcmask);
+    const T q12 = coarse_ghost(q, I0, J0 + 1, ncx, ncy, bcmask);
+    const T q22 = coarse_ghost(q, I0 + 1, J0 + 1, ncx, ncy, bcmask);
+    const T ux = (T)1 - tx, uy = (T)1 - ty;
+    return q11 * ux * uy + q21 * tx * uy + q12 * ux * ty + q22 * tx * ty;
+}
+
+// ----------------------------------------------------------------- FP64 path
+
+// One colour of a red-black Gauss-Seidel sweep, in place.  Each cell of the
+// colour depends only on cells of the other colour, so the order inside a
+// colour is free.  Grid: (ceil(ceil(nx/2)/blockDim), ny).
+template <typename T>
+__global__ void k_rbgs_colour(T *__restrict__ p, const T *__restrict__ b, int nx, int ny,
+                              int bcmask, int colour, const int *skip)
+{
+    if (skip && *skip) return;
+    const int j = blockIdx.y;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = 2 * t + ((colour + j) & 1);
+    if (i >= nx) return;
+    const size_t idx = (size_t)j * nx + i;
+    T s = (T)0;
+    if (i > 0) s += p[idx - 1];
+    if (i < nx - 1) s += p[idx + 1];
+    if (j > 0) s += p[idx - nx];
+    if (j < ny - 1) s += p[idx + nx];
+    p[idx] = (s - b[idx]) * inv_diag<T>(diag_count(i, j, nx, ny, bcmask));
+}
+
+// Residual r = b - A_f p, its m x m block sums (restriction) and the partial
+// sums (||r||^2, sum p, sum p^2).  One CTA per coarse cell.
+template <typename T>
+__global__ void k_resid(const T *__restrict__ p, const T *__restrict__ b, T *__restrict__ rc,
+                        double *partials, int nx, int ny, int m, int bcmask, const int *skip,
+                        IsmState *ctl_st = nullptr, int ctl_mode = -1)
+{
+    if (skip && *skip) return;
+    const int I = blockIdx.x, J = blockIdx.y, ncx = gridDim.x;
+    const int mm = m * m;
+    T acc = 0, r2 = 0, ps = 0, p2 = 0;
+    for (int k = threadIdx.x; k < mm; k += blockDim.x) {
+        const int i = I * m + (k % m), j = J * m + (k / m);
+        const size_t idx = (size_t)j * nx + i;
+        const T pc = p[idx];
+        T s = (T)0;
+        if (i > 0) s += p[idx - 1];
+        if (i < nx - 1) s += p[idx + 1];
+        if (j > 0) s += p[idx - nx];
+        if (j < ny - 1) s += p[idx + nx];
+        const T r = b[idx] - (s - (T)diag_count(i, j, nx, ny, bcmask) * pc);
+        acc += r;
+        r2 += r * r;
+        ps += pc;
+        p2 += pc * pc;
+    }
+    // block sum of r (deterministic tree) -> rc
+    __shared__ T redT[32];
+    T a = warp_sum(acc);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) redT[w] = a;
+    __syncthreads();
+    if (w == 0) {
+        T t = lane < nw ? redT[lane] : (T)0;
+        t = warp_sum(t);
+        if (lane == 0) rc[(size_t)J * ncx + I] = t;
+    }
+    double v[3] = {(double)r2, (double)ps, (double)p2};
+    block_partials<3>(v, partials, ncx * gridDim.y, J * ncx + I);
+    if (ctl_mode >= 0) ctl_last_block(ctl_st, partials, ncx * gridDim.y, 3, ctl_mode);
+}
+
+// p = p - mean + P e_c  (mean: state field when use_mean, else 0)
+template <typename T>
+__global__ void k_prolong(T *__restrict__ p, const T *__restrict__ ec, int nx, int ny, int m,
+                          int ncx, int ncy, int bcmask, int kind, const IsmState *st,
+                          int use_mean, const int *skip)
+{
+    if (skip && *skip) return;
+    const int j = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    const size_t idx = (size_t)j * nx + i;
+    T v = p[idx];
+    if (use_mean) v -= (T)st->mean;
+    p[idx] = v + prolong_value<T>(ec, i, j, m, ncx, ncy, bcmask, kind);
+}
+
+// ----------------------------------------------------------------- coarse solve
+// A_c = (Qy x Qx) diag(mu) (Qy x Qx)^T, so A_c^+ r_c = Qy [(Qy^T R Qx) / mu] Qx^T
+// with 1/mu := 0 on the null mode.  R, E are ncy x ncx row-major.
+
+// Row-parallel dense products with the j (or i) sums split over JS chunks
+// of threads so that many loads are in flight; partial sums are combined in
+// fixed order.  smem: (JS + 1) * n values.
+template <typename T, typename F>
+__device__ __forceinline__ void row_times_matrix(int n_out, int n_in, F term, T *part, T *out)
+{
+    const int nth = blockDim.x;
+    const int JS = n_out >= nth ? 1 : nth / n_out;
+    const int chunk = (n_in + JS - 1) / JS;
+    for (int t = threadIdx.x; t < n_out * JS; t += nth) {
+        const int o = t % n_out, c = t / n_out;
+        const int j0 = c * chunk, j1 = min(n_in, j0 + chunk);
+        T s = (T)0;
+#pragma unroll 4
+        for (int j = j0; j < j1; ++j) s += term(j, o);
+        part[c * n_out + o] = s;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < n_out; o += nth) {
+        T s = (T)0;
+        for (int c = 0; c < JS; ++c) s += part[c * n_out + o];
+        out[o] = s;
+    }
+    __syncthreads();
+}
+
+// T[l][k] = Minv[l][k] * sum_i (sum_j QyT[l][j] R[j][i]) Qx[i][k]; one CTA per row l.
+// FROM_PARTS: R[j][i] is the fixed-order sum of the 4 partial block sums.
+template <typename T, bool FROM_PARTS>
+__global__ void k_coarse1(const T *__restrict__ R, const T *__restrict__ QyT,
+                          const T *__restrict__ Qx, const T *__restrict__ Minv,
+                          T *__restrict__ Tm, int ncx, int ncy, const int *skip)
+{
+    if (skip && *skip) return;
+    extern __shared__ unsigned char smraw[];
+    T *w = reinterpret_cast<T *>(smraw);
+    T *v = w + ncx;
+    T *part = v + ncx;
+    const int l = blockIdx.x;
+    const T *qrow = QyT + (size_t)l * ncy;
+    row_times_matrix<T>(ncx, ncy, [&](int j, int i) -> T {
+        const size_t k = (size_t)j * ncx + i;
+        T rv;
+        if (FROM_PARTS) {
+            const T *q4 = R + 4 * k;
+            rv = ((q4[0] + q4[1]) + q4[2]) + q4[3];
+        } else {
+            rv = R[k];
+        }
+        return qrow[j] * rv;
+    }, part, w);
+    row_times_matrix<T>(ncx, ncx, [&](int i, int k) -> T { return w[i] * Qx[(size_t)i * ncx + k]; }, part, v);
+    for (int k = threadIdx.x; k < ncx; k += blockDim.x)
+        Tm[(size_t)l * ncx + k] = v[k] * Minv[(size_t)l * ncx + k];
+}
+
+// E[j][i] = sum_k (sum_l Qy[j][l] T[l][k]) QxT[k][i]; one CTA per row j.
+// MAKE_G: also the x-interpolated row G[j][x], x = 0..nx-1 (bilinear rule of
+// Eq. 5 along x with the mirror ghosts; constant per block for ACM), used by
+// the fused prolongation, and the partial block sums of row j are cleared
+// for the next restriction.
+template <typename T, bool MAKE_G>
+__global__ void k_coarse2(const T *__restrict__ Tm, const T *__restrict__ Qy,
+                          const T *__restrict__ QxT, T *__restrict__ E, int ncx, int ncy,
+                          const int *skip, T *__restrict__ G, int nx, int m, int bcmask, int kind,
+                          T *__restrict__ rcpart)
+{
+    if (skip && *skip) return;
+    extern __shared__ unsigned char smraw[];
+    T *w = reinterpret_cast<T *>(smraw);
+    T *erow = w + ncx;
+    T *part = erow + ncx;
+    const int j = blockIdx.x;
+    const T *qrow = Qy + (size_t)j * ncy;
+    row_times_matrix<T>(ncx, ncy, [&](int l, int k) -> T { return qrow[l] * Tm[(size_t)l * ncx + k]; }, part, w);
+    row_times_matrix<T>(ncx, ncx, [&](int k, int i) -> T { return w[k] * QxT[(size_t)k * ncx + i]; }, part, erow);
+    for (int i = threadIdx.x; i < ncx; i += blockDim.x) E[(size_t)j * ncx + i] = erow[i];
+    if (MAKE_G) {
+        for (int i = threadIdx.x; i < 4 * ncx; i += blockDim.x) rcpart[(size_t)j * ncx * 4 + i] = (T)0;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            T g;
+            if (kind == ISM_COARSE_ACM) {
+                g = erow[x / m];
+            } else {
+                const int hm = m >> 1;
+                const int I0 = (x - hm + m) / m - 1;
+                const T tx = ((T)(x - I0 * m - hm) + (T)0.5) / (T)m;
+                T qa = I0 < 0 ? ((bcmask & 1) ? -erow[0] : erow[0]) : erow[I0];
+                T qb = I0 + 1 >= ncx ? ((bcmask & 2) ? -erow[ncx - 1] : erow[ncx - 1]) : erow[I0 + 1];
+                g = ((T)1 - tx) * qa + tx * qb;
+            }
+            G[(size_t)j * nx + x] = g;
+        }
+    }
+}

@@ -1,0 +1,383 @@
+// ism_sweep32.cuh -- single-precision fused smoothing pass, register tiled.
+//
+// One CTA owns a 128 x 128 region of the fine grid: 8 warps stacked along y,
+// 16 rows each; lane l of a warp holds columns 4l..4l+3 of its 16 rows in
+// registers, plus one halo row above and below.  A red-black half-sweep
+// (Sec. 3.1) updates, in every row, the two cells of the active colour:
+//   * the vertical neighbours are registers of the same thread,
+//   * the in-thread horizontal neighbours are registers,
+//   * the one outer horizontal neighbour comes from lane l-1 or l+1 with a
+//     single warp shuffle (the active colour alternates by row, so a row
+//     needs either the left or the right one, never both),
+// i.e. five instructions per cell update.  After each half-sweep the first
+// and last rows of every warp are exchanged through shared memory
+// (double-buffered, one barrier per half-sweep).
+//
+// K sweeps run on the region before it is written back.  Values at the
+// region edge are stale (shuffles wrap to the lane itself, the outermost
+// halo rows are never refreshed); the error front moves one cell per
+// half-sweep, so after 2K half-sweeps every cell at distance >= 2K from the
+// region edge equals K sequential sweeps.  The CTA writes back its valid
+// tile, the region minus a halo H = 2K (+1 with the residual) on each side.
+//
+// Cells outside the domain are 0 and never updated (the neighbour sum then
+// equals the sum over in-domain neighbours).  CTAs whose region lies strictly
+// inside the domain take a path with divisor 4 everywhere and the right-hand
+// side pre-scaled by 1/4; CTAs touching the boundary compute each cell's
+// divisor d = 4 +- 1 per boundary face (Neumann -1, Dirichlet-0 +1).
+//
+// Options fused into the pass:
+//  PROLONG: add P e_c - mean while loading.  P e_c is evaluated from the
+//           x-interpolated coarse rows G[J][x] (made by the coarse solve):
+//           p += (1 - t_y) G[J0][x] + t_y G[J0+1][x] (Eq. 5, separable form).
+//  RESID:   residual r = b - A_f p of the valid tile, its partial m x m block
+//           sums (rcpart: 4 slots per coarse cell, one per covering tile,
+//           summed in fixed order by the coarse solve) and the norm partials.
+#pragma once
+
+#include "ism_kernels.cuh"
+
+constexpr int SNC = 4;                  // columns per thread
+constexpr int SRR = 16;                 // rows per warp
+constexpr int SNW = 8;                  // warps per CTA
+constexpr int SRW = 32 * SNC;           // region width 128
+constexpr int SRH = SNW * SRR;          // region height 128
+constexpr int STHREADS = 32 * SNW;      // 256
+constexpr int SMAXK = 8;                // sweeps per pass (H <= 17, valid tile >= 94)
+
+struct SweepArgs {
+    float *e0, *e1;           // ping-pong iterate buffers
+    const float *b;           // right-hand side
+    const float *G;           // x-interpolated coarse correction rows, ncy x nx (PROLONG)
+    float *rcpart;            // 4 partial block sums per coarse cell (RESID), zeroed before
+    double *partials;         // per-CTA ||r||^2, sum p, sum p^2 (RESID)
+    IsmState *st;             // mean_e (PROLONG); control block (RESID with ctl_mode >= 0)
+    const int *skip;          // phase-finished flag or NULL
+    const int *curp;          // buffer index of the input at q = 0, or NULL (= 0)
+    int nx, ny, m, lm, ncx, ncy, bcmask, kind, K, q, use_mean, ctl_mode;
+    int H, Hc, TW, TH;        // row halo, column halo (multiple of 4), valid tile width / height
+    int gx, gy;               // tile grid
+    int ix0, iy0;             // interior launch: tile = block + (ix0, iy0)
+    const int2 *edge_tiles;   // edge launch: tile = edge_tiles[block]
+};
+
+// Row halo 2K (+1 for the residual); the column halo is rounded up to a
+// multiple of 4 so that every thread's 4 columns are one aligned float4.
+__host__ __device__ inline int sweep_halo(int K, bool resid) { return 2 * K + (resid ? 1 : 0); }
+__host__ __device__ inline int sweep_halo_cols(int K, bool resid) { return (sweep_halo(K, resid) + 3) & ~3; }
+__host__ __device__ inline int sweep_tile_w(int K, bool resid) { return SRW - 2 * sweep_halo_cols(K, resid); }
+__host__ __device__ inline int sweep_tile_h(int K, bool resid) { return SRH - 2 * sweep_halo(K, resid); }
+
+// b of this thread's 4 cells of a row, stored as (q0, q2, q1, q3) so the two
+// cells of one colour are adjacent
+__device__ __forceinline__ int bperm(int q) { return (q & 1) * 2 + (q >> 1); }
+
+// Divisor contribution of the south / north faces for global row y.
+__device__ __forceinline__ float row_adj(int y, int ny, int bcmask)
+{
+    float d = 0.0f;
+    if (y == 0) d += (bcmask & 4) ? 1.0f : -1.0f;
+    if (y == ny - 1) d += (bcmask & 8) ? 1.0f : -1.0f;
+    return d;
+}
+
+// Boundary data of a warp for the edge launch: rows [rlo, rhi) of the warp
+// lie in the domain; row rs (rn) is the domain's south (north) row, or -1;
+// the divisor of a cell is 4 + column part + adjS/adjN on those rows.
+struct EdgeRows {
+    int rlo, rhi, rs, rn;
+    float inv_s[SNC], inv_n[SNC];   // 1/d on the south and north domain rows
+};
+
+__device__ __forceinline__ float edge_inv(const EdgeRows &er, const float (&rq)[SNC], int r, int q)
+{
+    return r == er.rs ? er.inv_s[q] : (r == er.rn ? er.inv_n[q] : rq[q]);
+}
+
+// Half-sweep of colour parity PAR over the warp's rows; EDGE selects the
+// boundary-aware update (out-of-domain cells are never updated).
+template <int PAR, bool EDGE>
+__device__ __forceinline__ void half_sweep(float (&P)[SRR + 2][SNC], const float *bs,
+                                           const float (&idq)[SNC], const float (&rq)[SNC],
+                                           const bool colin, const EdgeRows &er)
+{
+#pragma unroll
+    for (int r = 0; r < SRR; ++r) {
+        const int qp = PAR ^ (r & 1);            // which pair of columns has the active colour
+        const float2 bb = *reinterpret_cast<const float2 *>(bs + r * SRW + 2 * qp);
+        if (qp == 0) {
+            const float left = __shfl_up_sync(FULLMASK, P[r + 1][3], 1);
+            float s0 = ((left + P[r + 1][1]) + P[r][0]) + P[r + 2][0];
+            float s2 = ((P[r + 1][1] + P[r + 1][3]) + P[r][2]) + P[r + 2][2];
+            if (!EDGE) {
+                P[r + 1][0] = fmaf(s0, 0.25f, -bb.x);
+                P[r + 1][2] = fmaf(s2, 0.25f, -bb.y);
+            } else if (colin && r >= er.rlo && r < er.rhi) {
+                P[r + 1][0] = (s0 - bb.x) * edge_inv(er, rq, r, 0);
+                P[r + 1][2] = (s2 - bb.y) * edge_inv(er, rq, r, 2);
+            }
+        } else {
+            const float right = __shfl_down_sync(FULLMASK, P[r + 1][0], 1);
+            float s1 = ((P[r + 1][0] + P[r + 1][2]) + P[r][1]) + P[r + 2][1];
+            float s3 = ((P[r + 1][2] + right) + P[r][3]) + P[r + 2][3];
+            if (!EDGE) {
+                P[r + 1][1] = fmaf(s1, 0.25f, -bb.x);
+                P[r + 1][3] = fmaf(s3, 0.25f, -bb.y);
+            } else if (colin && r >= er.rlo && r < er.rhi) {
+                P[r + 1][1] = (s1 - bb.x) * edge_inv(er, rq, r, 1);
+                P[r + 1][3] = (s3 - bb.y) * edge_inv(er, rq, r, 3);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void exchange_rows(float (&P)[SRR + 2][SNC], float *xch, int buf,
+                                              int w, int lane)
+{
+    float4 *X = reinterpret_cast<float4 *>(xch);
+    // xch layout: [2 buffers][SNW warps][2 rows][32 lanes] float4
+    const int base = buf * SNW * 2 * 32;
+    X[base + (w * 2 + 0) * 32 + lane] = make_float4(P[1][0], P[1][1], P[1][2], P[1][3]);
+    X[base + (w * 2 + 1) * 32 + lane] = make_float4(P[SRR][0], P[SRR][1], P[SRR][2], P[SRR][3]);
+    __syncthreads();
+    if (w > 0) {
+        const float4 v = X[base + ((w - 1) * 2 + 1) * 32 + lane];
+        P[0][0] = v.x; P[0][1] = v.y; P[0][2] = v.z; P[0][3] = v.w;
+    }
+    if (w < SNW - 1) {
+        const float4 v = X[base + ((w + 1) * 2 + 0) * 32 + lane];
+        P[SRR + 1][0] = v.x; P[SRR + 1][1] = v.y; P[SRR + 1][2] = v.z; P[SRR + 1][3] = v.w;
+    }
+}
+
+// G rows needed by a region: its rows span at most SRH/8 + 3 coarse rows (m >= 8)
+constexpr int SGROWS = SRH / 8 + 3;
+inline size_t sweep_smem_bytes()
+{
+    return (size_t)SRH * SRW * 4 + (size_t)2 * SNW * 2 * SRW * 4 + (size_t)SGROWS * SRW * 4;
+}
+
+// EDGE: the launch over the tiles whose region touches the domain boundary
+// (listed in edge_tiles); otherwise the launch over the interior tiles.
+template <bool PROLONG, bool RESID, bool EDGE>
+__global__ void __launch_bounds__(STHREADS, 2) k_sweep32(SweepArgs a)
+{
+    if (a.skip && *a.skip) return;
+    int bx, by;
+    if (EDGE) {
+        const int2 t = a.edge_tiles[blockIdx.x];
+        bx = t.x;
+        by = t.y;
+    } else {
+        bx = blockIdx.x + a.ix0;
+        by = blockIdx.y + a.iy0;
+    }
+    extern __shared__ __align__(16) float sm[];
+    float *bsm = sm;                       // SRH x SRW (b per thread, colour-pair order)
+    float *xch = sm + SRH * SRW;           // row exchange buffers
+    float *gsm = xch + 2 * SNW * 2 * SRW;  // coarse correction rows G[Jg0 ..] of this region
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nx = a.nx, ny = a.ny, H = a.H, Hc = a.Hc, TW = a.TW, TH = a.TH;
+    const int x0 = bx * TW - Hc, y0 = by * TH - H;  // region origin, x0 % 4 == 0
+    const int cx = x0 + SNC * lane;        // first column of this thread
+    const int ry0 = w * SRR;               // first region row of this warp
+    constexpr bool edge = EDGE;
+    const int in = ((a.curp ? *a.curp : 0) + a.q) & 1;
+    const float *__restrict__ pin = in ? a.e1 : a.e0;
+    float *__restrict__ pout = in ? a.e0 : a.e1;
+    float *bs = bsm + ry0 * SRW + SNC * lane;   // this thread's b, row stride SRW
+    // nx % 4 == 0 and cx % 4 == 0: a thread's 4 columns are all in or all out
+    const bool colin = (unsigned)cx < (unsigned)nx;
+    const bool colvalid = colin && (SNC * lane >= Hc) && (SNC * lane < Hc + TW);
+
+    // divisor part from the W/E faces and its reciprocal (edge launch)
+    float idq[SNC], rq[SNC];
+#pragma unroll
+    for (int q = 0; q < SNC; ++q) {
+        const int x = cx + q;
+        float d = 4.0f;
+        if (x == 0) d += (a.bcmask & 1) ? 1.0f : -1.0f;
+        if (x == nx - 1) d += (a.bcmask & 2) ? 1.0f : -1.0f;
+        idq[q] = d;
+        rq[q] = __frcp_rn(d);
+    }
+    EdgeRows er;
+    {
+        const int yw = y0 + ry0;                     // global row of the warp's row 0
+        er.rlo = max(0, -yw);
+        er.rhi = min(SRR, ny - yw);
+        er.rs = (yw <= 0 && 0 < yw + SRR) ? -yw : -1;
+        er.rn = (yw <= ny - 1 && ny - 1 < yw + SRR) ? ny - 1 - yw : -1;
+        const float adjS = (a.bcmask & 4) ? 1.0f : -1.0f;
+        const float adjN = (a.bcmask & 8) ? 1.0f : -1.0f;
+#pragma unroll
+        for (int q = 0; q < SNC; ++q) {
+            er.inv_s[q] = __frcp_rn(idq[q] + adjS);   // ny >= 8: a row is never both
+            er.inv_n[q] = __frcp_rn(idq[q] + adjN);
+        }
+    }
+
+    // 1. load p (rows -1..SRR) with the fused prolongation, and b
+    float P[SRR + 2][SNC];
+    float mean = 0.f;
+    if (PROLONG && a.use_mean) mean = (float)a.st->mean_e;
+    const int m = a.m, lm = a.lm, hm = m >> 1;
+    const float invm = 1.0f / (float)m;
+    // rows of G used by region rows y0-1 .. y0+SRH (clamped to the coarse grid)
+    int Jg0 = 0;
+    if (PROLONG) {
+        Jg0 = a.kind == ISM_COARSE_ACM ? max(0, (y0 - 1) >> lm) : max(0, ((y0 - 1 - hm + m) >> lm) - 1);
+        const int Jg1 = min(a.ncy - 1, a.kind == ISM_COARSE_ACM ? (y0 + SRH) >> lm : ((y0 + SRH - hm + m) >> lm));
+        const int nrow = Jg1 - Jg0 + 1;
+        for (int t = threadIdx.x; t < nrow * 32; t += STHREADS) {
+            const int jr = t >> 5, l = t & 31, x = x0 + SNC * l;
+            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+            if ((unsigned)x < (unsigned)nx) g = *reinterpret_cast<const float4 *>(a.G + (size_t)(Jg0 + jr) * nx + x);
+            reinterpret_cast<float4 *>(gsm)[jr * 32 + l] = g;
+        }
+        __syncthreads();
+    }
+    const float4 *gs4 = reinterpret_cast<const float4 *>(gsm) + lane;
+#pragma unroll
+    for (int r = 0; r < SRR + 2; ++r) {
+        const int y = y0 + ry0 + r - 1;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((unsigned)y < (unsigned)ny && colin) {
+            v = *reinterpret_cast<const float4 *>(pin + (size_t)y * nx + cx);
+            if (PROLONG) {
+                float4 ga, gb;
+                float wa, wb;
+                if (a.kind == ISM_COARSE_ACM) {
+                    ga = gs4[((y >> lm) - Jg0) * 32];
+                    gb = ga;
+                    wa = 1.0f;
+                    wb = 0.0f;
+                } else {
+                    const int J0 = ((y - hm + m) >> lm) - 1;
+                    const float ty = ((float)(y - J0 * m - hm) + 0.5f) * invm;
+                    int Ja = J0, Jb = J0 + 1;
+                    float sa = 1.f, sb = 1.f;
+                    if (Ja < 0) { Ja = 0; if (a.bcmask & 4) sa = -1.f; }
+                    if (Jb >= a.ncy) { Jb = a.ncy - 1; if (a.bcmask & 8) sb = -1.f; }
+                    ga = gs4[(Ja - Jg0) * 32];
+                    gb = gs4[(Jb - Jg0) * 32];
+                    wa = sa * (1.0f - ty);
+                    wb = sb * ty;
+                }
+                v.x = (v.x - mean) + fmaf(wa, ga.x, wb * gb.x);
+                v.y = (v.y - mean) + fmaf(wa, ga.y, wb * gb.y);
+                v.z = (v.z - mean) + fmaf(wa, ga.z, wb * gb.z);
+                v.w = (v.w - mean) + fmaf(wa, ga.w, wb * gb.w);
+            }
+        }
+        P[r][0] = v.x; P[r][1] = v.y; P[r][2] = v.z; P[r][3] = v.w;
+    }
+#pragma unroll
+    for (int r = 0; r < SRR; ++r) {
+        const int y = y0 + ry0 + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((unsigned)y < (unsigned)ny && colin) v = *reinterpret_cast<const float4 *>(a.b + (size_t)y * nx + cx);
+        if (!edge) { v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f; }
+        *reinterpret_cast<float4 *>(bs + r * SRW) = make_float4(v.x, v.z, v.y, v.w);
+    }
+
+    // 2. 2K half-sweeps, red ((x+y) even) first
+    const int base = (x0 + y0 + ry0) & 1;      // colour parity of (column 0, row 0) of this warp
+    for (int s = 0; s < 2 * a.K; ++s) {
+        const int par = (s & 1) ^ base;        // active colour c = s & 1: q-parity = c ^ base ^ (r & 1)
+        if (par == 0) half_sweep<0, EDGE>(P, bs, idq, rq, colin, er);
+        else half_sweep<1, EDGE>(P, bs, idq, rq, colin, er);
+        exchange_rows(P, xch, s & 1, w, lane);
+    }
+
+    // 3. write back the valid tile (rows [H, H+TH), columns [Hc, Hc+TW) of the region)
+    if (colvalid) {
+#pragma unroll
+        for (int r = 0; r < SRR; ++r) {
+            const int rr = ry0 + r, y = y0 + rr;
+            if (rr >= H && rr < H + TH && (unsigned)y < (unsigned)ny)
+                *reinterpret_cast<float4 *>(pout + (size_t)y * nx + cx) =
+                    make_float4(P[r + 1][0], P[r + 1][1], P[r + 1][2], P[r + 1][3]);
+        }
+    }
+
+    if (RESID) {
+        // 4. residual of the valid tile; per-thread sums of r over the (up to
+        //    three) coarse rows that this warp's 16 rows touch
+        const int yw = y0 + ry0, Jw = yw >> lm;          // floor division (yw may be < 0)
+        const int r1 = ((Jw + 1) << lm) - yw, r2 = ((Jw + 2) << lm) - yw;
+        float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+        float r2s = 0.f, ps = 0.f, p2 = 0.f;
+#pragma unroll
+        for (int r = 0; r < SRR; ++r) {
+            const float left = __shfl_up_sync(FULLMASK, P[r + 1][3], 1);
+            const float right = __shfl_down_sync(FULLMASK, P[r + 1][0], 1);
+            const int rr = ry0 + r, y = y0 + rr;
+            const bool ok = colvalid && rr >= H && rr < H + TH && (unsigned)y < (unsigned)ny;
+            const float4 bv = *reinterpret_cast<const float4 *>(bs + r * SRW);
+            const float bq[SNC] = {bv.x, bv.z, bv.y, bv.w};
+            const float ra = row_adj(y, ny, a.bcmask);
+            float rowsum = 0.f;
+#pragma unroll
+            for (int q = 0; q < SNC; ++q) {
+                const float lf = q == 0 ? left : P[r + 1][q - 1];
+                const float rt = q == SNC - 1 ? right : P[r + 1][q + 1];
+                const float pc = P[r + 1][q];
+                const float sn = ((lf + rt) + P[r][q]) + P[r + 2][q];
+                const float bb = EDGE ? bq[q] : 4.0f * bq[q];
+                const float res = EDGE ? bb - (sn - (idq[q] + ra) * pc) : bb - fmaf(-4.0f, pc, sn);
+                if (ok) { rowsum += res; r2s = fmaf(res, res, r2s); ps += pc; p2 = fmaf(pc, pc, p2); }
+            }
+            if (r < r1) acc0 += rowsum;
+            else if (r < r2) acc1 += rowsum;
+            else acc2 += rowsum;
+        }
+        // 5. partial block sums over (coarse cell) x (valid tile): gather the
+        //    per-thread sums of every coarse cell in fixed (warp, row-part,
+        //    lane) order
+        __syncthreads();                                  // xch is reused below
+        float *racc = xch;                                // [SNW][3][32]
+        racc[(w * 3 + 0) * 32 + lane] = acc0;
+        racc[(w * 3 + 1) * 32 + lane] = acc1;
+        racc[(w * 3 + 2) * 32 + lane] = acc2;
+        __syncthreads();
+        const int gx_lo = bx * TW, gx_hi = min(gx_lo + TW, nx);
+        const int gy_lo = by * TH, gy_hi = min(gy_lo + TH, ny);
+        const int I0 = gx_lo >> lm, I1 = (gx_hi - 1) >> lm, J0 = gy_lo >> lm, J1 = (gy_hi - 1) >> lm;
+        const int nbx = I1 - I0 + 1, nb = nbx * (J1 - J0 + 1);
+        for (int cb = threadIdx.x; cb < nb; cb += STHREADS) {
+            const int I = I0 + cb % nbx, J = J0 + cb / nbx;
+            // lanes whose 4 columns lie in coarse column I
+            const int l0 = max(0, (I * m - x0 + 3) >> 2), l1 = min(32, ((I + 1) * m - x0 + 3) >> 2);
+            float sacc = 0.f;
+            for (int ww = 0; ww < SNW; ++ww) {
+                const int k = J - ((y0 + ww * SRR) >> lm);
+                if (k < 0 || k > 2) continue;
+                const float *row = racc + (ww * 3 + k) * 32;
+                for (int l = l0; l < l1; ++l) sacc += row[l];
+            }
+            const int slot = (bx - (I * m) / TW) + 2 * (by - (J * m) / TH);
+            a.rcpart[((size_t)J * a.ncx + I) * 4 + slot] = sacc;
+        }
+        // 6. norm partials (per-warp float sums combined in double), then the
+        //    fused convergence control in the last CTA to finish
+        __shared__ double red[3][SNW];
+        const double v0 = warp_sum(r2s), v1 = warp_sum(ps), v2 = warp_sum(p2);
+        if (lane == 0) { red[0][w] = v0; red[1][w] = v1; red[2][w] = v2; }
+        __syncthreads();
+        const int nblk = a.gx * a.gy;
+        if (threadIdx.x < 3) {
+            double t = 0.0;
+            for (int k = 0; k < SNW; ++k) t += red[threadIdx.x][k];
+            a.partials[(size_t)threadIdx.x * nblk + by * a.gx + bx] = t;
+        }
+        if (a.ctl_mode >= 0) ctl_last_block(a.st, a.partials, nblk, 3, a.ctl_mode);
+    }
+}
+
+// Sum of the 4 partial block sums (fixed order) -> R (ncy x ncx).
+__device__ __forceinline__ float rc_from_parts(const float *rcpart, size_t k)
+{
+    const float4 v = reinterpret_cast<const float4 *>(rcpart)[k];
+    return ((v.x + v.y) + v.z) + v.w;
+}

@@ -1,0 +1,213 @@
+"""Thin Python binding of the ISM C ABI (include/ism.h).
+
+Argument marshalling only: torch tensors become device pointers, the current
+torch CUDA stream becomes the context's ordering stream, and status codes
+become return values (or exceptions via ``check``).  Every numerical step
+runs in the CUDA library; when ``libism.so`` is missing the binding raises
+instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libism.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ism.h")
+
+ISM_OK, ISM_ERR_ARG, ISM_ERR_NOT_CONVERGED, ISM_ERR_NONFINITE, ISM_ERR_CUDA, ISM_ERR_NOMEM = range(6)
+ISM_BC_NEUMANN, ISM_BC_DIRICHLET0 = 0, 1
+ISM_FP64, ISM_MIXED = 0, 1
+ISM_COARSE_ISM, ISM_COARSE_ACM = 0, 1
+ISM_VEL_NOSLIP, ISM_VEL_FREESLIP, ISM_VEL_INFLOW, ISM_VEL_OUTFLOW = 0, 1, 2, 3
+
+
+class IsmOptions(C.Structure):
+    _fields_ = [("nu", C.c_int), ("sweeps_per_pass", C.c_int), ("kind", C.c_int),
+                ("max_outer", C.c_int), ("inner_max", C.c_int), ("inner_tol", C.c_double),
+                ("floor_mult", C.c_double), ("check_every", C.c_int), ("use_graphs", C.c_int)]
+
+
+class IsmError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)} ({status})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+_VP, _I, _D = C.c_void_p, C.c_int, C.c_double
+_SIGS = {
+    "ism_status_str": (C.c_char_p, [_I]),
+    "ism_setup": (_I, [_I, _I, _D, C.POINTER(C.c_int), _I, _I, _VP, C.POINTER(_VP)]),
+    "ism_destroy": (None, [_VP]),
+    "ism_get_options": (_I, [_VP, C.POINTER(IsmOptions)]),
+    "ism_set_options": (_I, [_VP, C.POINTER(IsmOptions)]),
+    "ism_solve": (_I, [_VP, _VP, _VP, _D, _I, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "ism_last_history": (_I, [_VP, C.POINTER(C.c_double), _I]),
+    "ism_last_counts": (_I, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
+    "ism_smooth": (_I, [_VP, _VP, _VP, _I]),
+    "ism_residual_restrict": (_I, [_VP, _VP, _VP, _VP, C.POINTER(C.c_double)]),
+    "ism_coarse_solve": (_I, [_VP, _VP, _VP]),
+    "ism_prolong_add": (_I, [_VP, _VP, _VP]),
+    "ism_set_flow": (_I, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_double), _VP, _D]),
+    "proj_step": (_I, [_VP, _VP, _VP, _VP, _D, _D]),
+    "ism_proj_tol": (_I, [_VP, _D, _I, _I]),
+    "ism_last_dp": (_VP, [_VP]),
+    "ism_solve_batched": (_I, [_I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _D, _I,
+                               C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+}
+
+
+def declared_functions(header: str = HEADER):
+    """Names of the functions declared in include/ism.h."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b([a-z_][a-z0-9_]*)\s*\(", text)) - {"defined"})
+
+
+def lib():
+    """Load libism.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"ISM CUDA library not built ({LIB_PATH}); "
+                                   "run __graft_entry__.build() or python -m paper_1309_7128_gb300.build")
+            L = C.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_str(s: int) -> str:
+    return lib().ism_status_str(int(s)).decode()
+
+
+def check(status: int, where: str = "ism", ok=(ISM_OK,)):
+    if status not in ok:
+        raise IsmError(status, where)
+    return status
+
+
+def _ptr(t):
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+class Ctx:
+    """Owning handle of an ism_ctx."""
+
+    def __init__(self, handle, nx, ny, m, prec):
+        self.handle = handle
+        self.nx, self.ny, self.m, self.prec = nx, ny, m, prec
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.ism_destroy(h)
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def ism_setup(nx, ny, h, bc, coarsen, prec=ISM_FP64, stream=None):
+    """Returns (status, Ctx or None)."""
+    L = lib()
+    bca = (C.c_int * 4)(*[int(x) for x in bc])
+    out = C.c_void_p()
+    s = L.ism_setup(int(nx), int(ny), float(h), bca, int(coarsen), int(prec),
+                    _stream(stream) if stream is not False else C.c_void_p(0), C.byref(out))
+    return s, (Ctx(out.value, nx, ny, coarsen, prec) if s == ISM_OK else None)
+
+
+def ism_get_options(ctx):
+    o = IsmOptions()
+    check(lib().ism_get_options(ctx.handle, C.byref(o)), "ism_get_options")
+    return o
+
+
+def ism_set_options(ctx, opt):
+    return lib().ism_set_options(ctx.handle, C.byref(opt))
+
+
+def ism_solve(ctx, rhs, p, tol=1e-8, max_cycles=100000):
+    """Returns (status, cycles, relres)."""
+    c = C.c_int(0)
+    r = C.c_double(0.0)
+    s = lib().ism_solve(ctx.handle, _ptr(rhs), _ptr(p), float(tol), int(max_cycles), C.byref(c), C.byref(r))
+    return s, c.value, r.value
+
+
+def ism_last_history(ctx, cap=4096):
+    buf = (C.c_double * cap)()
+    n = lib().ism_last_history(ctx.handle, buf, cap)
+    return list(buf[:n])
+
+
+def ism_last_counts(ctx):
+    o, c, l = C.c_int(), C.c_int(), C.c_longlong()
+    check(lib().ism_last_counts(ctx.handle, C.byref(o), C.byref(c), C.byref(l)), "ism_last_counts")
+    return o.value, c.value, l.value
+
+
+def ism_smooth(ctx, p, b, sweeps):
+    return lib().ism_smooth(ctx.handle, _ptr(p), _ptr(b), int(sweeps))
+
+
+def ism_residual_restrict(ctx, p, b, rc):
+    norms = (C.c_double * 2)()
+    s = lib().ism_residual_restrict(ctx.handle, _ptr(p), _ptr(b), _ptr(rc), norms)
+    return s, norms[0], norms[1]
+
+
+def ism_coarse_solve(ctx, rc, ec):
+    return lib().ism_coarse_solve(ctx.handle, _ptr(rc), _ptr(ec))
+
+
+def ism_prolong_add(ctx, ec, p):
+    return lib().ism_prolong_add(ctx.handle, _ptr(ec), _ptr(p))
+
+
+def ism_set_flow(ctx, vel_bc, wall_u=(0.0, 0.0, 0.0, 0.0), u_in=None, conv_u=1.0):
+    vb = (C.c_int * 4)(*[int(x) for x in vel_bc])
+    wu = (C.c_double * 4)(*[float(x) for x in wall_u])
+    return lib().ism_set_flow(ctx.handle, vb, wu, _ptr(u_in), float(conv_u))
+
+
+def ism_proj_tol(ctx, tol=1e-8, max_cycles=100000, warm_start=False):
+    return lib().ism_proj_tol(ctx.handle, float(tol), int(max_cycles), int(bool(warm_start)))
+
+
+def proj_step(ctx, u, v, p, dt, nu):
+    return lib().proj_step(ctx.handle, _ptr(u), _ptr(v), _ptr(p), float(dt), float(nu))
+
+
+def ism_last_dp(ctx):
+    """Device address of the context's last pressure increment (nx*ny doubles)."""
+    return lib().ism_last_dp(ctx.handle)
+
+
+def ism_solve_batched(ctxs, rhs, p, tol=1e-8, max_cycles=100000):
+    """Returns (status, cycles list, relres list)."""
+    n = len(ctxs)
+    ca = (C.c_void_p * n)(*[c.handle for c in ctxs])
+    ra = (C.c_void_p * n)(*[t.data_ptr() for t in rhs])
+    pa = (C.c_void_p * n)(*[t.data_ptr() for t in p])
+    cyc = (C.c_int * n)()
+    rel = (C.c_double * n)()
+    s = lib().ism_solve_batched(n, ca, ra, pa, float(tol), int(max_cycles), cyc, rel)
+    return s, list(cyc), list(rel)

@@ -1,0 +1,136 @@
+"""Each step of the cycle on the GPU (kernel-level C-ABI entry points) against
+the CPU oracle, element by element, on grids that span several 64 x 64
+tiles with ragged edges and every face-type mix."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth.inputs import random_field, smooth_rhs
+from tests.conftest import ALL_BCS
+from tests.gpu_util import dev32, dev64, ensure_built, host, ism, setup
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(160, 96, 32), (96, 160, 16), (128, 64, 8), (256, 192, 32)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+@pytest.mark.parametrize("nx,ny,m", SHAPES)
+@pytest.mark.parametrize("bc", ALL_BCS)
+def test_smooth_fp64(nx, ny, m, bc):
+    p = random_field(nx, ny, 1)
+    b = random_field(nx, ny, 2)
+    ctx = setup(nx, ny, m, bc)
+    pd, bd = dev64(p), dev64(b)
+    ism.check(ism.ism_smooth(ctx, pd, bd, 3))
+    ref = p.copy()
+    for _ in range(3):
+        O.rbgs_sweep(ref, b, bc)
+    np.testing.assert_allclose(host(pd), ref, rtol=0, atol=1e-13 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("nx,ny,m", SHAPES)
+@pytest.mark.parametrize("bc", ALL_BCS)
+@pytest.mark.parametrize("sweeps", [1, 4, 7])
+def test_smooth_fused_fp32(nx, ny, m, bc, sweeps):
+    """Fused multi-sweep pass (temporal blocking) against the oracle's float
+    sweeps: the same operations in the same order, so agreement is at the
+    level of one rounding per update."""
+    p = random_field(nx, ny, 3).astype(np.float32)
+    b = random_field(nx, ny, 4).astype(np.float32)
+    ctx = setup(nx, ny, m, bc, prec=ism.ISM_MIXED)
+    pd, bd = dev32(p), dev32(b)
+    ism.check(ism.ism_smooth(ctx, pd, bd, sweeps))
+    ref = np.ascontiguousarray(p.copy())
+    L = O.lib()
+    bca = np.asarray(bc, dtype=np.int32)
+    for _ in range(sweeps):
+        L.or_rbgs_sweep_f32(nx, ny, bca, ref, np.ascontiguousarray(b))
+    np.testing.assert_allclose(host(pd), ref.astype(np.float64), rtol=0, atol=2e-6 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("nx,ny,m", SHAPES)
+@pytest.mark.parametrize("bc", ALL_BCS)
+def test_residual_restrict(nx, ny, m, bc):
+    p = random_field(nx, ny, 5)
+    b = random_field(nx, ny, 6)
+    ctx = setup(nx, ny, m, bc)
+    rc = dev64(np.zeros((ny // m, nx // m)))
+    s, rnorm, psum = ism.ism_residual_restrict(ctx, dev64(p), dev64(b), rc)
+    ism.check(s)
+    r = O.residual(p, b, bc)
+    ref = O.restrict(r, m)
+    np.testing.assert_allclose(host(rc), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    assert abs(rnorm - np.linalg.norm(r)) <= 1e-12 * np.linalg.norm(r)
+    assert abs(psum - p.sum()) <= 1e-12 * np.abs(p).sum()
+    # single precision
+    ctx32 = setup(nx, ny, m, bc, prec=ism.ISM_MIXED)
+    rc32 = dev32(np.zeros((ny // m, nx // m)))
+    p32, b32 = p.astype(np.float32), b.astype(np.float32)
+    ism.check(ism.ism_residual_restrict(ctx32, dev32(p32), dev32(b32), rc32)[0])
+    ref32 = O.restrict(O.residual(p32.astype(np.float64), b32.astype(np.float64), bc), m)
+    np.testing.assert_allclose(host(rc32), ref32, rtol=0, atol=1e-5 * np.abs(ref32).max())
+
+
+@pytest.mark.parametrize("nx,ny,m", SHAPES)
+@pytest.mark.parametrize("bc", ALL_BCS)
+@pytest.mark.parametrize("kind", ["ism", "acm"])
+def test_coarse_solve(nx, ny, m, bc, kind):
+    ncx, ncy = nx // m, ny // m
+    rc = random_field(ncx, ncy, 7)
+    if not any(bc):
+        rc -= rc.mean()
+    ref = O.OracleISM(nx, ny, m, bc, kind=kind).coarse_solve(rc)
+    for prec, tol in ((ism.ISM_FP64, 1e-11), (ism.ISM_MIXED, 2e-5)):
+        ctx = setup(nx, ny, m, bc, prec=prec, kind=0 if kind == "ism" else 1)
+        mk = dev64 if prec == ism.ISM_FP64 else dev32
+        ec = mk(np.zeros_like(rc))
+        ism.check(ism.ism_coarse_solve(ctx, mk(rc), ec))
+        got = host(ec)
+        if not any(bc):
+            got -= got.mean()       # solutions are defined up to a constant
+        np.testing.assert_allclose(got, ref - (ref.mean() if not any(bc) else 0.0),
+                                   rtol=0, atol=tol * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("nx,ny,m", SHAPES)
+@pytest.mark.parametrize("bc", ALL_BCS)
+@pytest.mark.parametrize("kind", ["ism", "acm"])
+def test_prolong_add(nx, ny, m, bc, kind):
+    q = random_field(nx // m, ny // m, 8)
+    p = random_field(nx, ny, 9)
+    ref = p.copy()
+    if kind == "ism":
+        O.prolong_add(ref, q, m, bc)
+    else:
+        O.prolong_const_add(ref, q, m)
+    ctx = setup(nx, ny, m, bc, kind=0 if kind == "ism" else 1)
+    pd = dev64(p)
+    ism.check(ism.ism_prolong_add(ctx, dev64(q), pd))
+    np.testing.assert_allclose(host(pd), ref, rtol=0, atol=1e-14 * np.abs(ref).max())
+
+
+def test_full_size_single_cycle_fp32():
+    """2048^2, 32h (the benchmark grid): one cycle of GPU steps against the
+    oracle's steps from the same single-precision state."""
+    nx = ny = 2048
+    m = 32
+    b = smooth_rhs(nx, ny, 0).astype(np.float32)
+    rng = np.random.Generator(np.random.PCG64(11))
+    p = (rng.standard_normal((ny, nx)) * 1e-6).astype(np.float32)
+    ctx = setup(nx, ny, m, prec=ism.ISM_MIXED)
+    pd, bd = dev32(p), dev32(b)
+    rc = dev32(np.zeros((ny // m, nx // m)))
+    ism.check(ism.ism_residual_restrict(ctx, pd, bd, rc)[0])
+    rc_ref = O.restrict(O.residual(p.astype(np.float64), b.astype(np.float64), (0, 0, 0, 0)), m)
+    np.testing.assert_allclose(host(rc), rc_ref, rtol=0, atol=1e-4 * np.abs(rc_ref).max())
+    ism.check(ism.ism_smooth(ctx, pd, bd, 8))
+    ref = np.ascontiguousarray(p.copy())
+    bca = np.zeros(4, dtype=np.int32)
+    for _ in range(8):
+        O.lib().or_rbgs_sweep_f32(nx, ny, bca, ref, np.ascontiguousarray(b))
+    np.testing.assert_allclose(host(pd), ref.astype(np.float64), rtol=0, atol=2e-6 * np.abs(ref).max())

@@ -1,0 +1,150 @@
+"""Whole pressure solves on the GPU against the CPU oracle.
+
+FP64 path: same pressure field to 1e-12 relative and the same cycle count.
+Mixed path (single-precision cycles inside FP64 refinement): relative
+residual <= tol, and the field within 1e-9 relative of the converged oracle
+solution.  Edge cases: zero and non-finite right-hand sides, exact initial
+guess, exhausted cycle cap, all face-type mixes, ragged tiles."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth.inputs import random_field, smooth_rhs
+from tests.gpu_util import dev64, ensure_built, host, ism, rel, setup
+
+pytestmark = pytest.mark.gpu
+
+CASES = [  # nx, ny, m, bc
+    (256, 256, 16, (0, 0, 0, 0)),     # config 0
+    (160, 96, 32, (0, 0, 0, 0)),
+    (96, 160, 16, (0, 1, 0, 0)),
+    (128, 64, 8, (1, 1, 1, 1)),
+    (192, 128, 32, (1, 0, 0, 1)),
+    (224, 96, 16, (0, 0, 1, 0)),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+def gpu_solve(b, nx, ny, m, bc, prec, tol=1e-8, p0=None, max_cycles=100000, **opts):
+    ctx = setup(nx, ny, m, bc, prec=prec, **opts)
+    rhs = dev64(b)
+    p = dev64(np.zeros((ny, nx)) if p0 is None else p0)
+    s, cyc, relres = ism.ism_solve(ctx, rhs, p, tol, max_cycles)
+    return s, host(p), cyc, relres, ism.ism_last_history(ctx), ctx
+
+
+@pytest.mark.parametrize("nx,ny,m,bc", CASES)
+def test_fp64_matches_oracle(nx, ny, m, bc):
+    b = smooth_rhs(nx, ny, 1) + (1e-6 if any(bc) else 0.0)
+    ref = O.OracleISM(nx, ny, m, bc)
+    p_ref, c_ref, h_ref = ref.solve(b, tol=1e-8)
+    s, p, c, r, h, _ = gpu_solve(b, nx, ny, m, bc, ism.ISM_FP64)
+    assert s == ism.ISM_OK
+    assert c == c_ref
+    assert rel(p, p_ref) <= 1e-12
+    np.testing.assert_allclose(h, h_ref, rtol=1e-6, atol=1e-13)   # rounding-level differences
+    assert abs(r - h_ref[-1]) <= 1e-13
+
+
+def test_fp64_acm_matches_oracle():
+    nx = ny = 256
+    b = smooth_rhs(nx, ny, 0)
+    p_ref, c_ref, _ = O.OracleISM(nx, ny, 16, kind="acm").solve(b, tol=1e-8)
+    s, p, c, r, h, _ = gpu_solve(b, nx, ny, 16, (0, 0, 0, 0), ism.ISM_FP64, kind=1)
+    assert s == ism.ISM_OK and c == c_ref
+    assert rel(p, p_ref) <= 1e-12
+
+
+def test_config0_ism_beats_acm_on_gpu():
+    b = smooth_rhs(256, 256, 0)
+    c_ism = gpu_solve(b, 256, 256, 16, (0, 0, 0, 0), ism.ISM_FP64)[2]
+    c_acm = gpu_solve(b, 256, 256, 16, (0, 0, 0, 0), ism.ISM_FP64, kind=1)[2]
+    assert c_ism < c_acm / 2
+
+
+@pytest.mark.parametrize("nx,ny,m,bc", CASES)
+def test_mixed_reaches_tolerance_and_matches_oracle(nx, ny, m, bc):
+    b = smooth_rhs(nx, ny, 2) + (1e-6 if any(bc) else 0.0)
+    ref = O.OracleISM(nx, ny, m, bc)
+    p_ex, _, h_ex = ref.solve(b, tol=1e-11)
+    s, p, c, r, h, ctx = gpu_solve(b, nx, ny, m, bc, ism.ISM_MIXED)
+    assert s == ism.ISM_OK
+    assert r <= 1e-8 and h[-1] == r
+    assert rel(p, p_ex) <= 1e-9
+    # the FP64 residual of the returned field, measured by the oracle
+    bb = ref.prepare_rhs(b)
+    assert np.linalg.norm(O.residual(p, bb, bc)) / np.linalg.norm(bb) <= 1.01e-8
+    outer, cycles, _ = ism.ism_last_counts(ctx)
+    assert outer >= 2 and cycles == c
+
+
+def test_zero_rhs_gives_zero_solution():
+    s, p, c, r, h, _ = gpu_solve(np.zeros((64, 64)), 64, 64, 16, (0, 0, 0, 0), ism.ISM_FP64,
+                                 p0=random_field(64, 64, 1))
+    assert s == ism.ISM_OK and c == 0 and np.all(p == 0.0)
+
+
+def test_exact_initial_guess_needs_no_cycle():
+    nx = ny = 128
+    b = smooth_rhs(nx, ny, 3)
+    p_ref, _, _ = O.OracleISM(nx, ny, 16).solve(b, tol=1e-11)
+    for prec in (ism.ISM_FP64, ism.ISM_MIXED):
+        s, p, c, r, h, _ = gpu_solve(b, nx, ny, 16, (0, 0, 0, 0), prec, p0=p_ref)
+        assert s == ism.ISM_OK and c == 0 and r <= 1e-8
+
+
+def test_cycle_cap_reports_not_converged_with_last_iterate():
+    nx = ny = 128
+    b = smooth_rhs(nx, ny, 4)
+    ref = O.OracleISM(nx, ny, 16)
+    p5, c5, h5 = ref.solve(b, tol=1e-30, max_cycles=5)
+    s, p, c, r, h, _ = gpu_solve(b, nx, ny, 16, (0, 0, 0, 0), ism.ISM_FP64, tol=1e-30, max_cycles=5)
+    assert s == ism.ISM_ERR_NOT_CONVERGED and c == 5
+    assert rel(p, p5) <= 1e-12 and abs(r - h5[-1]) <= 1e-9 * h5[-1]
+
+
+def test_nonfinite_rhs_is_reported_and_p_untouched():
+    b = smooth_rhs(64, 64, 5)
+    b[10, 10] = np.nan
+    p0 = random_field(64, 64, 6)
+    for prec in (ism.ISM_FP64, ism.ISM_MIXED):
+        s, p, c, r, h, _ = gpu_solve(b, 64, 64, 16, (0, 0, 0, 0), prec, p0=p0)
+        assert s == ism.ISM_ERR_NONFINITE
+        assert np.array_equal(p, p0)
+
+
+@pytest.mark.parametrize("use_graphs", [0, 1])
+@pytest.mark.parametrize("check_every", [1, 7])
+def test_loop_control_variants_agree(use_graphs, check_every):
+    nx = ny = 128
+    b = smooth_rhs(nx, ny, 7)
+    p_ref, c_ref, _ = O.OracleISM(nx, ny, 16).solve(b, tol=1e-8)
+    s, p, c, r, h, _ = gpu_solve(b, nx, ny, 16, (0, 0, 0, 0), ism.ISM_FP64,
+                                 use_graphs=use_graphs, check_every=check_every)
+    assert s == ism.ISM_OK and c == c_ref and rel(p, p_ref) <= 1e-12
+
+
+@pytest.mark.parametrize("nu,k", [(8, 4), (8, 2), (4, 4), (6, 3), (1, 1)])
+def test_mixed_sweep_fusion_options(nu, k):
+    nx, ny = 192, 128
+    b = smooth_rhs(nx, ny, 8)
+    p_ex, _, _ = O.OracleISM(nx, ny, 32, nu=nu).solve(b, tol=1e-11)
+    s, p, c, r, h, _ = gpu_solve(b, nx, ny, 32, (0, 0, 0, 0), ism.ISM_MIXED, nu=nu, sweeps_per_pass=k)
+    assert s == ism.ISM_OK and r <= 1e-8 and rel(p, p_ex) <= 1e-9
+
+
+def test_full_size_mixed_and_fp64_agree():
+    """2048^2, 32h: the benchmark's solve.  Both precisions reach 1e-8 and
+    agree; the oracle's FP64 residual of the mixed result confirms it."""
+    nx = ny = 2048
+    b = smooth_rhs(nx, ny, 0)
+    s1, pm, cm, rm, _, _ = gpu_solve(b, nx, ny, 32, (0, 0, 0, 0), ism.ISM_MIXED)
+    s2, pd, cd, rd, _, _ = gpu_solve(b, nx, ny, 32, (0, 0, 0, 0), ism.ISM_FP64)
+    assert s1 == ism.ISM_OK and s2 == ism.ISM_OK and rm <= 1e-8 and rd <= 1e-8
+    bb = b - b.mean()
+    assert np.linalg.norm(O.residual(pm, bb, (0, 0, 0, 0))) / np.linalg.norm(bb) <= 1.01e-8
+    assert rel(pm, pd) <= 1e-7
