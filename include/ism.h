@@ -164,6 +164,14 @@ ism_status ism_coarse_solve(ism_ctx *ctx, const void *rc, void *ec);
  * constant per block for ISM_COARSE_ACM). */
 ism_status ism_prolong_add(ism_ctx *ctx, const void *ec, void *p);
 
+/* Measurement helper: run `reps` smoothing passes of `sweeps` sweeps each
+ * (as ism_smooth, one fused pass per call for ISM_MIXED) on p, b and return
+ * in *us_per_pass the mean device time of one pass, taken with CUDA events
+ * on the library's work stream.  Synchronises.  No counterpart in the paper
+ * (Table 1 reports per-kernel wall times, Sec. 4.1). */
+ism_status ism_time_pass(ism_ctx *ctx, void *p, const void *b, int sweeps, int reps,
+                         double *us_per_pass);
+
 /* ---------------- projection time step (Sec. 2.2-2.3, Eq. 3-4) ---------- */
 
 /* Velocity boundary setup for proj_step.

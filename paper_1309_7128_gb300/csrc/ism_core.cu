@@ -861,3 +861,40 @@ extern "C" ism_status ism_prolong_add(ism_ctx *ctx, const void *ec, void *p)
     ISM_LAUNCH_CHECK(ctx);
     return ism_leave(ctx);
 }
+
+extern "C" ism_status ism_time_pass(ism_ctx *ctx, void *p, const void *b, int sweeps, int reps,
+                                    double *us_per_pass)
+{
+    if (!ctx || !p || !b || sweeps < 1 || reps < 1 || !us_per_pass) return ISM_ERR_ARG;
+    if (ctx->prec == ISM_MIXED && sweeps > SMAXK) return ISM_ERR_ARG;
+    cudaEvent_t e0, e1;
+    ISM_CUDA_TRY(cudaEventCreate(&e0));
+    ISM_CUDA_TRY(cudaEventCreate(&e1));
+    ism_status st = ism_smooth(ctx, p, b, sweeps);          // warm-up
+    if (st == ISM_OK) {
+        TRY(ism_enter(ctx));
+        ISM_CUDA_TRY(cudaEventRecord(e0, ctx->ws));
+        for (int r = 0; r < reps && st == ISM_OK; ++r) {
+            if (ctx->prec == ISM_FP64) {
+                st = launch_sweeps<double>(ctx, (double *)p, (const double *)b, sweeps, nullptr);
+            } else {
+                SweepArgs a = inner_args(ctx, ctx->st_k, (float *)p, ctx->e32[1], (const float *)b, nullptr, nullptr);
+                a.use_mean = 0;
+                a.K = sweeps;
+                a.q = r & 1;
+                st = launch_sweep32(ctx, a, false, false);
+            }
+        }
+        ISM_CUDA_TRY(cudaEventRecord(e1, ctx->ws));
+        ISM_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        ISM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        *us_per_pass = 1000.0 * ms / reps;
+        if (ctx->prec == ISM_MIXED && (reps & 1))
+            ISM_CUDA_TRY(cudaMemcpyAsync(p, ctx->e32[1], (size_t)ctx->n * 4, cudaMemcpyDeviceToDevice, ctx->ws));
+        ism_leave(ctx);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}

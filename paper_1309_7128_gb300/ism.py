@@ -57,6 +57,7 @@ _SIGS = {
     "proj_step": (_I, [_VP, _VP, _VP, _VP, _D, _D]),
     "ism_proj_tol": (_I, [_VP, _D, _I, _I]),
     "ism_last_dp": (_VP, [_VP]),
+    "ism_time_pass": (_I, [_VP, _VP, _VP, _I, _I, C.POINTER(C.c_double)]),
     "ism_solve_batched": (_I, [_I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _D, _I,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]),
 }
@@ -172,6 +173,13 @@ def ism_residual_restrict(ctx, p, b, rc):
     norms = (C.c_double * 2)()
     s = lib().ism_residual_restrict(ctx.handle, _ptr(p), _ptr(b), _ptr(rc), norms)
     return s, norms[0], norms[1]
+
+
+def ism_time_pass(ctx, p, b, sweeps, reps):
+    """Returns (status, mean device microseconds per smoothing pass)."""
+    us = C.c_double(0.0)
+    s = lib().ism_time_pass(ctx.handle, _ptr(p), _ptr(b), int(sweeps), int(reps), C.byref(us))
+    return s, us.value
 
 
 def ism_coarse_solve(ctx, rc, ec):
