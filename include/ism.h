@@ -156,6 +156,33 @@ ism_status ism_smooth(ism_ctx *ctx, void *p, const void *b, int sweeps);
 ism_status ism_residual_restrict(ism_ctx *ctx, const void *p, const void *b,
                                  void *rc, double *norms);
 
+/* ism_residual_restrict_noalloc -- the FP64 residual and restriction of
+ * ism_residual_restrict for callers that must not allocate device memory
+ * (a stream capture in progress, real-time loops that cannot take the
+ * synchronisation of cudaMalloc/cudaFree, hosts whose device memory belongs
+ * to their own arena).  The paper has no counterpart; this is a library
+ * convenience.  It needs no context and allocates nothing, on the device or
+ * the host: the per-block partial sums live in a fixed 768 KiB array
+ * compiled into the library (held by every GPU that loads it until the
+ * process exits).
+ *   nx, ny, coarsen, bc  as for ism_setup (bc: host, 4 ints);
+ *                        (nx/coarsen)*(ny/coarsen) must be <= 32768, else
+ *                        ISM_ERR_ARG (nothing launched).
+ *   p, b                 device, nx*ny doubles (read only).
+ *   rc                   device, (ny/m)*(nx/m) doubles: block sums of b - A_f p.
+ *   norms                device, 2 doubles: ||b - A_f p||_2 and sum(p).
+ *   stream               cudaStream_t (NULL = legacy default stream); the
+ *                        call is asynchronous on it.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call uses the same array, so calls whose kernels overlap on the GPU
+ * (different streams without ordering) race and give wrong results; calls
+ * on one stream, or otherwise ordered, are safe.  Each call overwrites all
+ * the entries it reads, so nothing needs clearing between calls. */
+ism_status ism_residual_restrict_noalloc(int nx, int ny, int coarsen, const int bc[4],
+                                         const double *p, const double *b, double *rc,
+                                         double *norms, void *stream);
+
 /* e_c = A_c^+ r_c (exact coarse solve on the mean-free subspace when all
  * faces are Neumann); rc, ec: device, (ny/m)*(nx/m) values of T. */
 ism_status ism_coarse_solve(ism_ctx *ctx, const void *rc, void *ec);

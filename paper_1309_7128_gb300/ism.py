@@ -58,6 +58,7 @@ _SIGS = {
     "ism_proj_tol": (_I, [_VP, _D, _I, _I]),
     "ism_last_dp": (_VP, [_VP]),
     "ism_time_pass": (_I, [_VP, _VP, _VP, _I, _I, C.POINTER(C.c_double)]),
+    "ism_residual_restrict_noalloc": (_I, [_I, _I, _I, C.POINTER(C.c_int), _VP, _VP, _VP, _VP, _VP]),
     "ism_solve_batched": (_I, [_I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _D, _I,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]),
 }
@@ -173,6 +174,14 @@ def ism_residual_restrict(ctx, p, b, rc):
     norms = (C.c_double * 2)()
     s = lib().ism_residual_restrict(ctx.handle, _ptr(p), _ptr(b), _ptr(rc), norms)
     return s, norms[0], norms[1]
+
+
+def ism_residual_restrict_noalloc(nx, ny, coarsen, bc, p, b, rc, norms, stream=None):
+    """Context-free FP64 residual + restriction; norms is a device tensor of
+    2 doubles.  Returns the status."""
+    bca = (C.c_int * 4)(*[int(x) for x in bc])
+    return lib().ism_residual_restrict_noalloc(int(nx), int(ny), int(coarsen), bca, _ptr(p), _ptr(b),
+                                               _ptr(rc), _ptr(norms), _stream(stream))
 
 
 def ism_time_pass(ctx, p, b, sweeps, reps):
