@@ -20,13 +20,16 @@
 // ================================================================ control
 
 __global__ void __launch_bounds__(256) k_ctl(IsmState *st, const double *partials, int nblk,
-                                             int nq, int mode)
+                                             int nq, int mode, unsigned long long cond)
 {
     __shared__ double S[ISM_NQ];
     if ((mode == CTL_FP64_AFTER || mode == CTL_OUTER_AFTER) && st->done) return;
     if (mode == CTL_INNER && st->inner_done) return;
     ctl_reduce(partials, nblk, nq, S);
-    if (threadIdx.x == 0) ctl_decide(st, S, mode);
+    if (threadIdx.x == 0) {
+        ctl_decide(st, S, mode);
+        ctl_set_condition(st, mode, cond);
+    }
 }
 
 // ================================================================ rhs preparation
@@ -53,11 +56,12 @@ __global__ void k_rhs_stats(const double *__restrict__ x, double *__restrict__ y
 
 // ================================================================ mixed-path outer kernels
 
-// FP64 refinement step.  UPDATE: p_out = p_in + e (e = inner iterate selected
-// by st->cur); then r = b - A_f p_out in FP64, r32 = (float) r, partials
+// FP64 refinement step on the ping-pong pair p0/p1 (st->c64 selects the
+// current iterate).  UPDATE: p_out = p_in + e (e = inner iterate selected by
+// st->cur); then r = b - A_f p_out in FP64, r32 = (float) r, partials
 // (||r||^2, sum p_out).  Grid (ceil(nx/256), ny).
 template <bool UPDATE>
-__global__ void k_refine(const double *__restrict__ p_in, double *__restrict__ p_out,
+__global__ void k_refine(double *p0, double *p1,
                          const float *e0, const float *e1, const double *__restrict__ b,
                          float *__restrict__ r32, double *partials, int nx, int ny, int bcmask,
                          const IsmState *st)
@@ -65,6 +69,8 @@ __global__ void k_refine(const double *__restrict__ p_in, double *__restrict__ p
     const int j = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float *__restrict__ e = (UPDATE && st->cur) ? e1 : e0;
+    const double *__restrict__ p_in = st->c64 ? p1 : p0;
+    double *__restrict__ p_out = st->c64 ? p0 : p1;
     double r2 = 0.0, ps = 0.0;
     if (i < nx) {
         const size_t idx = (size_t)j * nx + i;
@@ -90,10 +96,11 @@ __global__ void k_refine(const double *__restrict__ p_in, double *__restrict__ p
 }
 
 // out = in - mean (mean of the final iterate when all faces are Neumann);
-// zeros when the right-hand side vanished.
-__global__ void k_finalize(const double *__restrict__ in, double *__restrict__ out, long long n,
+// zeros when the right-hand side vanished.  in_alt replaces in when st->c64.
+__global__ void k_finalize(const double *in, const double *in_alt, double *out, long long n,
                            const IsmState *st, int sub_mean)
 {
+    if (in_alt && st->c64) in = in_alt;
     const double mu = sub_mean ? st->mean : 0.0;
     const bool zero = st->zero_rhs != 0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -126,7 +133,7 @@ static void default_options(ism_options *o)
     o->inner_tol = 1e-3;
     o->floor_mult = 4.0;
     o->check_every = 16;
-    o->use_graphs = 1;
+    o->use_graphs = 2;
 }
 
 static const double kPi = 3.14159265358979323846;
@@ -203,7 +210,9 @@ static void free_graphs(ism_ctx *ctx)
 {
     if (ctx->g_fp64) cudaGraphExecDestroy(ctx->g_fp64);
     if (ctx->g_inner) cudaGraphExecDestroy(ctx->g_inner);
-    ctx->g_fp64 = ctx->g_inner = nullptr;
+    if (ctx->gc_fp64) cudaGraphExecDestroy(ctx->gc_fp64);
+    if (ctx->gc_mixed) cudaGraphExecDestroy(ctx->gc_mixed);
+    ctx->g_fp64 = ctx->g_inner = ctx->gc_fp64 = ctx->gc_mixed = nullptr;
 }
 
 extern "C" void ism_destroy(ism_ctx *ctx)
@@ -374,6 +383,7 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     if (o->sweeps_per_pass < 1 || o->sweeps_per_pass > SMAXK || o->nu % o->sweeps_per_pass) return ISM_ERR_ARG;
     if (o->kind != ISM_COARSE_ISM && o->kind != ISM_COARSE_ACM) return ISM_ERR_ARG;
     if (o->max_outer < 1 || o->inner_max < 1 || o->check_every < 1 || o->check_every > 4096) return ISM_ERR_ARG;
+    if (o->use_graphs < 0 || o->use_graphs > 2) return ISM_ERR_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
     const int kind_changed = o->kind != ctx->opt.kind;
     cudaStreamSynchronize(ctx->ws);
@@ -430,19 +440,20 @@ static ism_status launch_coarse(ism_ctx *ctx, const T *rc, T *ec, T *Tm, const i
 
 template <typename T>
 static ism_status launch_resid(ism_ctx *ctx, const T *p, const T *b, T *rc, const int *skip,
-                               int ctl_mode = -1)
+                               int ctl_mode = -1, unsigned long long cond = 0)
 {
     const int th = std::min(256, ctx->m * ctx->m);
     k_resid<T><<<dim3(ctx->ncx, ctx->ncy), th, 0, ctx->ws>>>(p, b, rc, ctx->partials, ctx->nx,
                                                                 ctx->ny, ctx->m, ctx->bcmask, skip,
-                                                                ctx->st, ctl_mode);
+                                                                ctx->st, ctl_mode, cond);
     ISM_LAUNCH_CHECK(ctx);
     return ISM_OK;
 }
 
-static ism_status launch_ctl(ism_ctx *ctx, IsmState *st, int nblk, int nq, int mode)
+static ism_status launch_ctl(ism_ctx *ctx, IsmState *st, int nblk, int nq, int mode,
+                             unsigned long long cond = 0)
 {
-    k_ctl<<<1, 256, 0, ctx->ws>>>(st, ctx->partials, nblk, nq, mode);
+    k_ctl<<<1, 256, 0, ctx->ws>>>(st, ctx->partials, nblk, nq, mode, cond);
     ISM_LAUNCH_CHECK(ctx);
     return ISM_OK;
 }
@@ -555,8 +566,9 @@ static ism_status launch_sweep32(ism_ctx *ctx, SweepArgs a, bool prolong, bool r
 
 // ================================================================ host: cycles
 
-// One FP64 cycle; every kernel returns at once when st->done is set.
-static ism_status fp64_cycle(ism_ctx *ctx)
+// One FP64 cycle; every kernel returns at once when st->done is set.  cond:
+// while-node handle that the residual's control sets (0 outside such a node).
+static ism_status fp64_cycle(ism_ctx *ctx, unsigned long long cond = 0)
 {
     const int *skip = &ctx->st->done;
     TRY((launch_coarse<double, false>(ctx, ctx->rc64, ctx->ec64, ctx->T64, skip)));
@@ -565,7 +577,7 @@ static ism_status fp64_cycle(ism_ctx *ctx)
         ctx->opt.kind, ctx->st, ctx->singular, skip);
     ISM_LAUNCH_CHECK(ctx);
     TRY(launch_sweeps<double>(ctx, ctx->p64[0], ctx->b64, ctx->opt.nu, skip));
-    return launch_resid<double>(ctx, ctx->p64[0], ctx->b64, ctx->rc64, skip, CTL_FP64_AFTER);
+    return launch_resid<double>(ctx, ctx->p64[0], ctx->b64, ctx->rc64, skip, CTL_FP64_AFTER, cond);
 }
 
 static SweepArgs inner_args(ism_ctx *ctx, IsmState *st, float *e0, float *e1, const float *b,
@@ -579,6 +591,7 @@ static SweepArgs inner_args(ism_ctx *ctx, IsmState *st, float *e0, float *e1, co
     a.bcmask = ctx->bcmask; a.kind = ctx->opt.kind; a.K = ctx->opt.sweeps_per_pass;
     a.q = 0; a.use_mean = ctx->singular; a.ctl_mode = -1;
     a.H = a.Hc = a.TW = a.TH = 0;
+    a.cond = 0;
     return a;
 }
 
@@ -586,13 +599,14 @@ static SweepArgs inner_args(ism_ctx *ctx, IsmState *st, float *e0, float *e1, co
 // coarse solve (from the partial block sums of the previous pass), then nu/K
 // fused passes (the first adds the prolongation, the last computes the
 // residual and its restriction), then the control kernel.
-static ism_status inner_cycle(ism_ctx *ctx)
+static ism_status inner_cycle(ism_ctx *ctx, unsigned long long cond = 0)
 {
     const int *skip = &ctx->st->inner_done;
     TRY((launch_coarse<float, true>(ctx, ctx->rcpart, ctx->ec32, ctx->T32, skip)));
     const int npass = ctx->opt.nu / ctx->opt.sweeps_per_pass;
     SweepArgs a = inner_args(ctx, ctx->st, ctx->e32[0], ctx->e32[1], ctx->r32, skip, &ctx->st->cur);
     a.ctl_mode = CTL_INNER;
+    a.cond = cond;
     for (int q = 0; q < npass; ++q) {
         a.q = q;
         TRY(launch_sweep32(ctx, a, q == 0, q == npass - 1));
@@ -608,7 +622,7 @@ static ism_status run_chunks(ism_ctx *ctx, bool inner, int max_chunks)
     cudaGraphExec_t *gx = inner ? &ctx->g_inner : &ctx->g_fp64;
     int *glen = inner ? &ctx->g_inner_len : &ctx->g_fp64_len;
     for (int it = 0; it < max_chunks; ++it) {
-        if (ctx->opt.use_graphs) {
+        if (ctx->opt.use_graphs >= 1) {
             if (!*gx) {
                 cudaGraph_t g;
                 const long long l0 = ctx->launches;
@@ -670,14 +684,158 @@ static ism_status read_state(ism_ctx *ctx)
     return ISM_OK;
 }
 
+// ---------------------------------------------------------------- device-side loops
+//
+// use_graphs = 2: the whole iteration is one CUDA graph.  A while node
+// repeats the cycle; its condition is set by the control point fused into the
+// last kernel of the cycle (cudaGraphSetConditional), so a solve needs one
+// graph launch and one host synchronisation.  The mixed path nests the
+// single-precision cycle loop inside the refinement loop.
+
+template <typename F>
+static ism_status capture_into(ism_ctx *ctx, cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
+                               F fn, cudaGraphNode_t *last)
+{
+    ISM_CUDA_TRY(cudaStreamBeginCaptureToGraph(ctx->ws, g, deps, nullptr, ndeps,
+                                               cudaStreamCaptureModeThreadLocal));
+    ism_status s = fn();
+    if (s == ISM_OK && last) {
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t *d = nullptr;
+        size_t nd = 0;
+        if (cudaStreamGetCaptureInfo(ctx->ws, &cs, nullptr, nullptr, &d, nullptr, &nd) != cudaSuccess || nd != 1)
+            s = ISM_ERR_CUDA;
+        else
+            *last = d[0];
+    }
+    cudaGraph_t out = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->ws, &out);
+    if (s != ISM_OK) return s;
+    return e == cudaSuccess ? ISM_OK : ISM_ERR_CUDA;
+}
+
+static inline ism_status ISM_CUDA_OK(cudaError_t e) { return e == cudaSuccess ? ISM_OK : ISM_ERR_CUDA; }
+
+static ism_status add_while_handle(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
+                                   cudaGraphConditionalHandle h, cudaGraphNode_t *node, cudaGraph_t *body)
+{
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    ISM_CUDA_TRY(cudaGraphAddNode(node, g, deps, nullptr, ndeps, &p));
+    *body = p.conditional.phGraph_out[0];
+    return ISM_OK;
+}
+
+static ism_status add_while(cudaGraph_t g, const cudaGraphNode_t *deps, size_t ndeps,
+                            cudaGraphConditionalHandle *h, cudaGraphNode_t *node, cudaGraph_t *body)
+{
+    ISM_CUDA_TRY(cudaGraphConditionalHandleCreate(h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = *h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    ISM_CUDA_TRY(cudaGraphAddNode(node, g, deps, nullptr, ndeps, &p));
+    *body = p.conditional.phGraph_out[0];
+    return ISM_OK;
+}
+
+// First step of an inner solve: e = 0 and the restriction of its residual r
+// (a pass with no sweeps).
+static ism_status inner_init(ism_ctx *ctx)
+{
+    k_zero<<<4 * 152, 256, 0, ctx->ws>>>(ctx->e32[0], ctx->n);
+    ISM_LAUNCH_CHECK(ctx);
+    k_zero<<<64, 256, 0, ctx->ws>>>(ctx->rcpart, (long long)ctx->ncx * ctx->ncy * 4);
+    ISM_LAUNCH_CHECK(ctx);
+    SweepArgs a = inner_args(ctx, ctx->st, ctx->e32[0], ctx->e32[1], ctx->r32, nullptr, nullptr);
+    a.K = 0;
+    return launch_sweep32(ctx, a, false, true);
+}
+
+static ism_status refine_update(ism_ctx *ctx, unsigned long long cond)
+{
+    const dim3 rg = row_grid(ctx->nx, ctx->ny, 256);
+    k_refine<true><<<rg, 256, 0, ctx->ws>>>(ctx->p64[0], ctx->p64[1], ctx->e32[0], ctx->e32[1],
+                                            ctx->b64, ctx->r32, ctx->partials, ctx->nx, ctx->ny,
+                                            ctx->bcmask, ctx->st);
+    ISM_LAUNCH_CHECK(ctx);
+    return launch_ctl(ctx, ctx->st, rg.x * rg.y, 2, CTL_OUTER_AFTER, cond);
+}
+
+static ism_status build_cond_fp64(ism_ctx *ctx)
+{
+    cudaGraph_t g;
+    ISM_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle h;
+    cudaGraphNode_t n;
+    cudaGraph_t body;
+    const long long l0 = ctx->launches;
+    ism_status s = add_while(g, nullptr, 0, &h, &n, &body);
+    if (s == ISM_OK) s = capture_into(ctx, body, nullptr, 0, [&]() { return fp64_cycle(ctx, h); }, nullptr);
+    if (s == ISM_OK && cudaGraphInstantiate(&ctx->gc_fp64, g, 0) != cudaSuccess) s = ISM_ERR_CUDA;
+    cudaGraphDestroy(g);
+    ctx->g_fp64_len = (int)(ctx->launches - l0);   // launches per cycle
+    ctx->launches = l0;
+    if (s != ISM_OK) { cudaGetLastError(); ctx->gc_fp64 = nullptr; }
+    return s;
+}
+
+static ism_status build_cond_mixed(ism_ctx *ctx)
+{
+    cudaGraph_t g;
+    ISM_CUDA_TRY(cudaGraphCreate(&g, 0));
+    cudaGraphConditionalHandle ho, hi;
+    cudaGraphNode_t no, ni, last;
+    cudaGraph_t bo, bi;
+    const long long l0 = ctx->launches;
+    ism_status s = add_while(g, nullptr, 0, &ho, &no, &bo);
+    // outer body: inner init (which arms the inner loop), then the inner loop,
+    // then the FP64 update + control.  The inner handle lives on the outer
+    // body, so it exists before the capture that arms it.
+    if (s == ISM_OK) s = ISM_CUDA_OK(cudaGraphConditionalHandleCreate(&hi, bo, 1, cudaGraphCondAssignDefault));
+    if (s == ISM_OK)
+        s = capture_into(ctx, bo, nullptr, 0, [&]() {
+            ism_status r = inner_init(ctx);
+            if (r != ISM_OK) return r;
+            k_arm_condition<<<1, 1, 0, ctx->ws>>>(hi);
+            ISM_LAUNCH_CHECK(ctx);
+            return ISM_OK;
+        }, &last);
+    if (s == ISM_OK) s = add_while_handle(bo, &last, 1, hi, &ni, &bi);
+    const long long l1 = ctx->launches;
+    if (s == ISM_OK) s = capture_into(ctx, bi, nullptr, 0, [&]() { return inner_cycle(ctx, hi); }, nullptr);
+    const long long l2 = ctx->launches;
+    if (s == ISM_OK) s = capture_into(ctx, bo, &ni, 1, [&]() { return refine_update(ctx, ho); }, nullptr);
+    if (s == ISM_OK && cudaGraphInstantiate(&ctx->gc_mixed, g, 0) != cudaSuccess) s = ISM_ERR_CUDA;
+    cudaGraphDestroy(g);
+    ctx->g_inner_len = (int)(l2 - l1);                          // launches per inner cycle
+    ctx->g_fp64_len = (int)((ctx->launches - l0) - (l2 - l1));  // launches per refinement iteration
+    ctx->launches = l0;
+    if (s != ISM_OK) { cudaGetLastError(); ctx->gc_mixed = nullptr; }
+    return s;
+}
+
 static ism_status solve_fp64(ism_ctx *ctx)
 {
     TRY(launch_resid<double>(ctx, ctx->p64[0], ctx->b64, ctx->rc64, nullptr, CTL_FP64_INIT));
     TRY(read_state(ctx));
-    const int C = ctx->opt.check_every;
-    const int max_chunks = ctx->st_host->max_cycles / C + 2;
-    if (!ctx->st_host->done) TRY(run_chunks(ctx, false, max_chunks));
-    k_finalize<<<4 * 152, 256, 0, ctx->ws>>>(ctx->p64[0], ctx->p64[0], ctx->n, ctx->st, ctx->singular);
+    if (!ctx->st_host->done) {
+        if (ctx->opt.use_graphs == 2) {
+            if (!ctx->gc_fp64) TRY(build_cond_fp64(ctx));
+            const int c0 = ctx->st_host->cycles;
+            ISM_CUDA_TRY(cudaGraphLaunch(ctx->gc_fp64, ctx->ws));
+            TRY(read_state(ctx));
+            ctx->launches += (long long)(ctx->st_host->cycles - c0 + 1) * ctx->g_fp64_len;
+        } else {
+            const int C = ctx->opt.check_every;
+            TRY(run_chunks(ctx, false, ctx->st_host->max_cycles / C + 2));
+        }
+    }
+    k_finalize<<<4 * 152, 256, 0, ctx->ws>>>(ctx->p64[0], nullptr, ctx->p64[0], ctx->n, ctx->st, ctx->singular);
     ISM_LAUNCH_CHECK(ctx);
     return read_state(ctx);
 }
@@ -686,35 +844,29 @@ static ism_status solve_mixed(ism_ctx *ctx)
 {
     const dim3 rg = row_grid(ctx->nx, ctx->ny, 256);
     const int nrb = rg.x * rg.y;
-    int c64 = 0;
-    k_refine<false><<<rg, 256, 0, ctx->ws>>>(ctx->p64[0], nullptr, ctx->e32[0], ctx->e32[1],
+    k_refine<false><<<rg, 256, 0, ctx->ws>>>(ctx->p64[0], ctx->p64[1], ctx->e32[0], ctx->e32[1],
                                              ctx->b64, ctx->r32, ctx->partials, ctx->nx, ctx->ny,
                                              ctx->bcmask, ctx->st);
     ISM_LAUNCH_CHECK(ctx);
     TRY(launch_ctl(ctx, ctx->st, nrb, 2, CTL_OUTER_INIT));
-    const int C = ctx->opt.check_every;
-    for (;;) {
+    TRY(read_state(ctx));
+    if (!ctx->st_host->done && ctx->opt.use_graphs == 2) {
+        if (!ctx->gc_mixed) TRY(build_cond_mixed(ctx));
+        ISM_CUDA_TRY(cudaGraphLaunch(ctx->gc_mixed, ctx->ws));
         TRY(read_state(ctx));
-        if (ctx->st_host->done) break;
-        // inner solve of A e = r32 from e = 0
-        ISM_CUDA_TRY(cudaMemsetAsync(ctx->e32[0], 0, (size_t)ctx->n * sizeof(float), ctx->ws));
-        ISM_CUDA_TRY(cudaMemsetAsync(ctx->rcpart, 0, (size_t)ctx->ncx * ctx->ncy * 16, ctx->ws));
-        {   // restriction of r (the residual of e = 0): a pass with no sweeps
-            SweepArgs a = inner_args(ctx, ctx->st, ctx->e32[0], ctx->e32[1], ctx->r32, nullptr, nullptr);
-            a.K = 0;
-            TRY(launch_sweep32(ctx, a, false, true));
+        ctx->launches += (long long)ctx->st_host->cycles * ctx->g_inner_len +
+                         (long long)ctx->st_host->outer * ctx->g_fp64_len;
+    } else {
+        const int C = ctx->opt.check_every;
+        while (!ctx->st_host->done) {
+            TRY(inner_init(ctx));
+            const int max_chunks = std::min(ctx->opt.inner_max, ctx->st_host->max_cycles) / C + 2;
+            TRY(run_chunks(ctx, true, max_chunks));
+            TRY(refine_update(ctx, 0));
+            TRY(read_state(ctx));
         }
-        const int max_chunks = std::min(ctx->opt.inner_max, ctx->st_host->max_cycles) / C + 2;
-        TRY(run_chunks(ctx, true, max_chunks));
-        // p <- p + e, r = b - A p (FP64)
-        k_refine<true><<<rg, 256, 0, ctx->ws>>>(ctx->p64[c64], ctx->p64[c64 ^ 1], ctx->e32[0],
-                                                ctx->e32[1], ctx->b64, ctx->r32, ctx->partials,
-                                                ctx->nx, ctx->ny, ctx->bcmask, ctx->st);
-        ISM_LAUNCH_CHECK(ctx);
-        c64 ^= 1;
-        TRY(launch_ctl(ctx, ctx->st, nrb, 2, CTL_OUTER_AFTER));
     }
-    k_finalize<<<4 * 152, 256, 0, ctx->ws>>>(ctx->p64[c64], ctx->p64[0], ctx->n, ctx->st, ctx->singular);
+    k_finalize<<<4 * 152, 256, 0, ctx->ws>>>(ctx->p64[0], ctx->p64[1], ctx->p64[0], ctx->n, ctx->st, ctx->singular);
     ISM_LAUNCH_CHECK(ctx);
     return read_state(ctx);
 }

@@ -33,6 +33,7 @@ struct IsmState {
     double mean_e;     // mixed: mean of the inner iterate
     double r32norm;    // mixed: ||r|| of the current inner right-hand side
     double rin, enorm; // mixed: latest inner residual and iterate norms
+    int c64;           // mixed: which FP64 buffer holds the outer iterate
     unsigned int ticket; // CTAs finished in the current fused-control kernel
     double hist[ISM_HMAX];
 };
@@ -74,7 +75,8 @@ struct ism_ctx {
     struct SweepPlan { int gx, gy, ix0, ix1, iy0, iy1, nedge; int2 *edge; } plans[9][2];
 
     // CUDA graphs of a chunk of cycles
-    cudaGraphExec_t g_fp64, g_inner;
+    cudaGraphExec_t g_fp64, g_inner;       // chunks of cycles (use_graphs = 1)
+    cudaGraphExec_t gc_fp64, gc_mixed;     // whole solve with device-side loops (use_graphs = 2)
     int g_fp64_len, g_inner_len;
 
     // last solve

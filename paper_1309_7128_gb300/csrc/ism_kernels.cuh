@@ -129,7 +129,10 @@ __device__ __forceinline__ void ctl_decide(IsmState *st, const double *S, int mo
         const bool after = (mode == CTL_FP64_AFTER || mode == CTL_OUTER_AFTER);
         int k;
         if (fp64) { if (after) st->cycles++; k = st->cycles; }
-        else { if (after) st->outer++; k = st->outer; }
+        else {
+            if (after) { st->outer++; st->c64 ^= 1; }    // the refinement wrote the other buffer
+            k = st->outer;
+        }
         const double rel = st->bnorm > 0.0 ? sqrt(S[0]) / st->bnorm : 0.0;
         st->relres = rel;
         st->mean = S[1] * st->inv_n;
@@ -167,11 +170,21 @@ __device__ __forceinline__ void ctl_decide(IsmState *st, const double *S, int mo
     }
 }
 
+// Loop condition of a CUDA-graph while node driven by a control point: keep
+// iterating while the phase is not finished.
+__device__ __forceinline__ void ctl_set_condition(const IsmState *st, int mode, unsigned long long cond)
+{
+    if (!cond) return;
+    const unsigned run = (mode == CTL_INNER) ? (st->inner_done ? 0u : 1u) : (st->done ? 0u : 1u);
+    cudaGraphSetConditional((cudaGraphConditionalHandle)cond, run);
+}
+
 // Last-CTA-done control: every CTA has written its partial sums; the CTA
 // that finishes last reduces them in fixed order and applies the control
-// decision, then re-arms the ticket.  No CTA waits for another.
+// decision (and the loop condition of the enclosing graph node, when cond is
+// nonzero), then re-arms the ticket.  No CTA waits for another.
 __device__ __forceinline__ void ctl_last_block(IsmState *st, const double *partials, int nblk,
-                                               int nq, int mode)
+                                               int nq, int mode, unsigned long long cond = 0)
 {
     __shared__ int am_last;
     __shared__ double S[ISM_NQ];
@@ -185,7 +198,22 @@ __device__ __forceinline__ void ctl_last_block(IsmState *st, const double *parti
     if (threadIdx.x == 0) {
         ctl_decide(st, S, mode);
         st->ticket = 0;
+        ctl_set_condition(st, mode, cond);
     }
+}
+
+static __global__ void k_zero(float *__restrict__ x, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        x[i] = 0.0f;
+}
+
+// Arm a graph while node: a handle created on a body graph starts each
+// execution of that body with no defined value, so the enclosing body sets it.
+static __global__ void k_arm_condition(unsigned long long cond)
+{
+    cudaGraphSetConditional((cudaGraphConditionalHandle)cond, 1u);
 }
 
 // ----------------------------------------------------------------- interpolation
@@ -254,7 +282,7 @@ __global__ void k_rbgs_colour(T *__restrict__ p, const T *__restrict__ b, int nx
 template <typename T>
 __global__ void k_resid(const T *__restrict__ p, const T *__restrict__ b, T *__restrict__ rc,
                         double *partials, int nx, int ny, int m, int bcmask, const int *skip,
-                        IsmState *ctl_st = nullptr, int ctl_mode = -1)
+                        IsmState *ctl_st = nullptr, int ctl_mode = -1, unsigned long long cond = 0)
 {
     if (skip && *skip) return;
     const int I = blockIdx.x, J = blockIdx.y, ncx = gridDim.x;
@@ -288,7 +316,7 @@ __global__ void k_resid(const T *__restrict__ p, const T *__restrict__ b, T *__r
     }
     double v[3] = {(double)r2, (double)ps, (double)p2};
     block_partials<3>(v, partials, ncx * gridDim.y, J * ncx + I);
-    if (ctl_mode >= 0) ctl_last_block(ctl_st, partials, ncx * gridDim.y, 3, ctl_mode);
+    if (ctl_mode >= 0) ctl_last_block(ctl_st, partials, ncx * gridDim.y, 3, ctl_mode, cond);
 }
 
 // p = p - mean + P e_c  (mean: state field when use_mean, else 0)
@@ -324,8 +352,15 @@ __device__ __forceinline__ void row_times_matrix(int n_out, int n_in, F term, T 
         const int o = t % n_out, c = t / n_out;
         const int j0 = c * chunk, j1 = min(n_in, j0 + chunk);
         T s = (T)0;
-#pragma unroll 4
-        for (int j = j0; j < j1; ++j) s += term(j, o);
+        int j = j0;
+        for (; j + 8 <= j1; j += 8) {          // 8 independent terms in flight
+            T u[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) u[q] = term(j + q, o);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s += u[q];
+        }
+        for (; j < j1; ++j) s += term(j, o);
         part[c * n_out + o] = s;
     }
     __syncthreads();

@@ -199,7 +199,8 @@ static ism_status ensure_proj_buffers(ism_ctx *ctx)
 }
 
 // defined in ism_core.cu
-__global__ void k_ctl(IsmState *st, const double *partials, int nblk, int nq, int mode);
+__global__ void k_ctl(IsmState *st, const double *partials, int nblk, int nq, int mode,
+                      unsigned long long cond);
 __global__ void k_rhs_stats(const double *__restrict__ x, double *__restrict__ y, long long n,
                             const IsmState *st, int mode, int sub_mean, double *partials);
 
@@ -233,11 +234,11 @@ extern "C" ism_status proj_step(ism_ctx *ctx, float *u, float *v, float *p, doub
     const dim3 dg((nx + 255) / 256, ny);
     k_divergence<<<dg, 256, 0, ctx->ws>>>(ctx->us, ctx->vs, ctx->b64, nx, ny, ctx->h, dt, ctx->partials);
     ISM_LAUNCH_CHECK(ctx);
-    k_ctl<<<1, 256, 0, ctx->ws>>>(ctx->st, ctx->partials, dg.x * dg.y, 1, 0 /*CTL_RHS_MEAN*/);
+    k_ctl<<<1, 256, 0, ctx->ws>>>(ctx->st, ctx->partials, dg.x * dg.y, 1, 0 /*CTL_RHS_MEAN*/, 0);
     ISM_LAUNCH_CHECK(ctx);
     k_rhs_stats<<<4 * 152, 256, 0, ctx->ws>>>(ctx->b64, ctx->b64, ctx->n, ctx->st, 1, ctx->singular, ctx->partials);
     ISM_LAUNCH_CHECK(ctx);
-    k_ctl<<<1, 256, 0, ctx->ws>>>(ctx->st, ctx->partials, 4 * 152, 1, 1 /*CTL_RHS_NORM*/);
+    k_ctl<<<1, 256, 0, ctx->ws>>>(ctx->st, ctx->partials, 4 * 152, 1, 1 /*CTL_RHS_NORM*/, 0);
     ISM_LAUNCH_CHECK(ctx);
 
     // initial guess: previous increment (warm start) or zero

@@ -59,6 +59,7 @@ struct SweepArgs {
     int gx, gy;               // tile grid
     int ix0, iy0;             // interior launch: tile = block + (ix0, iy0)
     const int2 *edge_tiles;   // edge launch: tile = edge_tiles[block]
+    unsigned long long cond;  // graph while-node handle set by the control, or 0
 };
 
 // Row halo 2K (+1 for the residual); the column halo is rounded up to a
@@ -68,9 +69,13 @@ __host__ __device__ inline int sweep_halo_cols(int K, bool resid) { return (swee
 __host__ __device__ inline int sweep_tile_w(int K, bool resid) { return SRW - 2 * sweep_halo_cols(K, resid); }
 __host__ __device__ inline int sweep_tile_h(int K, bool resid) { return SRH - 2 * sweep_halo(K, resid); }
 
-// b of this thread's 4 cells of a row, stored as (q0, q2, q1, q3) so the two
-// cells of one colour are adjacent
-__device__ __forceinline__ int bperm(int q) { return (q & 1) * 2 + (q >> 1); }
+// b in shared memory: per region row two planes of 32 float2, plane 0 holding
+// (b_q0, b_q2) and plane 1 (b_q1, b_q3) of each lane's columns 4l+q, so the
+// two cells of one colour are one conflict-free 8-byte load.
+__device__ __forceinline__ const float2 *bplane(const float *row, int qp, int lane)
+{
+    return reinterpret_cast<const float2 *>(row + qp * 64) + lane;
+}
 
 // Divisor contribution of the south / north faces for global row y.
 __device__ __forceinline__ float row_adj(int y, int ny, int bcmask)
@@ -97,14 +102,14 @@ __device__ __forceinline__ float edge_inv(const EdgeRows &er, const float (&rq)[
 // Half-sweep of colour parity PAR over the warp's rows; EDGE selects the
 // boundary-aware update (out-of-domain cells are never updated).
 template <int PAR, bool EDGE>
-__device__ __forceinline__ void half_sweep(float (&P)[SRR + 2][SNC], const float *bs,
+__device__ __forceinline__ void half_sweep(float (&P)[SRR + 2][SNC], const float *bs, const int lane,
                                            const float (&idq)[SNC], const float (&rq)[SNC],
                                            const bool colin, const EdgeRows &er)
 {
 #pragma unroll
     for (int r = 0; r < SRR; ++r) {
         const int qp = PAR ^ (r & 1);            // which pair of columns has the active colour
-        const float2 bb = *reinterpret_cast<const float2 *>(bs + r * SRW + 2 * qp);
+        const float2 bb = *bplane(bs + r * SRW, qp, lane);
         if (qp == 0) {
             const float left = __shfl_up_sync(FULLMASK, P[r + 1][3], 1);
             float s0 = ((left + P[r + 1][1]) + P[r][0]) + P[r + 2][0];
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(STHREADS, 2) k_sweep32(SweepArgs a)
     const int in = ((a.curp ? *a.curp : 0) + a.q) & 1;
     const float *__restrict__ pin = in ? a.e1 : a.e0;
     float *__restrict__ pout = in ? a.e0 : a.e1;
-    float *bs = bsm + ry0 * SRW + SNC * lane;   // this thread's b, row stride SRW
+    float *bs = bsm + ry0 * SRW;           // this warp's b rows (two colour planes per row)
     // nx % 4 == 0 and cx % 4 == 0: a thread's 4 columns are all in or all out
     const bool colin = (unsigned)cx < (unsigned)nx;
     const bool colvalid = colin && (SNC * lane >= Hc) && (SNC * lane < Hc + TW);
@@ -278,15 +283,17 @@ __global__ void __launch_bounds__(STHREADS, 2) k_sweep32(SweepArgs a)
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if ((unsigned)y < (unsigned)ny && colin) v = *reinterpret_cast<const float4 *>(a.b + (size_t)y * nx + cx);
         if (!edge) { v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f; }
-        *reinterpret_cast<float4 *>(bs + r * SRW) = make_float4(v.x, v.z, v.y, v.w);
+        float2 *row = reinterpret_cast<float2 *>(bs + r * SRW);
+        row[lane] = make_float2(v.x, v.z);
+        row[32 + lane] = make_float2(v.y, v.w);
     }
 
     // 2. 2K half-sweeps, red ((x+y) even) first
     const int base = (x0 + y0 + ry0) & 1;      // colour parity of (column 0, row 0) of this warp
     for (int s = 0; s < 2 * a.K; ++s) {
         const int par = (s & 1) ^ base;        // active colour c = s & 1: q-parity = c ^ base ^ (r & 1)
-        if (par == 0) half_sweep<0, EDGE>(P, bs, idq, rq, colin, er);
-        else half_sweep<1, EDGE>(P, bs, idq, rq, colin, er);
+        if (par == 0) half_sweep<0, EDGE>(P, bs, lane, idq, rq, colin, er);
+        else half_sweep<1, EDGE>(P, bs, lane, idq, rq, colin, er);
         exchange_rows(P, xch, s & 1, w, lane);
     }
 
@@ -314,8 +321,8 @@ __global__ void __launch_bounds__(STHREADS, 2) k_sweep32(SweepArgs a)
             const float right = __shfl_down_sync(FULLMASK, P[r + 1][0], 1);
             const int rr = ry0 + r, y = y0 + rr;
             const bool ok = colvalid && rr >= H && rr < H + TH && (unsigned)y < (unsigned)ny;
-            const float4 bv = *reinterpret_cast<const float4 *>(bs + r * SRW);
-            const float bq[SNC] = {bv.x, bv.z, bv.y, bv.w};
+            const float2 b02 = *bplane(bs + r * SRW, 0, lane), b13 = *bplane(bs + r * SRW, 1, lane);
+            const float bq[SNC] = {b02.x, b13.x, b02.y, b13.y};
             const float ra = row_adj(y, ny, a.bcmask);
             float rowsum = 0.f;
 #pragma unroll
@@ -371,7 +378,7 @@ __global__ void __launch_bounds__(STHREADS, 2) k_sweep32(SweepArgs a)
             for (int k = 0; k < SNW; ++k) t += red[threadIdx.x][k];
             a.partials[(size_t)threadIdx.x * nblk + by * a.gx + bx] = t;
         }
-        if (a.ctl_mode >= 0) ctl_last_block(a.st, a.partials, nblk, 3, a.ctl_mode);
+        if (a.ctl_mode >= 0) ctl_last_block(a.st, a.partials, nblk, 3, a.ctl_mode, a.cond);
     }
 }
 

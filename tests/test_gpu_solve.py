@@ -117,7 +117,7 @@ def test_nonfinite_rhs_is_reported_and_p_untouched():
         assert np.array_equal(p, p0)
 
 
-@pytest.mark.parametrize("use_graphs", [0, 1])
+@pytest.mark.parametrize("use_graphs", [0, 1, 2])
 @pytest.mark.parametrize("check_every", [1, 7])
 def test_loop_control_variants_agree(use_graphs, check_every):
     nx = ny = 128
