@@ -50,11 +50,14 @@ def cavity_dt(n=N_GRID, nu=RE_NU, lid=LID):
     return h, 0.9 * min(0.4 * h / lid, 0.25 * h * h / nu, 2.0 * nu / lid ** 2)
 
 
-def workload_config():
-    return {"workload": "lid-driven cavity 2048x2048 MAC, Re=1000, ISM 32h (64x64 coarse), "
-                        "FP32 cycles in FP64 refinement to rel. residual 1e-8",
-            "nx": N_GRID, "ny": N_GRID, "coarsen": COARSEN, "nu_sweeps": 8, "sweeps_per_pass": 4,
-            "tol": TOL, "l2": "flushed between timed steps (512 MB write)"}
+def workload_config(tuned=None):
+    cfg = {"workload": "lid-driven cavity 2048x2048 MAC, Re=1000, ISM 32h (64x64 coarse), "
+                       "FP32 cycles in FP64 refinement to rel. residual 1e-8",
+           "nx": N_GRID, "ny": N_GRID, "coarsen": COARSEN, "tol": TOL,
+           "l2": "flushed between timed steps (512 MB write)"}
+    if tuned:
+        cfg.update(tuned)
+    return cfg
 
 
 # ------------------------------------------------------------------ distributed
@@ -242,11 +245,31 @@ def run_ours(args):
     def make_ctx(prec):
         s, ctx = ism.ism_setup(n, n, h, (0, 0, 0, 0), COARSEN, prec)
         ism.check(s, "ism_setup")
+        o = ism.ism_get_options(ctx)
+        o.use_graphs = args.use_graphs
+        ism.check(ism.ism_set_options(ctx, o), "ism_set_options")
         ism.check(ism.ism_set_flow(ctx, cav, (0, 0, 0, LID), None, 1.0), "ism_set_flow")
         ism.check(ism.ism_proj_tol(ctx, TOL, 1_000_000, False), "ism_proj_tol")
         return ctx
 
-    ctx = make_ctx(ism.ISM_MIXED)
+    # autotune sweeps per cycle / per fused pass on a smooth right-hand side (untimed)
+    from synth.inputs import smooth_rhs
+    rhs_tune = torch.tensor(smooth_rhs(n, n, 0), dtype=torch.float64, device=dev)
+
+    def tuned_ctx(prec):
+        c = make_ctx(prec)
+        if args.no_autotune:
+            o = ism.ism_get_options(c)
+            o.nu = args.nu if prec == ism.ISM_MIXED else args.nu_fp64
+            o.sweeps_per_pass = args.sweeps_per_pass if prec == ism.ISM_MIXED else 4
+            ism.check(ism.ism_set_options(c, o), "ism_set_options")
+        else:
+            s, o = ism.ism_autotune(c, rhs_tune, TOL, 1_000_000)
+            ism.check(s, "ism_autotune")
+        return c, {"nu_sweeps": o.nu, "sweeps_per_pass": o.sweeps_per_pass,
+                   "autotuned": not args.no_autotune}
+
+    ctx, opt_mixed = tuned_ctx(ism.ISM_MIXED)
     u = torch.zeros((n, n + 1), dtype=torch.float32, device=dev)
     v = torch.zeros((n + 1, n), dtype=torch.float32, device=dev)
     p = torch.zeros((n, n), dtype=torch.float32, device=dev)
@@ -291,7 +314,7 @@ def run_ours(args):
     value = world * args.steps / (total_ms / 1000.0)
 
     # ---- FP64 ISM on the same steps (state copied from the mixed run)
-    ctx64 = make_ctx(ism.ISM_FP64)
+    ctx64, opt_fp64 = tuned_ctx(ism.ISM_FP64)
     u64, v64, p64 = u.clone(), v.clone(), p.clone()
     fp64_ms, fp64_cycles = [], []
     for _ in range(args.fp64_steps):
@@ -312,7 +335,8 @@ def run_ours(args):
     # ---- dominant kernel: the fused 4-sweep single-precision pass, timed alone
     b32 = torch.randn((n, n), dtype=torch.float32, device=dev) * 1e-6
     e32 = torch.zeros((n, n), dtype=torch.float32, device=dev)
-    s, us_pass = ism.ism_time_pass(ctx, e32, b32, 4, 50)
+    kpass = opt_mixed["sweeps_per_pass"]
+    s, us_pass = ism.ism_time_pass(ctx, e32, b32, kpass, 50)
     ism.check(s, "ism_time_pass")
     bytes_pass = 12.0 * n * n                    # read p and b, write p (4 B each)
     achieved = bytes_pass / (us_pass * 1e-6) / 1e9
@@ -320,7 +344,7 @@ def run_ours(args):
     traffic = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "k_sweep32: fused 4-sweep red-black pass (interior + edge launches)",
+                "kernel": f"k_sweep32: fused {kpass}-sweep red-black pass (interior + edge launches)",
                 "us_per_launch": round(us_pass, 2), "algorithmic_bytes_per_launch": bytes_pass,
                 "peak_source": peak_kind,
                 "note": "2048^2 single-precision fields are L2-resident between passes"}
@@ -355,7 +379,8 @@ def run_ours(args):
     out = {"metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-           "data": "synthetic (cavity from rest)", "config": workload_config(),
+           "data": "synthetic (cavity from rest)",
+           "config": workload_config({"mixed_options": opt_mixed, "fp64_options": opt_fp64, "use_graphs": args.use_graphs}),
            "fp64": {"value": round(fp64_value, 3), "unit": UNIT, "steps": args.fp64_steps,
                     "ms_per_step": round(fp64_total / args.fp64_steps, 3),
                     "cycles_per_solve": fp64_cycles},
@@ -414,6 +439,14 @@ def main():
     ap.add_argument("--cpu-cycles", type=int, default=12)
     ap.add_argument("--ref-cycles", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use --nu / --sweeps-per-pass / --nu-fp64 instead of ism_autotune")
+    ap.add_argument("--nu", type=int, default=32)
+    ap.add_argument("--sweeps-per-pass", type=int, default=8)
+    ap.add_argument("--nu-fp64", type=int, default=32)
+    ap.add_argument("--use-graphs", type=int, default=2, choices=[0, 1, 2],
+                    help="2: one graph per solve with device-side loops (default); 1: graphs of "
+                         "16-cycle chunks (the form whose kernels ncu lists one by one); 0: plain launches")
     ap.add_argument("--cpu-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_sample:

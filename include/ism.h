@@ -76,15 +76,17 @@ typedef enum {
 
 /* Solver options (ism_get_options fills the defaults). */
 typedef struct {
-    int nu;               /* post-smoothing red-black sweeps per cycle (default 8) */
-    int sweeps_per_pass;  /* single precision: sweeps fused into one pass over memory (default 4; nu % it == 0) */
+    int nu;               /* post-smoothing red-black sweeps per cycle (default 8 FP64, 16 mixed) */
+    int sweeps_per_pass;  /* single precision: sweeps fused into one pass over memory (1..8,
+                             nu % it == 0; default 4 FP64 (unused), 8 mixed) */
     int kind;             /* ism_coarse_kind (default ISM_COARSE_ISM) */
     int max_outer;        /* mixed: refinement iterations cap (default 50) */
     int inner_max;        /* mixed: single-precision cycles per refinement iteration cap (default 10000) */
     double inner_tol;     /* mixed: inner stop when ||r_in|| <= inner_tol ||r|| ... (default 1e-3) */
     double floor_mult;    /* ... or ||r_in|| <= floor_mult 2^-23 ||e|| (rounding floor, default 4) */
-    int check_every;      /* cycles launched between host reads of the convergence flag (default 16) */
-    int use_graphs;       /* capture the cycle loop in CUDA graphs (default 1) */
+    int check_every;      /* use_graphs 0/1: cycles launched between host reads of the flags (default 16) */
+    int use_graphs;       /* 0: plain launches; 1: CUDA graphs of check_every cycles; 2 (default):
+                             the whole solve as one graph with device-side while loops */
 } ism_options;
 
 typedef struct ism_ctx ism_ctx;
@@ -131,6 +133,16 @@ ism_status ism_set_options(ism_ctx *ctx, const ism_options *opt);
  * Synchronises the context's stream. */
 ism_status ism_solve(ism_ctx *ctx, const double *rhs, double *p, double tol,
                      int max_cycles, int *cycles_out, double *relres_out);
+
+/* ism_autotune -- choose the sweeps per cycle and per fused pass for this
+ * context by timing complete solves of rhs (device, nx*ny doubles) from a
+ * zero initial guess over a fixed candidate list; keeps the fastest
+ * candidate in the context's options and copies it to *best (host, may be
+ * NULL).  No counterpart in the paper (its tile size and coarse tolerance
+ * were tuned by hand, Sec. 4.1, 4.3.1).  Allocates one nx*ny double buffer
+ * for the duration of the call.  Synchronises. */
+ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, int max_cycles,
+                        ism_options *best);
 
 /* Relative-residual history of the last solve: one entry per cycle (FP64)
  * or per refinement iteration (mixed), starting with the initial guess.

@@ -123,10 +123,14 @@ extern "C" const char *ism_status_str(ism_status s)
     return "unknown status";
 }
 
-static void default_options(ism_options *o)
+static void default_options(ism_options *o, int prec)
 {
-    o->nu = 8;
-    o->sweeps_per_pass = 4;
+    // FP64: 8 sweeps per cycle (the reading used by the oracle).  Mixed: 16
+    // sweeps per cycle in two fused passes of 8 -- the total number of sweeps
+    // to a given tolerance hardly depends on nu, and fewer cycles mean fewer
+    // coarse solves and residual passes.
+    o->nu = prec == ISM_MIXED ? 16 : 8;
+    o->sweeps_per_pass = prec == ISM_MIXED ? 8 : 4;
     o->kind = ISM_COARSE_ISM;
     o->max_outer = 50;
     o->inner_max = 10000;
@@ -281,7 +285,7 @@ extern "C" ism_status ism_setup(int nx, int ny, double h, const int bc[4], int c
     ctx->singular = ctx->bcmask == 0;
     ctx->prec = prec;
     ctx->user_stream = (cudaStream_t)stream;
-    default_options(&ctx->opt);
+    default_options(&ctx->opt, prec);
     ctx->proj_tol = 1e-8;
     ctx->proj_max_cycles = 100000;
     ctx->conv_u = 1.0;
@@ -1048,5 +1052,52 @@ extern "C" ism_status ism_time_pass(ism_ctx *ctx, void *p, const void *b, int sw
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    return st;
+}
+
+// ================================================================ autotuner
+
+extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, int max_cycles,
+                                   ism_options *best)
+{
+    if (!ctx || !rhs || !(tol > 0.0) || max_cycles < 1) return ISM_ERR_ARG;
+    static const int cand_mixed[][2] = {{8, 4}, {8, 8}, {16, 8}, {24, 8}, {32, 8}, {16, 4}};
+    static const int cand_fp64[][2] = {{8, 4}, {16, 4}, {32, 4}};
+    const int (*cand)[2] = ctx->prec == ISM_MIXED ? cand_mixed : cand_fp64;
+    const int ncand = ctx->prec == ISM_MIXED ? 6 : 3;
+    const ism_options saved = ctx->opt;
+    double *p = nullptr;
+    if (cudaMalloc((void **)&p, (size_t)ctx->n * 8) != cudaSuccess) { cudaGetLastError(); return ISM_ERR_NOMEM; }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    ism_options opt = saved, win = saved;
+    float best_ms = 1e30f;
+    ism_status st = ISM_OK;
+    for (int c = 0; c < ncand && st == ISM_OK; ++c) {
+        opt.nu = cand[c][0];
+        opt.sweeps_per_pass = cand[c][1];
+        if ((st = ism_set_options(ctx, &opt)) != ISM_OK) break;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && st == ISM_OK; ++rep) {     // first run builds the graph
+            cudaMemsetAsync(p, 0, (size_t)ctx->n * 8, ctx->user_stream);
+            cudaEventRecord(e0, ctx->user_stream);
+            int cyc = 0;
+            double rel = 0.0;
+            ism_status s = ism_solve(ctx, rhs, p, tol, max_cycles, &cyc, &rel);
+            cudaEventRecord(e1, ctx->user_stream);
+            cudaEventSynchronize(e1);
+            if (s != ISM_OK) { ms = 1e30f; break; }
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (ms < best_ms) { best_ms = ms; win = opt; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(p);
+    if (st != ISM_OK) { ism_set_options(ctx, &saved); return st; }
+    if (best_ms >= 1e29f) { ism_set_options(ctx, &saved); return ISM_ERR_NOT_CONVERGED; }
+    st = ism_set_options(ctx, &win);
+    if (best) *best = win;
     return st;
 }

@@ -58,6 +58,7 @@ _SIGS = {
     "ism_proj_tol": (_I, [_VP, _D, _I, _I]),
     "ism_last_dp": (_VP, [_VP]),
     "ism_time_pass": (_I, [_VP, _VP, _VP, _I, _I, C.POINTER(C.c_double)]),
+    "ism_autotune": (_I, [_VP, _VP, _D, _I, C.POINTER(IsmOptions)]),
     "ism_residual_restrict_noalloc": (_I, [_I, _I, _I, C.POINTER(C.c_int), _VP, _VP, _VP, _VP, _VP]),
     "ism_solve_batched": (_I, [_I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _D, _I,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]),
@@ -152,6 +153,13 @@ def ism_solve(ctx, rhs, p, tol=1e-8, max_cycles=100000):
     r = C.c_double(0.0)
     s = lib().ism_solve(ctx.handle, _ptr(rhs), _ptr(p), float(tol), int(max_cycles), C.byref(c), C.byref(r))
     return s, c.value, r.value
+
+
+def ism_autotune(ctx, rhs, tol=1e-8, max_cycles=100000):
+    """Returns (status, chosen IsmOptions)."""
+    o = IsmOptions()
+    s = lib().ism_autotune(ctx.handle, _ptr(rhs), float(tol), int(max_cycles), C.byref(o))
+    return s, o
 
 
 def ism_last_history(ctx, cap=4096):

@@ -148,3 +148,18 @@ def test_full_size_mixed_and_fp64_agree():
     bb = b - b.mean()
     assert np.linalg.norm(O.residual(pm, bb, (0, 0, 0, 0))) / np.linalg.norm(bb) <= 1.01e-8
     assert rel(pm, pd) <= 1e-7
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_autotune_picks_a_working_candidate(prec):
+    nx = ny = 256
+    b = smooth_rhs(nx, ny, 9)
+    ctx = setup(nx, ny, 32, (0, 0, 0, 0), prec=prec)
+    s, o = ism.ism_autotune(ctx, dev64(b), 1e-8, 100000)
+    assert s == ism.ISM_OK and o.nu % o.sweeps_per_pass == 0
+    cur = ism.ism_get_options(ctx)
+    assert (cur.nu, cur.sweeps_per_pass) == (o.nu, o.sweeps_per_pass)
+    p_ex, _, _ = O.OracleISM(nx, ny, 32, nu=o.nu).solve(b, tol=1e-11)
+    p = dev64(np.zeros((ny, nx)))
+    s, c, r = ism.ism_solve(ctx, dev64(b), p, 1e-8, 100000)
+    assert s == ism.ISM_OK and r <= 1e-8 and rel(host(p), p_ex) <= 1e-9
