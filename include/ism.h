@@ -243,12 +243,22 @@ ism_status ism_proj_tol(ism_ctx *ctx, double tol, int max_cycles, int warm_start
 const double *ism_last_dp(const ism_ctx *ctx);
 
 /* ---------------- batched ensemble ----------------------------------------
- * Solve n independent problems, each described by its own context (same
- * precision, same stream as ctxs[0]); one set of launches advances every
- * unfinished problem by one step per launch.
- *   ctxs   host, n contexts.  rhs, p: host arrays of n device pointers.
- *   cycles_out: host, n ints or NULL.  relres_out: host, n doubles or NULL.
- * Returns ISM_OK if every problem converged, else the first failing status. */
+ * ism_solve_batched -- solve n independent problems, each described by its
+ * own context, to ||rhs - A_f p|| <= tol ||rhs|| each (BASELINE config 4; the
+ * paper solves one problem at a time).  All contexts must be ISM_MIXED, on
+ * the same device, with equal nu, sweeps_per_pass, max_outer and inner_max;
+ * grids, coarsening and boundary faces may differ.  The solve is one CUDA
+ * graph on ctxs[0]'s stream: every launch covers the work items of all
+ * unfinished problems (a finished problem drops out), so one set of
+ * launches advances every problem by one cycle; per problem the arithmetic
+ * and the decisions are those of ism_solve.  The graph is built on the first
+ * call with a given list of contexts and reused while the list is unchanged.
+ *   ctxs   host, n distinct contexts.  rhs, p: host arrays of n device pointers
+ *          (as for ism_solve: p holds the initial guess and receives the result).
+ *   max_cycles  cap on single-precision cycles per problem (>= 1).
+ *   cycles_out, relres_out: host, n entries each, or NULL.
+ * Returns ISM_OK if every problem converged, else the first failing status;
+ * ISM_ERR_ARG (nothing launched) for invalid or mismatched contexts. */
 ism_status ism_solve_batched(int n, ism_ctx *const *ctxs, const double *const *rhs,
                              double *const *p, double tol, int max_cycles,
                              int *cycles_out, double *relres_out);

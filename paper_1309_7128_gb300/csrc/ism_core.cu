@@ -219,9 +219,12 @@ static void free_graphs(ism_ctx *ctx)
     ctx->g_fp64 = ctx->g_inner = ctx->gc_fp64 = ctx->gc_mixed = nullptr;
 }
 
+void ism_batch_free(void *plan);   // ism_batched.cu
+
 extern "C" void ism_destroy(ism_ctx *ctx)
 {
     if (!ctx) return;
+    if (ctx->batch) ism_batch_free(ctx->batch);
     if (ctx->ws) cudaStreamSynchronize(ctx->ws);
     if (ctx->ws2) cudaStreamSynchronize(ctx->ws2);
     free_graphs(ctx);
@@ -283,6 +286,10 @@ extern "C" ism_status ism_setup(int nx, int ny, double h, const int bc[4], int c
         if (bc[f]) ctx->bcmask |= 1 << f;
     }
     ctx->singular = ctx->bcmask == 0;
+    {
+        static unsigned long long next_uid = 1;
+        ctx->uid = __atomic_fetch_add(&next_uid, 1ULL, __ATOMIC_RELAXED);
+    }
     ctx->prec = prec;
     ctx->user_stream = (cudaStream_t)stream;
     default_options(&ctx->opt, prec);

@@ -34,6 +34,7 @@ struct IsmState {
     double r32norm;    // mixed: ||r|| of the current inner right-hand side
     double rin, enorm; // mixed: latest inner residual and iterate norms
     int c64;           // mixed: which FP64 buffer holds the outer iterate
+    int skip_init;     // batched: 0 while a new inner solve still needs its first restriction
     unsigned int ticket; // CTAs finished in the current fused-control kernel
     double hist[ISM_HMAX];
 };
@@ -83,6 +84,8 @@ struct ism_ctx {
     int last_cycles, last_outer, last_status, last_nhist;
     double last_relres;
     long long launches;
+    unsigned long long uid;    // unique per context (batched plan cache key)
+    void *batch;               // cached batched-solve plan (ism_batched.cu), owned
 
     // projection step
     int vel_bc[4];

@@ -150,7 +150,9 @@ __device__ __forceinline__ void ctl_decide(IsmState *st, const double *S, int mo
             st->cur = 0;
             st->mean_e = 0.0;
             st->r32norm = sqrt(S[0]);
+            st->skip_init = 0;
         }
+        if (!fp64 && st->done) st->inner_done = 1;   // a finished problem runs no more cycles
         break;
     }
     case CTL_INNER: {
@@ -372,19 +374,17 @@ __device__ __forceinline__ void row_times_matrix(int n_out, int n_in, F term, T 
     __syncthreads();
 }
 
-// T[l][k] = Minv[l][k] * sum_i (sum_j QyT[l][j] R[j][i]) Qx[i][k]; one CTA per row l.
+// T[l][k] = Minv[l][k] * sum_i (sum_j QyT[l][j] R[j][i]) Qx[i][k] for row l (one CTA).
 // FROM_PARTS: R[j][i] is the fixed-order sum of the 4 partial block sums.
 template <typename T, bool FROM_PARTS>
-__global__ void k_coarse1(const T *__restrict__ R, const T *__restrict__ QyT,
-                          const T *__restrict__ Qx, const T *__restrict__ Minv,
-                          T *__restrict__ Tm, int ncx, int ncy, const int *skip)
+__device__ __forceinline__ void coarse1_row(const T *__restrict__ R, const T *__restrict__ QyT,
+                                            const T *__restrict__ Qx, const T *__restrict__ Minv,
+                                            T *__restrict__ Tm, int ncx, int ncy, int l)
 {
-    if (skip && *skip) return;
     extern __shared__ unsigned char smraw[];
     T *w = reinterpret_cast<T *>(smraw);
     T *v = w + ncx;
     T *part = v + ncx;
-    const int l = blockIdx.x;
     const T *qrow = QyT + (size_t)l * ncy;
     row_times_matrix<T>(ncx, ncy, [&](int j, int i) -> T {
         const size_t k = (size_t)j * ncx + i;
@@ -402,23 +402,30 @@ __global__ void k_coarse1(const T *__restrict__ R, const T *__restrict__ QyT,
         Tm[(size_t)l * ncx + k] = v[k] * Minv[(size_t)l * ncx + k];
 }
 
-// E[j][i] = sum_k (sum_l Qy[j][l] T[l][k]) QxT[k][i]; one CTA per row j.
+template <typename T, bool FROM_PARTS>
+__global__ void k_coarse1(const T *__restrict__ R, const T *__restrict__ QyT,
+                          const T *__restrict__ Qx, const T *__restrict__ Minv,
+                          T *__restrict__ Tm, int ncx, int ncy, const int *skip)
+{
+    if (skip && *skip) return;
+    coarse1_row<T, FROM_PARTS>(R, QyT, Qx, Minv, Tm, ncx, ncy, blockIdx.x);
+}
+
+// E[j][i] = sum_k (sum_l Qy[j][l] T[l][k]) QxT[k][i] for row j (one CTA).
 // MAKE_G: also the x-interpolated row G[j][x], x = 0..nx-1 (bilinear rule of
 // Eq. 5 along x with the mirror ghosts; constant per block for ACM), used by
 // the fused prolongation, and the partial block sums of row j are cleared
 // for the next restriction.
 template <typename T, bool MAKE_G>
-__global__ void k_coarse2(const T *__restrict__ Tm, const T *__restrict__ Qy,
-                          const T *__restrict__ QxT, T *__restrict__ E, int ncx, int ncy,
-                          const int *skip, T *__restrict__ G, int nx, int m, int bcmask, int kind,
-                          T *__restrict__ rcpart)
+__device__ __forceinline__ void coarse2_row(const T *__restrict__ Tm, const T *__restrict__ Qy,
+                                            const T *__restrict__ QxT, T *__restrict__ E, int ncx,
+                                            int ncy, T *__restrict__ G, int nx, int m, int bcmask,
+                                            int kind, T *__restrict__ rcpart, int j)
 {
-    if (skip && *skip) return;
     extern __shared__ unsigned char smraw[];
     T *w = reinterpret_cast<T *>(smraw);
     T *erow = w + ncx;
     T *part = erow + ncx;
-    const int j = blockIdx.x;
     const T *qrow = Qy + (size_t)j * ncy;
     row_times_matrix<T>(ncx, ncy, [&](int l, int k) -> T { return qrow[l] * Tm[(size_t)l * ncx + k]; }, part, w);
     row_times_matrix<T>(ncx, ncx, [&](int k, int i) -> T { return w[k] * QxT[(size_t)k * ncx + i]; }, part, erow);
@@ -440,4 +447,14 @@ __global__ void k_coarse2(const T *__restrict__ Tm, const T *__restrict__ Qy,
             G[(size_t)j * nx + x] = g;
         }
     }
+}
+
+template <typename T, bool MAKE_G>
+__global__ void k_coarse2(const T *__restrict__ Tm, const T *__restrict__ Qy,
+                          const T *__restrict__ QxT, T *__restrict__ E, int ncx, int ncy,
+                          const int *skip, T *__restrict__ G, int nx, int m, int bcmask, int kind,
+                          T *__restrict__ rcpart)
+{
+    if (skip && *skip) return;
+    coarse2_row<T, MAKE_G>(Tm, Qy, QxT, E, ncx, ncy, G, nx, m, bcmask, kind, rcpart, blockIdx.x);
 }

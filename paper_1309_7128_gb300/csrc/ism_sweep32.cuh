@@ -164,19 +164,10 @@ inline size_t sweep_smem_bytes()
 
 // EDGE: the launch over the tiles whose region touches the domain boundary
 // (listed in edge_tiles); otherwise the launch over the interior tiles.
+// The pass on tile (bx, by) of the problem described by a; one CTA.
 template <bool PROLONG, bool RESID, bool EDGE>
-__global__ void __launch_bounds__(STHREADS, 2) k_sweep32(SweepArgs a)
+__device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, const int by)
 {
-    if (a.skip && *a.skip) return;
-    int bx, by;
-    if (EDGE) {
-        const int2 t = a.edge_tiles[blockIdx.x];
-        bx = t.x;
-        by = t.y;
-    } else {
-        bx = blockIdx.x + a.ix0;
-        by = blockIdx.y + a.iy0;
-    }
     extern __shared__ __align__(16) float sm[];
     float *bsm = sm;                       // SRH x SRW (b per thread, colour-pair order)
     float *xch = sm + SRH * SRW;           // row exchange buffers
@@ -380,6 +371,30 @@ __global__ void __launch_bounds__(STHREADS, 2) k_sweep32(SweepArgs a)
         }
         if (a.ctl_mode >= 0) ctl_last_block(a.st, a.partials, nblk, 3, a.ctl_mode, a.cond);
     }
+}
+
+template <bool PROLONG, bool RESID, bool EDGE>
+__global__ void __launch_bounds__(STHREADS, 2) k_sweep32(SweepArgs a)
+{
+    if (a.skip && *a.skip) return;
+    if (EDGE) {
+        const int2 t = a.edge_tiles[blockIdx.x];
+        sweep_tile<PROLONG, RESID, EDGE>(a, t.x, t.y);
+    } else {
+        sweep_tile<PROLONG, RESID, EDGE>(a, blockIdx.x + a.ix0, blockIdx.y + a.iy0);
+    }
+}
+
+// Batched form: work item (problem, tile x, tile y) per CTA over the per-problem
+// argument table; problems whose phase is finished return at once.
+template <bool PROLONG, bool RESID, bool EDGE>
+__global__ void __launch_bounds__(STHREADS, 2) k_sweep32_batch(const SweepArgs *__restrict__ table,
+                                                               const int4 *__restrict__ work)
+{
+    const int4 w = work[blockIdx.x];
+    const SweepArgs &a = table[w.x];
+    if (a.skip && *a.skip) return;
+    sweep_tile<PROLONG, RESID, EDGE>(a, w.y, w.z);
 }
 
 // Sum of the 4 partial block sums (fixed order) -> R (ncy x ncx).
