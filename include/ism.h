@@ -242,10 +242,52 @@ ism_status ism_proj_tol(ism_ctx *ctx, double tol, int max_cycles, int warm_start
  * the context (valid until the next call on it). */
 const double *ism_last_dp(const ism_ctx *ctx);
 
+/* ---------------- adjoint of the projection step ------------------------
+ * No counterpart in the paper, which runs the step forwards only.  The
+ * adjoint is the transpose of the linearisation of proj_step (Sec. 2.2-2.3,
+ * Eq. 3-4) at the step's input state: transposed correction, the pressure
+ * solve again (A_f is symmetric, so its adjoint is the same ISM solve, run
+ * to the tolerance set by ism_proj_tol from a zero initial guess), transposed
+ * divergence (= minus the gradient), transposed predictor.  The exact solve
+ * is differentiated: the solver's own iterations are not. */
+
+/* Given the input velocities (u, v) of one proj_step and the adjoints
+ * (gu, gv, gp) of its outputs (u', v', p'), overwrite gu, gv, gp with the
+ * adjoints of its inputs (u, v, p).  The step is linear in p, so p is not
+ * needed.  Layouts as proj_step; all device, float.  Uses the flow setup of
+ * ism_set_flow and the dt, nu given; the context's predicted-velocity
+ * buffers are overwritten, its last increment (ism_last_dp) is not.
+ * Returns the status of the adjoint pressure solve. */
+ism_status proj_step_adjoint(ism_ctx *ctx, const float *u, const float *v, double dt,
+                             double nu, float *gu, float *gv, float *gp);
+
+/* Enstrophy of a MAC velocity field, E = 1/2 sum_nodes w^2 h^2 with the
+ * vorticity w = dv/dx - du/dy at the interior grid nodes (boundary nodes
+ * left out).  value: host, may be NULL; gu, gv: device (layouts as
+ * proj_step), receive dE/du, dE/dv when not NULL.  Synchronises when value
+ * is requested.  Not in the paper: the loss of the differentiable rollout. */
+ism_status ism_enstrophy(ism_ctx *ctx, const float *u, const float *v, double *value,
+                         float *gu, float *gv);
+
+/* Differentiable rollout: `steps` proj_steps from (u0, v0, p0) (device,
+ * not modified), loss = ism_enstrophy of the final velocity (host *loss, may
+ * be NULL).  With gu, gv, gp all non-NULL (device) they receive the gradient
+ * of the loss with respect to u0, v0, p0, by reverse sweeps with checkpoints
+ * every `every` steps (>= 1): the forward keeps the state before every
+ * every-th step, each segment is replayed from its checkpoint and then
+ * traversed by proj_step_adjoint.  All three NULL: forward and loss only.
+ * Device memory: (steps/every + 2) states of ~20 bytes per cell plus `every`
+ * velocity pairs, owned by the context and kept for the next call.
+ * Synchronises.  Returns ISM_OK, or the first non-OK solve status
+ * (ISM_ERR_NOT_CONVERGED keeps going; other errors stop the call). */
+ism_status proj_rollout_grad(ism_ctx *ctx, const float *u0, const float *v0, const float *p0,
+                             double dt, double nu, int steps, int every, double *loss,
+                             float *gu, float *gv, float *gp);
+
 /* ---------------- batched ensemble ----------------------------------------
  * ism_solve_batched -- solve n independent problems, each described by its
- * own context, to ||rhs - A_f p|| <= tol ||rhs|| each (BASELINE config 4; the
- * paper solves one problem at a time).  All contexts must be ISM_MIXED, on
+ * own context, to ||rhs - A_f p|| <= tol ||rhs|| each (an ensemble of
+ * uneven problems; the paper solves one problem at a time).  All contexts must be ISM_MIXED, on
  * the same device, with equal nu, sweeps_per_pass, max_outer and inner_max;
  * grids, coarsening and boundary faces may differ.  The solve is one CUDA
  * graph on ctxs[0]'s stream: every launch covers the work items of all

@@ -232,7 +232,8 @@ extern "C" void ism_destroy(ism_ctx *ctx)
                     ctx->QxT32, ctx->Qy32, ctx->QyT32, ctx->Minv32, ctx->b64, ctx->p64[0],
                     ctx->p64[1], ctx->e32[0], ctx->e32[1], ctx->r32, ctx->rc64, ctx->ec64,
                     ctx->T64, ctx->rc32, ctx->ec32, ctx->T32, ctx->partials, ctx->st,
-                    ctx->st_k, ctx->us, ctx->vs, ctx->dp, ctx->rcpart, ctx->G32};
+                    ctx->st_k, ctx->us, ctx->vs, ctx->dp, ctx->rcpart, ctx->G32,
+                    ctx->roll, ctx->scal};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int K = 0; K <= SMAXK; ++K)

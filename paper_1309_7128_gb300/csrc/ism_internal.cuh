@@ -97,6 +97,11 @@ struct ism_ctx {
     double *dp;                // pressure increment
     double proj_tol;
     int proj_max_cycles, proj_warm;
+
+    // adjoint rollout (ism_adjoint.cu): checkpoints, segment states, adjoint state
+    void *roll;                // one allocation, grown on demand
+    size_t roll_bytes;
+    double *scal;              // device scalars (loss)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -124,3 +129,5 @@ ism_status ism_solve_internal(ism_ctx *ctx, double tol, int max_cycles);
 ism_status ism_prepare_rhs(ism_ctx *ctx, const double *rhs);
 
 // Projection-step kernels (ism_proj.cu) need the residual solver above.
+// Allocate the predicted-velocity and increment buffers on first use.
+ism_status ism_proj_buffers(ism_ctx *ctx);

@@ -184,7 +184,7 @@ extern "C" ism_status ism_proj_tol(ism_ctx *ctx, double tol, int max_cycles, int
 
 extern "C" const double *ism_last_dp(const ism_ctx *ctx) { return ctx ? ctx->dp : nullptr; }
 
-static ism_status ensure_proj_buffers(ism_ctx *ctx)
+ism_status ism_proj_buffers(ism_ctx *ctx)
 {
     if (ctx->us) return ISM_OK;
     const size_t nx = ctx->nx, ny = ctx->ny;
@@ -209,7 +209,7 @@ extern "C" ism_status proj_step(ism_ctx *ctx, float *u, float *v, float *p, doub
     if (!ctx || !u || !v || !p || !(dt > 0.0) || !(nu >= 0.0) || !isfinite(dt) || !isfinite(nu))
         return ISM_ERR_ARG;
     if (!ctx->flow_set) return ISM_ERR_ARG;
-    TRY(ensure_proj_buffers(ctx));
+    TRY(ism_proj_buffers(ctx));
     TRY(ism_enter(ctx));
     const int nx = ctx->nx, ny = ctx->ny;
     FlowArgs f;

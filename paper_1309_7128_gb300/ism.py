@@ -62,6 +62,10 @@ _SIGS = {
     "ism_residual_restrict_noalloc": (_I, [_I, _I, _I, C.POINTER(C.c_int), _VP, _VP, _VP, _VP, _VP]),
     "ism_solve_batched": (_I, [_I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _D, _I,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "proj_step_adjoint": (_I, [_VP, _VP, _VP, _D, _D, _VP, _VP, _VP]),
+    "ism_enstrophy": (_I, [_VP, _VP, _VP, C.POINTER(C.c_double), _VP, _VP]),
+    "proj_rollout_grad": (_I, [_VP, _VP, _VP, _VP, _D, _D, _I, _I, C.POINTER(C.c_double),
+                               _VP, _VP, _VP]),
 }
 
 
@@ -236,3 +240,26 @@ def ism_solve_batched(ctxs, rhs, p, tol=1e-8, max_cycles=100000):
     rel = (C.c_double * n)()
     s = lib().ism_solve_batched(n, ca, ra, pa, float(tol), int(max_cycles), cyc, rel)
     return s, list(cyc), list(rel)
+
+
+def proj_step_adjoint(ctx, u, v, dt, nu, gu, gv, gp):
+    """Overwrite (gu, gv, gp), the adjoints of one step's outputs, with the
+    adjoints of its inputs; (u, v) are the step's input velocities."""
+    return lib().proj_step_adjoint(ctx.handle, _ptr(u), _ptr(v), float(dt), float(nu),
+                                   _ptr(gu), _ptr(gv), _ptr(gp))
+
+
+def ism_enstrophy(ctx, u, v, gu=None, gv=None):
+    """Returns (status, enstrophy); gu, gv (optional) receive its gradient."""
+    val = C.c_double(0.0)
+    s = lib().ism_enstrophy(ctx.handle, _ptr(u), _ptr(v), C.byref(val), _ptr(gu), _ptr(gv))
+    return s, val.value
+
+
+def proj_rollout_grad(ctx, u0, v0, p0, dt, nu, steps, every=20, gu=None, gv=None, gp=None):
+    """Returns (status, loss); with gu, gv, gp given they receive the gradient
+    of the final enstrophy with respect to (u0, v0, p0)."""
+    val = C.c_double(0.0)
+    s = lib().proj_rollout_grad(ctx.handle, _ptr(u0), _ptr(v0), _ptr(p0), float(dt), float(nu),
+                                int(steps), int(every), C.byref(val), _ptr(gu), _ptr(gv), _ptr(gp))
+    return s, val.value

@@ -79,7 +79,7 @@ def test_batched_rejects_mixed_options_and_fp64():
 
 
 def test_batched_full_ensemble_256():
-    """256 uneven Neumann cavity problems (config 4 shapes, 16h / 32h by
+    """256 uneven Neumann cavity problems (128..1024 per side, 16h / 32h by
     size): every problem reaches 1e-8 measured by the oracle's FP64 residual;
     three are compared with the oracle solution."""
     shapes = batch_shapes(256, seed=0)

@@ -15,7 +15,7 @@ from tests.gpu_util import dev64, ensure_built, host, ism, rel, setup
 pytestmark = pytest.mark.gpu
 
 CASES = [  # nx, ny, m, bc
-    (256, 256, 16, (0, 0, 0, 0)),     # config 0
+    (256, 256, 16, (0, 0, 0, 0)),     # 256^2 cavity, 16h
     (160, 96, 32, (0, 0, 0, 0)),
     (96, 160, 16, (0, 1, 0, 0)),
     (128, 64, 8, (1, 1, 1, 1)),
