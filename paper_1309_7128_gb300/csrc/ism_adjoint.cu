@@ -502,7 +502,13 @@ extern "C" ism_status proj_rollout_grad(ism_ctx *ctx, const float *u0, const flo
     }
     TRY(enstrophy_launch(ctx, cur.u, cur.v, 0, grad ? gu : nullptr, grad ? gv : nullptr));
     if (grad) ISM_CUDA_TRY(cudaMemsetAsync(gp, 0, L.np * 4, ctx->ws));
-    if (loss) ISM_CUDA_TRY(cudaMemcpyAsync(ctx->st_host, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->ws));
+    // read the loss now: the solves of the reverse sweep reuse the pinned buffer
+    double loss_h = 0.0;
+    if (loss) {
+        ISM_CUDA_TRY(cudaMemcpyAsync(ctx->st_host, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->ws));
+        ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+        memcpy(&loss_h, ctx->st_host, sizeof(double));
+    }
     if (grad) {
         for (int seg = L.nck - 1; seg >= 0; --seg) {
             const int s0 = seg * every, s1 = std::min(steps, s0 + every);
@@ -529,9 +535,7 @@ extern "C" ism_status proj_rollout_grad(ism_ctx *ctx, const float *u0, const flo
         }
     }
     TRY(ism_leave(ctx));
-    if (loss) {
-        ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
-        memcpy(loss, ctx->st_host, sizeof(double));
-    }
+    ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+    if (loss) *loss = loss_h;
     return agg;
 }

@@ -77,8 +77,11 @@ def test_step_adjoint_matches_oracle(flow, prec):
     assert s == ism.ISM_OK, ism.status_str(s)
     got = [host(g) for g in (gu, gv, gp)]
     assert relv(got, want) <= 1e-5
+    # entrywise, against the largest adjoint (p-bar cancels to ~0 exactly
+    # with a Dirichlet face and to its mean without one)
+    scale = max(np.abs(w).max() for w in want)
     for g, w in zip(got, want):
-        assert np.abs(g - w).max() <= 1e-4 * np.abs(w).max()
+        assert np.abs(g - w).max() <= 1e-5 * scale
 
 
 def test_step_adjoint_leaves_forward_increment_and_rejects_bad_args():
@@ -205,4 +208,4 @@ def test_rollout_gradient_central_differences_512():
         fd = (lp - lm) / (2 * eps)
         errs.append(abs(fd - ad) / max(abs(ad), 1e-3 * loss))
     print("central-difference relative errors:", ["%.2e" % e for e in errs])
-    assert max(errs) <= 2e-2
+    assert max(errs) <= 5e-4
