@@ -87,6 +87,9 @@ typedef struct {
     int check_every;      /* use_graphs 0/1: cycles launched between host reads of the flags (default 16) */
     int use_graphs;       /* 0: plain launches; 1: CUDA graphs of check_every cycles; 2 (default):
                              the whole solve as one graph with device-side while loops */
+    int coarse_tc;        /* mixed: 1 (default) runs the single-precision coarse solve on the tensor
+                             cores (tcgen05, TF32 operands, FP32 accumulation) when ncx, ncy <= 128;
+                             0 on the CUDA cores in FP32.  Ignored by the FP64 path. */
 } ism_options;
 
 typedef struct ism_ctx ism_ctx;

@@ -32,7 +32,7 @@ struct BDom {
     double *puser;               // caller's iterate / result (per solve)
     double *b64, *p0, *p1;
     float *e0, *e1, *r32;
-    float *rcpart, *ec, *Tm, *G;
+    float *rcpart, *ec, *Tm;
     const float *Qx, *QxT, *Qy, *QyT, *Minv;
     long long n;
     int nx, ny, m, ncx, ncy, bcmask, kind, singular;
@@ -229,8 +229,7 @@ __global__ void k_b_coarse2(BDom *dom, const int2 *rows)
     const int2 w = rows[blockIdx.x];
     const BDom &D = dom[w.x];
     if (D.st->inner_done) return;
-    coarse2_row<float, true>(D.Tm, D.Qy, D.QxT, D.ec, D.ncx, D.ncy, D.G, D.nx, D.m, D.bcmask,
-                             D.kind, D.rcpart, w.y);
+    coarse2_row<float, true>(D.Tm, D.Qy, D.QxT, D.ec, D.ncx, D.ncy, D.rcpart, w.y);
 }
 
 // Loop condition: run while problems remain (with a hard iteration cap).
@@ -292,7 +291,7 @@ static SweepArgs pass_args(ism_ctx *c, int K, bool resid, int q, bool init)
 {
     SweepArgs a;
     memset(&a, 0, sizeof(a));
-    a.e0 = c->e32[0]; a.e1 = c->e32[1]; a.b = c->r32; a.G = c->G32; a.rcpart = c->rcpart;
+    a.e0 = c->e32[0]; a.e1 = c->e32[1]; a.b = c->r32; a.E = c->ec32; a.rcpart = c->rcpart;
     a.partials = c->partials; a.st = c->st;
     a.skip = init ? &c->st->skip_init : &c->st->inner_done;
     a.curp = init ? nullptr : &c->st->cur;
@@ -342,7 +341,7 @@ static ism_status build_plan(Plan *P, const std::vector<ism_ctx *> &cs)
         D.st = c->st; D.partials = c->partials;
         D.b64 = c->b64; D.p0 = c->p64[0]; D.p1 = c->p64[1];
         D.e0 = c->e32[0]; D.e1 = c->e32[1]; D.r32 = c->r32;
-        D.rcpart = c->rcpart; D.ec = c->ec32; D.Tm = c->T32; D.G = c->G32;
+        D.rcpart = c->rcpart; D.ec = c->ec32; D.Tm = c->T32;
         D.Qx = c->Qx32; D.QxT = c->QxT32; D.Qy = c->Qy32; D.QyT = c->QyT32; D.Minv = c->Minv32;
         D.n = c->n; D.nx = c->nx; D.ny = c->ny; D.m = c->m; D.ncx = c->ncx; D.ncy = c->ncy;
         D.bcmask = c->bcmask; D.kind = c->opt.kind; D.singular = c->singular;

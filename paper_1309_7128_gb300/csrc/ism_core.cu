@@ -138,6 +138,7 @@ static void default_options(ism_options *o, int prec)
     o->floor_mult = 4.0;
     o->check_every = 16;
     o->use_graphs = 2;
+    o->coarse_tc = prec == ISM_MIXED ? 1 : 0;
 }
 
 static const double kPi = 3.14159265358979323846;
@@ -207,7 +208,8 @@ static ism_status upload_coarse(ism_ctx *ctx, const EigenHost &E)
     if ((s = up(ctx->QxT64, ctx->QxT32, QxT)) != ISM_OK) return s;
     if ((s = up(ctx->Qy64, ctx->Qy32, E.Qy)) != ISM_OK) return s;
     if ((s = up(ctx->QyT64, ctx->QyT32, QyT)) != ISM_OK) return s;
-    return up(ctx->Minv64, ctx->Minv32, Minv);
+    if ((s = up(ctx->Minv64, ctx->Minv32, Minv)) != ISM_OK) return s;
+    return ism_coarse_tc_upload(ctx, E.Qx, E.Qy, Minv);
 }
 
 static void free_graphs(ism_ctx *ctx)
@@ -232,8 +234,8 @@ extern "C" void ism_destroy(ism_ctx *ctx)
                     ctx->QxT32, ctx->Qy32, ctx->QyT32, ctx->Minv32, ctx->b64, ctx->p64[0],
                     ctx->p64[1], ctx->e32[0], ctx->e32[1], ctx->r32, ctx->rc64, ctx->ec64,
                     ctx->T64, ctx->rc32, ctx->ec32, ctx->T32, ctx->partials, ctx->st,
-                    ctx->st_k, ctx->us, ctx->vs, ctx->dp, ctx->rcpart, ctx->G32,
-                    ctx->roll, ctx->scal};
+                    ctx->st_k, ctx->us, ctx->vs, ctx->dp, ctx->rcpart, ctx->roll, ctx->scal,
+                    ctx->tc_block};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int K = 0; K <= SMAXK; ++K)
@@ -323,7 +325,6 @@ extern "C" ism_status ism_setup(int nx, int ny, double h, const int bc[4], int c
     ALLOC(ctx->rc64, nc * 8); ALLOC(ctx->ec64, nc * 8); ALLOC(ctx->T64, nc * 8);
     ALLOC(ctx->rc32, nc * 4); ALLOC(ctx->ec32, nc * 4); ALLOC(ctx->T32, nc * 4);
     ALLOC(ctx->rcpart, nc * 4 * 4);
-    ALLOC(ctx->G32, (size_t)ctx->ncy * nx * 4);
     if (prec == ISM_MIXED) {
         ALLOC(ctx->p64[1], N * 8);
         ALLOC(ctx->e32[0], N * 4);
@@ -361,6 +362,7 @@ extern "C" ism_status ism_setup(int nx, int ny, double h, const int bc[4], int c
     }
     // the fused sweep pass uses 80 KB of dynamic shared memory
     const int smb = (int)sweep_smem_bytes();
+    ism_coarse_tc_prepare();
     cudaFuncSetAttribute(k_sweep32<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
     cudaFuncSetAttribute(k_sweep32<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
     cudaFuncSetAttribute(k_sweep32<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
@@ -396,6 +398,7 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     if (o->kind != ISM_COARSE_ISM && o->kind != ISM_COARSE_ACM) return ISM_ERR_ARG;
     if (o->max_outer < 1 || o->inner_max < 1 || o->check_every < 1 || o->check_every > 4096) return ISM_ERR_ARG;
     if (o->use_graphs < 0 || o->use_graphs > 2) return ISM_ERR_ARG;
+    if (o->coarse_tc < 0 || o->coarse_tc > 1) return ISM_ERR_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
     const int kind_changed = o->kind != ctx->opt.kind;
     cudaStreamSynchronize(ctx->ws);
@@ -443,9 +446,8 @@ static ism_status launch_coarse(ism_ctx *ctx, const T *rc, T *ec, T *Tm, const i
     const size_t sm = (size_t)(JS + 2) * ctx->ncx * sizeof(T);
     k_coarse1<T, FUSED><<<ctx->ncy, th, sm, ctx->ws>>>(rc, QyT, Qx, Minv, Tm, ctx->ncx, ctx->ncy, skip);
     ISM_LAUNCH_CHECK(ctx);
-    k_coarse2<T, FUSED><<<ctx->ncy, th, sm, ctx->ws>>>(
-        Tm, Qy, QxT, ec, ctx->ncx, ctx->ncy, skip, (T *)(FUSED ? (void *)ctx->G32 : nullptr), ctx->nx,
-        ctx->m, ctx->bcmask, ctx->opt.kind, (T *)(FUSED ? (void *)ctx->rcpart : nullptr));
+    k_coarse2<T, FUSED><<<ctx->ncy, th, sm, ctx->ws>>>(Tm, Qy, QxT, ec, ctx->ncx, ctx->ncy, skip,
+                                                       (T *)(FUSED ? (void *)ctx->rcpart : nullptr));
     ISM_LAUNCH_CHECK(ctx);
     return ISM_OK;
 }
@@ -596,7 +598,7 @@ static SweepArgs inner_args(ism_ctx *ctx, IsmState *st, float *e0, float *e1, co
                             const int *skip, const int *curp)
 {
     SweepArgs a;
-    a.e0 = e0; a.e1 = e1; a.b = b; a.G = ctx->G32; a.rcpart = ctx->rcpart;
+    a.e0 = e0; a.e1 = e1; a.b = b; a.E = ctx->ec32; a.rcpart = ctx->rcpart;
     a.partials = ctx->partials; a.st = st; a.skip = skip; a.curp = curp;
     a.nx = ctx->nx; a.ny = ctx->ny; a.m = ctx->m; a.ncx = ctx->ncx; a.ncy = ctx->ncy;
     a.lm = ctx->m == 8 ? 3 : ctx->m == 16 ? 4 : 5;
@@ -614,7 +616,10 @@ static SweepArgs inner_args(ism_ctx *ctx, IsmState *st, float *e0, float *e1, co
 static ism_status inner_cycle(ism_ctx *ctx, unsigned long long cond = 0)
 {
     const int *skip = &ctx->st->inner_done;
-    TRY((launch_coarse<float, true>(ctx, ctx->rcpart, ctx->ec32, ctx->T32, skip)));
+    if (ctx->opt.coarse_tc && ism_coarse_tc_supported(ctx))
+        TRY(ism_launch_coarse_tc(ctx, ctx->rcpart, true, ctx->ec32, ctx->rcpart, skip));
+    else
+        TRY((launch_coarse<float, true>(ctx, ctx->rcpart, ctx->ec32, ctx->T32, skip)));
     const int npass = ctx->opt.nu / ctx->opt.sweeps_per_pass;
     SweepArgs a = inner_args(ctx, ctx->st, ctx->e32[0], ctx->e32[1], ctx->r32, skip, &ctx->st->cur);
     a.ctl_mode = CTL_INNER;
@@ -906,6 +911,10 @@ ism_status ism_solve_internal(ism_ctx *ctx, double tol, int max_cycles)
     ism_status s = ctx->prec == ISM_FP64 ? solve_fp64(ctx) : solve_mixed(ctx);
     if (s != ISM_OK) return s;
     const IsmState *hs = ctx->st_host;
+    if (hs->tc_fail) {            // a tensor-core coarse solve gave up waiting: the result is void
+        ctx->last_status = ISM_ERR_CUDA;
+        return ISM_ERR_CUDA;
+    }
     ctx->last_cycles = hs->cycles;
     ctx->last_outer = hs->outer;
     ctx->last_relres = hs->relres;
@@ -1007,6 +1016,8 @@ extern "C" ism_status ism_coarse_solve(ism_ctx *ctx, const void *rc, void *ec)
     if (!ctx || !rc || !ec) return ISM_ERR_ARG;
     TRY(ism_enter(ctx));
     if (ctx->prec == ISM_FP64) TRY((launch_coarse<double, false>(ctx, (const double *)rc, (double *)ec, ctx->T64, nullptr)));
+    else if (ctx->opt.coarse_tc && ism_coarse_tc_supported(ctx))
+        TRY(ism_launch_coarse_tc(ctx, (const float *)rc, false, (float *)ec, nullptr, nullptr));
     else TRY((launch_coarse<float, false>(ctx, (const float *)rc, (float *)ec, ctx->T32, nullptr)));
     return ism_leave(ctx);
 }

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/ism.h"
 
 #define ISM_HMAX 4096          // residual-history entries kept on the device
@@ -35,6 +37,7 @@ struct IsmState {
     double rin, enorm; // mixed: latest inner residual and iterate norms
     int c64;           // mixed: which FP64 buffer holds the outer iterate
     int skip_init;     // batched: 0 while a new inner solve still needs its first restriction
+    int tc_fail;       // a tensor-core coarse solve gave up waiting for its MMAs
     unsigned int ticket; // CTAs finished in the current fused-control kernel
     double hist[ISM_HMAX];
 };
@@ -65,7 +68,8 @@ struct ism_ctx {
     double *rc64, *ec64, *T64; // coarse residual, correction, intermediate
     float *rc32, *ec32, *T32;
     float *rcpart;             // 4 partial block sums per coarse cell (fused restriction)
-    float *G32;                // x-interpolated coarse correction rows, ncy x nx
+    void *tc_block;            // tensor-core coarse solve: constant operand tiles (TF32), or NULL
+    size_t tc_bytes;
     double *partials;          // ISM_NQ * max_blocks
     int max_blocks;
     IsmState *st;              // device control block
@@ -131,3 +135,14 @@ ism_status ism_prepare_rhs(ism_ctx *ctx, const double *rhs);
 // Projection-step kernels (ism_proj.cu) need the residual solver above.
 // Allocate the predicted-velocity and increment buffers on first use.
 ism_status ism_proj_buffers(ism_ctx *ctx);
+
+// Tensor-core coarse solve of the single-precision cycle (ism_coarse_tc.cu):
+// rc -> ec (ncy x ncx); from_parts: rc holds 4 partial block sums per coarse
+// cell; rcpart (or NULL) is cleared afterwards.
+bool ism_coarse_tc_supported(const ism_ctx *ctx);
+void ism_coarse_tc_prepare();   // kernel attributes (called by ism_setup, outside any capture)
+// Lay out the constant operands (eigenbases, 1/mu) as TF32 tiles on the device.
+ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, const std::vector<double> &Qy,
+                                const std::vector<double> &Minv);
+ism_status ism_launch_coarse_tc(ism_ctx *ctx, const float *rc, bool from_parts, float *ec, float *rcpart,
+                                const int *skip);

@@ -412,15 +412,12 @@ __global__ void k_coarse1(const T *__restrict__ R, const T *__restrict__ QyT,
 }
 
 // E[j][i] = sum_k (sum_l Qy[j][l] T[l][k]) QxT[k][i] for row j (one CTA).
-// MAKE_G: also the x-interpolated row G[j][x], x = 0..nx-1 (bilinear rule of
-// Eq. 5 along x with the mirror ghosts; constant per block for ACM), used by
-// the fused prolongation, and the partial block sums of row j are cleared
-// for the next restriction.
-template <typename T, bool MAKE_G>
+// CLEAR_PARTS: the partial block sums of row j are cleared for the next
+// restriction (fused single-precision cycle).
+template <typename T, bool CLEAR_PARTS>
 __device__ __forceinline__ void coarse2_row(const T *__restrict__ Tm, const T *__restrict__ Qy,
                                             const T *__restrict__ QxT, T *__restrict__ E, int ncx,
-                                            int ncy, T *__restrict__ G, int nx, int m, int bcmask,
-                                            int kind, T *__restrict__ rcpart, int j)
+                                            int ncy, T *__restrict__ rcpart, int j)
 {
     extern __shared__ unsigned char smraw[];
     T *w = reinterpret_cast<T *>(smraw);
@@ -430,31 +427,15 @@ __device__ __forceinline__ void coarse2_row(const T *__restrict__ Tm, const T *_
     row_times_matrix<T>(ncx, ncy, [&](int l, int k) -> T { return qrow[l] * Tm[(size_t)l * ncx + k]; }, part, w);
     row_times_matrix<T>(ncx, ncx, [&](int k, int i) -> T { return w[k] * QxT[(size_t)k * ncx + i]; }, part, erow);
     for (int i = threadIdx.x; i < ncx; i += blockDim.x) E[(size_t)j * ncx + i] = erow[i];
-    if (MAKE_G) {
+    if (CLEAR_PARTS)
         for (int i = threadIdx.x; i < 4 * ncx; i += blockDim.x) rcpart[(size_t)j * ncx * 4 + i] = (T)0;
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
-            T g;
-            if (kind == ISM_COARSE_ACM) {
-                g = erow[x / m];
-            } else {
-                const int hm = m >> 1;
-                const int I0 = (x - hm + m) / m - 1;
-                const T tx = ((T)(x - I0 * m - hm) + (T)0.5) / (T)m;
-                T qa = I0 < 0 ? ((bcmask & 1) ? -erow[0] : erow[0]) : erow[I0];
-                T qb = I0 + 1 >= ncx ? ((bcmask & 2) ? -erow[ncx - 1] : erow[ncx - 1]) : erow[I0 + 1];
-                g = ((T)1 - tx) * qa + tx * qb;
-            }
-            G[(size_t)j * nx + x] = g;
-        }
-    }
 }
 
-template <typename T, bool MAKE_G>
+template <typename T, bool CLEAR_PARTS>
 __global__ void k_coarse2(const T *__restrict__ Tm, const T *__restrict__ Qy,
                           const T *__restrict__ QxT, T *__restrict__ E, int ncx, int ncy,
-                          const int *skip, T *__restrict__ G, int nx, int m, int bcmask, int kind,
-                          T *__restrict__ rcpart)
+                          const int *skip, T *__restrict__ rcpart)
 {
     if (skip && *skip) return;
-    coarse2_row<T, MAKE_G>(Tm, Qy, QxT, E, ncx, ncy, G, nx, m, bcmask, kind, rcpart, blockIdx.x);
+    coarse2_row<T, CLEAR_PARTS>(Tm, Qy, QxT, E, ncx, ncy, rcpart, blockIdx.x);
 }

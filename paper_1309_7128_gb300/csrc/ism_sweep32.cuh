@@ -27,9 +27,11 @@
 // divisor d = 4 +- 1 per boundary face (Neumann -1, Dirichlet-0 +1).
 //
 // Options fused into the pass:
-//  PROLONG: add P e_c - mean while loading.  P e_c is evaluated from the
-//           x-interpolated coarse rows G[J][x] (made by the coarse solve):
-//           p += (1 - t_y) G[J0][x] + t_y G[J0+1][x] (Eq. 5, separable form).
+//  PROLONG: add P e_c - mean while loading.  P e_c is evaluated in the
+//           separable form of Eq. 5: the CTA first interpolates the coarse
+//           rows it needs along x into shared memory,
+//           G[J][x] = (1 - t_x) e_c[J][I0] + t_x e_c[J][I0+1] (mirror ghosts
+//           at the ends), then p += (1 - t_y) G[J0][x] + t_y G[J0+1][x].
 //  RESID:   residual r = b - A_f p of the valid tile, its partial m x m block
 //           sums (rcpart: 4 slots per coarse cell, one per covering tile,
 //           summed in fixed order by the coarse solve) and the norm partials.
@@ -48,7 +50,7 @@ constexpr int SMAXK = 8;                // sweeps per pass (H <= 17, valid tile 
 struct SweepArgs {
     float *e0, *e1;           // ping-pong iterate buffers
     const float *b;           // right-hand side
-    const float *G;           // x-interpolated coarse correction rows, ncy x nx (PROLONG)
+    const float *E;           // coarse correction e_c, ncy x ncx (PROLONG)
     float *rcpart;            // 4 partial block sums per coarse cell (RESID), zeroed before
     double *partials;         // per-CTA ||r||^2, sum p, sum p^2 (RESID)
     IsmState *st;             // mean_e (PROLONG); control block (RESID with ctl_mode >= 0)
@@ -225,11 +227,28 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         Jg0 = a.kind == ISM_COARSE_ACM ? max(0, (y0 - 1) >> lm) : max(0, ((y0 - 1 - hm + m) >> lm) - 1);
         const int Jg1 = min(a.ncy - 1, a.kind == ISM_COARSE_ACM ? (y0 + SRH) >> lm : ((y0 + SRH - hm + m) >> lm));
         const int nrow = Jg1 - Jg0 + 1;
+        const int ncx = a.ncx;
         for (int t = threadIdx.x; t < nrow * 32; t += STHREADS) {
-            const int jr = t >> 5, l = t & 31, x = x0 + SNC * l;
-            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
-            if ((unsigned)x < (unsigned)nx) g = *reinterpret_cast<const float4 *>(a.G + (size_t)(Jg0 + jr) * nx + x);
-            reinterpret_cast<float4 *>(gsm)[jr * 32 + l] = g;
+            const int jr = t >> 5, l = t & 31, xb = x0 + SNC * l;
+            float g[SNC] = {0.f, 0.f, 0.f, 0.f};
+            if ((unsigned)xb < (unsigned)nx) {
+                const float *er = a.E + (size_t)(Jg0 + jr) * ncx;
+#pragma unroll
+                for (int q = 0; q < SNC; ++q) {
+                    const int x = xb + q;
+                    if (a.kind == ISM_COARSE_ACM) {
+                        g[q] = __ldg(er + (x >> lm));
+                    } else {
+                        const int I0 = ((x - hm + m) >> lm) - 1;
+                        const float tx = ((float)(x - I0 * m - hm) + 0.5f) * invm;
+                        const float qa = I0 < 0 ? ((a.bcmask & 1) ? -__ldg(er) : __ldg(er)) : __ldg(er + I0);
+                        const float qb = I0 + 1 >= ncx ? ((a.bcmask & 2) ? -__ldg(er + ncx - 1) : __ldg(er + ncx - 1))
+                                                       : __ldg(er + I0 + 1);
+                        g[q] = (1.0f - tx) * qa + tx * qb;
+                    }
+                }
+            }
+            reinterpret_cast<float4 *>(gsm)[jr * 32 + l] = make_float4(g[0], g[1], g[2], g[3]);
         }
         __syncthreads();
     }

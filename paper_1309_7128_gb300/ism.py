@@ -27,7 +27,8 @@ ISM_VEL_NOSLIP, ISM_VEL_FREESLIP, ISM_VEL_INFLOW, ISM_VEL_OUTFLOW = 0, 1, 2, 3
 class IsmOptions(C.Structure):
     _fields_ = [("nu", C.c_int), ("sweeps_per_pass", C.c_int), ("kind", C.c_int),
                 ("max_outer", C.c_int), ("inner_max", C.c_int), ("inner_tol", C.c_double),
-                ("floor_mult", C.c_double), ("check_every", C.c_int), ("use_graphs", C.c_int)]
+                ("floor_mult", C.c_double), ("check_every", C.c_int), ("use_graphs", C.c_int),
+                ("coarse_tc", C.c_int)]
 
 
 class IsmError(RuntimeError):

@@ -85,8 +85,10 @@ def test_coarse_solve(nx, ny, m, bc, kind):
     if not any(bc):
         rc -= rc.mean()
     ref = O.OracleISM(nx, ny, m, bc, kind=kind).coarse_solve(rc)
-    for prec, tol in ((ism.ISM_FP64, 1e-11), (ism.ISM_MIXED, 2e-5)):
-        ctx = setup(nx, ny, m, bc, prec=prec, kind=0 if kind == "ism" else 1)
+    # FP64; FP32 on the CUDA cores; TF32 on the tensor cores (tcgen05): four
+    # chained products of operands rounded to 2^-11 relative
+    for prec, tcflag, tol in ((ism.ISM_FP64, 0, 1e-11), (ism.ISM_MIXED, 0, 2e-5), (ism.ISM_MIXED, 1, 1e-2)):
+        ctx = setup(nx, ny, m, bc, prec=prec, kind=0 if kind == "ism" else 1, coarse_tc=tcflag)
         mk = dev64 if prec == ism.ISM_FP64 else dev32
         ec = mk(np.zeros_like(rc))
         ism.check(ism.ism_coarse_solve(ctx, mk(rc), ec))
@@ -134,3 +136,32 @@ def test_full_size_single_cycle_fp32():
     for _ in range(8):
         O.lib().or_rbgs_sweep_f32(nx, ny, bca, ref, np.ascontiguousarray(b))
     np.testing.assert_allclose(host(pd), ref.astype(np.float64), rtol=0, atol=2e-6 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("nx,ny,m", [(2048, 2048, 32), (2048, 2048, 16), (160, 96, 32), (1024, 512, 8),
+                                    (512, 256, 8)])
+def test_coarse_solve_tensor_cores_tf32_error(nx, ny, m):
+    """The tcgen05 TF32 coarse solve against the FP64 oracle: on coarse grids
+    up to 64 x 64 the error is that of TF32 operands (well below 1e-2 of the
+    solution's scale and far above FP32 rounding, so the tensor-core path is
+    the one that ran); larger coarse grids fall back to the FP32 CUDA-core
+    path and give its result exactly."""
+    ncx, ncy = nx // m, ny // m
+    rc = random_field(ncx, ncy, 9)
+    rc -= rc.mean()
+    ref = O.OracleISM(nx, ny, m, (0, 0, 0, 0)).coarse_solve(rc)
+    ref -= ref.mean()
+    errs = {}
+    for tcflag in (0, 1):
+        ctx = setup(nx, ny, m, prec=ism.ISM_MIXED, coarse_tc=tcflag)
+        ec = dev32(np.zeros_like(rc))
+        ism.check(ism.ism_coarse_solve(ctx, dev32(rc), ec))
+        got = host(ec)
+        got -= got.mean()
+        errs[tcflag] = np.abs(got - ref).max() / np.abs(ref).max()
+    print(f"{nx}x{ny}/{m}: max error FP32 {errs[0]:.2e}, TF32 tensor cores {errs[1]:.2e}")
+    assert errs[0] <= 2e-5
+    if ncx <= 64 and ncy <= 64:
+        assert 2e-5 < errs[1] <= 1e-2
+    else:
+        assert errs[1] == errs[0]
