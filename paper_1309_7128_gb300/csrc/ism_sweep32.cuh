@@ -157,11 +157,14 @@ __device__ __forceinline__ void exchange_rows(float (&P)[SRR + 2][SNC], float *x
     }
 }
 
-// G rows needed by a region: its rows span at most SRH/8 + 3 coarse rows (m >= 8)
+// G rows needed by a region: its rows span at most SRH/8 + 3 coarse rows (m >= 8);
+// its columns at most SRW/8 + 3 coarse columns (e_c block staged before G)
 constexpr int SGROWS = SRH / 8 + 3;
+constexpr int SGCOLS = SRW / 8 + 3;
 inline size_t sweep_smem_bytes()
 {
-    return (size_t)SRH * SRW * 4 + (size_t)2 * SNW * 2 * SRW * 4 + (size_t)SGROWS * SRW * 4;
+    return (size_t)SRH * SRW * 4 + (size_t)2 * SNW * 2 * SRW * 4 + (size_t)SGROWS * SRW * 4 +
+           (size_t)SGROWS * SGCOLS * 4;
 }
 
 // EDGE: the launch over the tiles whose region touches the domain boundary
@@ -227,23 +230,36 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         Jg0 = a.kind == ISM_COARSE_ACM ? max(0, (y0 - 1) >> lm) : max(0, ((y0 - 1 - hm + m) >> lm) - 1);
         const int Jg1 = min(a.ncy - 1, a.kind == ISM_COARSE_ACM ? (y0 + SRH) >> lm : ((y0 + SRH - hm + m) >> lm));
         const int nrow = Jg1 - Jg0 + 1;
+        // (a) the block of e_c the region needs: rows Jg0..Jg1, columns Ic0..Ic1
+        //     (the bilinear neighbours of the in-domain columns), to shared memory
         const int ncx = a.ncx;
+        const int xs = max(x0, 0), xe = min(x0 + SRW, nx) - 1;
+        const bool acm = a.kind == ISM_COARSE_ACM;
+        const int Ic0 = acm ? (xs >> lm) : max(0, ((xs - hm + m) >> lm) - 1);
+        const int Ic1 = acm ? min(ncx - 1, xe >> lm) : min(ncx - 1, ((xe - hm + m) >> lm));
+        const int ncol = Ic1 - Ic0 + 1;
+        float *esm = gsm + SGROWS * SRW;
+        for (int t = threadIdx.x; t < nrow * ncol; t += STHREADS) {
+            const int jr = t / ncol, c = t - jr * ncol;
+            esm[t] = a.E[(size_t)(Jg0 + jr) * ncx + Ic0 + c];
+        }
+        __syncthreads();
+        // (b) G[J][x] for the region's columns
         for (int t = threadIdx.x; t < nrow * 32; t += STHREADS) {
             const int jr = t >> 5, l = t & 31, xb = x0 + SNC * l;
             float g[SNC] = {0.f, 0.f, 0.f, 0.f};
             if ((unsigned)xb < (unsigned)nx) {
-                const float *er = a.E + (size_t)(Jg0 + jr) * ncx;
+                const float *er = esm + jr * ncol - Ic0;      // er[I] = e_c[Jg0 + jr][I], Ic0 <= I <= Ic1
 #pragma unroll
                 for (int q = 0; q < SNC; ++q) {
                     const int x = xb + q;
-                    if (a.kind == ISM_COARSE_ACM) {
-                        g[q] = __ldg(er + (x >> lm));
+                    if (acm) {
+                        g[q] = er[x >> lm];
                     } else {
                         const int I0 = ((x - hm + m) >> lm) - 1;
                         const float tx = ((float)(x - I0 * m - hm) + 0.5f) * invm;
-                        const float qa = I0 < 0 ? ((a.bcmask & 1) ? -__ldg(er) : __ldg(er)) : __ldg(er + I0);
-                        const float qb = I0 + 1 >= ncx ? ((a.bcmask & 2) ? -__ldg(er + ncx - 1) : __ldg(er + ncx - 1))
-                                                       : __ldg(er + I0 + 1);
+                        const float qa = I0 < 0 ? ((a.bcmask & 1) ? -er[0] : er[0]) : er[I0];
+                        const float qb = I0 + 1 >= ncx ? ((a.bcmask & 2) ? -er[ncx - 1] : er[ncx - 1]) : er[I0 + 1];
                         g[q] = (1.0f - tx) * qa + tx * qb;
                     }
                 }
