@@ -104,3 +104,58 @@ def test_set_flow_validation():
     assert ism.ism_set_flow(ctx, (0, VEL_INFLOW, 0, 0), (0, 0, 0, 0), None, 1.0) == ism.ISM_ERR_ARG
     u = dev32(np.zeros((64, 65)))
     assert ism.proj_step(ctx, u, u, u, 0.1, 0.1) == ism.ISM_ERR_ARG     # flow not set
+
+
+def test_jet_full_size_8192x4096():
+    """The jet workload at full size: 8192 x 4096 cells, h = 1, 32h coarsening
+    (256 x 128 coarse grid), 64-cell inlet, Dirichlet-0 outflow.  Checks that
+    hold at any size, computed by the oracle: (1) the mixed solve of the
+    oracle's FP64 right-hand side (its predictor and divergence of a
+    developed GPU state) reaches 1e-8 by the oracle's own residual; (2) one
+    GPU projection step equals the oracle's correction of the oracle's
+    predictor with the GPU's increment, up to the FP32 rounding of the
+    velocities; (3) mass: the outflow carries the inflow."""
+    nx, ny, m = 8192, 4096, 32
+    h, nu = 1.0, 64.0 / 5000
+    dt = 0.9 * min(0.4 * h / 1.0, 0.25 * h * h / nu, 2 * nu / 1.0)
+    prof = f32(jet_inflow(ny, width=64, seed=0))
+    ctx = setup(nx, ny, m, O.pressure_bc(JET), prec=ism.ISM_MIXED, h=h)
+    keep = dev32(prof)
+    ism.check(ism.ism_set_flow(ctx, JET, (0, 0, 0, 0), keep, 1.0))
+    ism.check(ism.ism_proj_tol(ctx, 1e-8, 100000, False))
+    u0 = np.zeros((ny, nx + 1)); u0[:, 0] = prof
+    ud, vd, pd = dev32(u0), dev32(np.zeros((ny + 1, nx))), dev32(np.zeros((ny, nx)))
+    for _ in range(3):                                   # develop the inlet region
+        assert ism.proj_step(ctx, ud, vd, pd, dt, nu) == ism.ISM_OK
+    u1, v1, p1 = host(ud), host(vd), host(pd)
+
+    # (1) full-size solve of the oracle's right-hand side
+    us, vs = O.predictor(u1, v1, p1, h, dt, nu, JET, u_in=prof, conv_u=1.0)
+    b = O.divergence(us, vs, h, dt)
+    q = torch.zeros((ny, nx), dtype=torch.float64, device="cuda:0")
+    s, cyc, rr = ism.ism_solve(ctx, torch.tensor(b, device="cuda:0"), q, 1e-8, 100000)
+    assert s == ism.ISM_OK and rr <= 1e-8
+    dq = host(q)
+    assert np.linalg.norm(O.residual(dq, b, O.pressure_bc(JET))) / np.linalg.norm(b) <= 1.01e-8
+
+    # (2) one projection step against the oracle's predictor and correction
+    assert ism.proj_step(ctx, ud, vd, pd, dt, nu) == ism.ISM_OK
+    u2, v2, p2 = host(ud), host(vd), host(pd)
+    torch.cuda.synchronize()
+    dpg = host(_dp_view(ism.ism_last_dp(ctx), ny, nx))
+    ue, ve, pe = us.copy(), vs.copy(), p1.copy()
+    O.correct(ue, ve, pe, dpg, h, dt, JET)
+    scale = np.abs(ue).max()
+    assert np.abs(u2 - ue).max() <= 2e-5 * scale
+    assert np.abs(v2 - ve).max() <= 2e-5 * scale
+    assert np.abs(p2 - pe).max() <= 2e-5 * max(np.abs(pe).max(), 1e-12)
+    print(f"jet 8192x4096: cycles {cyc}, relres {rr:.2e}")
+
+    # (3) mass: outflow flux equals inflow flux
+    assert abs(u2[:, -1].sum() - prof.sum()) <= 1e-4 * prof.sum()
+
+
+def _dp_view(addr, ny, nx):
+    class _Arr:
+        __cuda_array_interface__ = {"shape": (ny, nx), "typestr": "<f8", "data": (addr, False), "version": 3}
+    return torch.as_tensor(_Arr(), device="cuda:0")
