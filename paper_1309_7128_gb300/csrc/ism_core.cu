@@ -1080,10 +1080,14 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
                                    ism_options *best)
 {
     if (!ctx || !rhs || !(tol > 0.0) || max_cycles < 1) return ISM_ERR_ARG;
-    static const int cand_mixed[][2] = {{8, 4}, {8, 8}, {16, 8}, {24, 8}, {32, 8}, {16, 4}};
-    static const int cand_fp64[][2] = {{8, 4}, {16, 4}, {32, 4}};
+    // a cycle costs a fixed part (coarse solve, fused prolongation and residual,
+    // control) plus one part per pass, and the total sweeps of a solve are
+    // nearly independent of nu: larger nu amortises the fixed part
+    static const int cand_mixed[][2] = {{8, 4},  {8, 8},  {16, 8}, {24, 8},  {32, 8},
+                                        {48, 8}, {64, 8}, {96, 8}, {128, 8}, {16, 4}};
+    static const int cand_fp64[][2] = {{8, 4}, {16, 4}, {32, 4}, {48, 4}, {64, 4}};
     const int (*cand)[2] = ctx->prec == ISM_MIXED ? cand_mixed : cand_fp64;
-    const int ncand = ctx->prec == ISM_MIXED ? 6 : 3;
+    const int ncand = ctx->prec == ISM_MIXED ? 10 : 5;
     const ism_options saved = ctx->opt;
     double *p = nullptr;
     if (cudaMalloc((void **)&p, (size_t)ctx->n * 8) != cudaSuccess) { cudaGetLastError(); return ISM_ERR_NOMEM; }

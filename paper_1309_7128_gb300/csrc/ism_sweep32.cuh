@@ -218,33 +218,52 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         }
     }
 
-    // 1. load p (rows -1..SRR) with the fused prolongation, and b
+    // 1. load p (rows -1..SRR) and b; with PROLONG, the block of e_c the region
+    //    needs is requested first, so that its latency overlaps the loads of p
+    //    and b, and the prolongation is added to the registers afterwards
     float P[SRR + 2][SNC];
-    float mean = 0.f;
-    if (PROLONG && a.use_mean) mean = (float)a.st->mean_e;
     const int m = a.m, lm = a.lm, hm = m >> 1;
     const float invm = 1.0f / (float)m;
-    // rows of G used by region rows y0-1 .. y0+SRH (clamped to the coarse grid)
-    int Jg0 = 0;
+    const bool acm = a.kind == ISM_COARSE_ACM;
+    // rows of e_c used by region rows y0-1 .. y0+SRH (clamped to the coarse grid)
+    int Jg0 = 0, nrow = 0, Ic0 = 0, ncol = 0;
+    float *esm = gsm + SGROWS * SRW;
     if (PROLONG) {
-        Jg0 = a.kind == ISM_COARSE_ACM ? max(0, (y0 - 1) >> lm) : max(0, ((y0 - 1 - hm + m) >> lm) - 1);
-        const int Jg1 = min(a.ncy - 1, a.kind == ISM_COARSE_ACM ? (y0 + SRH) >> lm : ((y0 + SRH - hm + m) >> lm));
-        const int nrow = Jg1 - Jg0 + 1;
-        // (a) the block of e_c the region needs: rows Jg0..Jg1, columns Ic0..Ic1
-        //     (the bilinear neighbours of the in-domain columns), to shared memory
-        const int ncx = a.ncx;
+        Jg0 = acm ? max(0, (y0 - 1) >> lm) : max(0, ((y0 - 1 - hm + m) >> lm) - 1);
+        const int Jg1 = min(a.ncy - 1, acm ? (y0 + SRH) >> lm : ((y0 + SRH - hm + m) >> lm));
+        nrow = Jg1 - Jg0 + 1;
+        // (a) columns Ic0..Ic1: the bilinear neighbours of the in-domain columns
         const int xs = max(x0, 0), xe = min(x0 + SRW, nx) - 1;
-        const bool acm = a.kind == ISM_COARSE_ACM;
-        const int Ic0 = acm ? (xs >> lm) : max(0, ((xs - hm + m) >> lm) - 1);
-        const int Ic1 = acm ? min(ncx - 1, xe >> lm) : min(ncx - 1, ((xe - hm + m) >> lm));
-        const int ncol = Ic1 - Ic0 + 1;
-        float *esm = gsm + SGROWS * SRW;
+        Ic0 = acm ? (xs >> lm) : max(0, ((xs - hm + m) >> lm) - 1);
+        const int Ic1 = acm ? min(a.ncx - 1, xe >> lm) : min(a.ncx - 1, ((xe - hm + m) >> lm));
+        ncol = Ic1 - Ic0 + 1;
         for (int t = threadIdx.x; t < nrow * ncol; t += STHREADS) {
             const int jr = t / ncol, c = t - jr * ncol;
-            esm[t] = a.E[(size_t)(Jg0 + jr) * ncx + Ic0 + c];
+            esm[t] = a.E[(size_t)(Jg0 + jr) * a.ncx + Ic0 + c];
         }
+    }
+#pragma unroll
+    for (int r = 0; r < SRR + 2; ++r) {
+        const int y = y0 + ry0 + r - 1;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((unsigned)y < (unsigned)ny && colin) v = *reinterpret_cast<const float4 *>(pin + (size_t)y * nx + cx);
+        P[r][0] = v.x; P[r][1] = v.y; P[r][2] = v.z; P[r][3] = v.w;
+    }
+#pragma unroll
+    for (int r = 0; r < SRR; ++r) {
+        const int y = y0 + ry0 + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if ((unsigned)y < (unsigned)ny && colin) v = *reinterpret_cast<const float4 *>(a.b + (size_t)y * nx + cx);
+        if (!edge) { v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f; }
+        float2 *row = reinterpret_cast<float2 *>(bs + r * SRW);
+        row[lane] = make_float2(v.x, v.z);
+        row[32 + lane] = make_float2(v.y, v.w);
+    }
+    if (PROLONG) {
+        const float mean = a.use_mean ? (float)a.st->mean_e : 0.f;
+        const int ncx = a.ncx;
         __syncthreads();
-        // (b) G[J][x] for the region's columns
+        // (b) G[J][x] = e_c interpolated along x for the region's columns
         for (int t = threadIdx.x; t < nrow * 32; t += STHREADS) {
             const int jr = t >> 5, l = t & 31, xb = x0 + SNC * l;
             float g[SNC] = {0.f, 0.f, 0.f, 0.f};
@@ -267,18 +286,15 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
             reinterpret_cast<float4 *>(gsm)[jr * 32 + l] = make_float4(g[0], g[1], g[2], g[3]);
         }
         __syncthreads();
-    }
-    const float4 *gs4 = reinterpret_cast<const float4 *>(gsm) + lane;
+        // (c) p += P e_c - mean along y, per loaded row
+        const float4 *gs4 = reinterpret_cast<const float4 *>(gsm) + lane;
 #pragma unroll
-    for (int r = 0; r < SRR + 2; ++r) {
-        const int y = y0 + ry0 + r - 1;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if ((unsigned)y < (unsigned)ny && colin) {
-            v = *reinterpret_cast<const float4 *>(pin + (size_t)y * nx + cx);
-            if (PROLONG) {
+        for (int r = 0; r < SRR + 2; ++r) {
+            const int y = y0 + ry0 + r - 1;
+            if ((unsigned)y < (unsigned)ny && colin) {
                 float4 ga, gb;
                 float wa, wb;
-                if (a.kind == ISM_COARSE_ACM) {
+                if (acm) {
                     ga = gs4[((y >> lm) - Jg0) * 32];
                     gb = ga;
                     wa = 1.0f;
@@ -295,23 +311,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
                     wa = sa * (1.0f - ty);
                     wb = sb * ty;
                 }
-                v.x = (v.x - mean) + fmaf(wa, ga.x, wb * gb.x);
-                v.y = (v.y - mean) + fmaf(wa, ga.y, wb * gb.y);
-                v.z = (v.z - mean) + fmaf(wa, ga.z, wb * gb.z);
-                v.w = (v.w - mean) + fmaf(wa, ga.w, wb * gb.w);
+                P[r][0] = (P[r][0] - mean) + fmaf(wa, ga.x, wb * gb.x);
+                P[r][1] = (P[r][1] - mean) + fmaf(wa, ga.y, wb * gb.y);
+                P[r][2] = (P[r][2] - mean) + fmaf(wa, ga.z, wb * gb.z);
+                P[r][3] = (P[r][3] - mean) + fmaf(wa, ga.w, wb * gb.w);
             }
         }
-        P[r][0] = v.x; P[r][1] = v.y; P[r][2] = v.z; P[r][3] = v.w;
-    }
-#pragma unroll
-    for (int r = 0; r < SRR; ++r) {
-        const int y = y0 + ry0 + r;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if ((unsigned)y < (unsigned)ny && colin) v = *reinterpret_cast<const float4 *>(a.b + (size_t)y * nx + cx);
-        if (!edge) { v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f; }
-        float2 *row = reinterpret_cast<float2 *>(bs + r * SRW);
-        row[lane] = make_float2(v.x, v.z);
-        row[32 + lane] = make_float2(v.y, v.w);
     }
 
     // 2. 2K half-sweeps, red ((x+y) even) first
