@@ -76,7 +76,7 @@ typedef enum {
 
 /* Solver options (ism_get_options fills the defaults). */
 typedef struct {
-    int nu;               /* post-smoothing red-black sweeps per cycle (default 8 FP64, 16 mixed) */
+    int nu;               /* post-smoothing red-black sweeps per cycle (default 8 FP64, 64 mixed) */
     int sweeps_per_pass;  /* single precision: sweeps fused into one pass over memory (1..8,
                              nu % it == 0; default 4 FP64 (unused), 8 mixed) */
     int kind;             /* ism_coarse_kind (default ISM_COARSE_ISM) */

@@ -59,7 +59,8 @@ struct Plan {
     int ncrows = 0;
     // fused-pass tables and work lists: index 0 = init pass (K = 0, residual),
     // 1 = plain pass geometry, 2 = residual pass geometry
-    SweepArgs *tab[10] = {};     // per pass q (q < npass) and tab[9] = init
+    std::vector<SweepArgs *> tab;   // per pass q (q < npass = nu / K)
+    SweepArgs *tab_init = nullptr;  // the init pass (K = 0, residual)
     int4 *work_in[3] = {}, *work_ed[3] = {};
     int nwork_in[3] = {}, nwork_ed[3] = {};
     int maxncx = 1;
@@ -79,8 +80,9 @@ void ism_batch_free(void *p)
     void *bufs[] = {P->dom, P->bst, P->chunks, P->crows, P->gather, P->gather_rel};
     for (void *b : bufs)
         if (b) cudaFree(b);
-    for (int i = 0; i < 10; ++i)
-        if (P->tab[i]) cudaFree(P->tab[i]);
+    for (SweepArgs *t : P->tab)
+        if (t) cudaFree(t);
+    if (P->tab_init) cudaFree(P->tab_init);
     for (int i = 0; i < 3; ++i) {
         if (P->work_in[i]) cudaFree(P->work_in[i]);
         if (P->work_ed[i]) cudaFree(P->work_ed[i]);
@@ -363,6 +365,7 @@ static ism_status build_plan(Plan *P, const std::vector<ism_ctx *> &cs)
         return ISM_ERR_NOMEM;
     }
     const int npass = P->nu / P->K;
+    P->tab.assign(npass, nullptr);
     for (int q = 0; q < npass; ++q) {
         std::vector<SweepArgs> t(P->n);
         for (int d = 0; d < P->n; ++d) t[d] = pass_args(cs[d], P->K, q == npass - 1, q, false);
@@ -371,7 +374,7 @@ static ism_status build_plan(Plan *P, const std::vector<ism_ctx *> &cs)
     {
         std::vector<SweepArgs> t(P->n);
         for (int d = 0; d < P->n; ++d) t[d] = pass_args(cs[d], 0, true, 0, true);
-        TRY(upload(&P->tab[9], t));
+        TRY(upload(&P->tab_init, t));
     }
     const int geomK[3] = {0, P->K, P->K};
     const bool geomR[3] = {true, false, true};
@@ -449,7 +452,7 @@ static ism_status body(ism_ctx *c0, Plan *P, unsigned long long cond, long long 
     k_b_refine<true><<<P->nchunks, 256, 0, c0->ws>>>(P->dom, P->chunks, P->bst);
     k_b_zero<<<P->nchunks, 256, 0, c0->ws>>>(P->dom, P->chunks);
     count += 2;
-    TRY((launch_pass<false, true>(c0, P->tab[9], P->work_in[0], P->nwork_in[0], P->work_ed[0],
+    TRY((launch_pass<false, true>(c0, P->tab_init, P->work_in[0], P->nwork_in[0], P->work_ed[0],
                                   P->nwork_ed[0], count)));
     k_b_coarse1<<<P->ncrows, 256, csm, c0->ws>>>(P->dom, P->crows);
     k_b_coarse2<<<P->ncrows, 256, csm, c0->ws>>>(P->dom, P->crows);

@@ -125,11 +125,11 @@ extern "C" const char *ism_status_str(ism_status s)
 
 static void default_options(ism_options *o, int prec)
 {
-    // FP64: 8 sweeps per cycle (the reading used by the oracle).  Mixed: 16
-    // sweeps per cycle in two fused passes of 8 -- the total number of sweeps
-    // to a given tolerance hardly depends on nu, and fewer cycles mean fewer
-    // coarse solves and residual passes.
-    o->nu = prec == ISM_MIXED ? 16 : 8;
+    // FP64: 8 sweeps per cycle (the reading used by the oracle).  Mixed: 64
+    // sweeps per cycle in eight fused passes of 8 -- the total number of
+    // sweeps to a given tolerance hardly depends on nu, while every cycle adds
+    // a fixed cost (coarse solve, fused prolongation and residual, control).
+    o->nu = prec == ISM_MIXED ? 64 : 8;
     o->sweeps_per_pass = prec == ISM_MIXED ? 8 : 4;
     o->kind = ISM_COARSE_ISM;
     o->max_outer = 50;

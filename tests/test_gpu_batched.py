@@ -96,3 +96,18 @@ def test_batched_full_ensemble_256():
         nx, ny = shapes[k]
         p_ex, _, _ = O.OracleISM(nx, ny, ms[k], nu=ism.ism_get_options(ctxs[k]).nu).solve(bs[k], tol=1e-11)
         assert rel(host(ps[k]), p_ex) <= 1e-9
+
+
+@pytest.mark.parametrize("nu", [72, 128])
+def test_batched_many_passes_per_cycle(nu):
+    """Cycles of nu / 8 > 8 fused passes (9 and 16 passes): every pass keeps
+    its own argument table; results match single-problem solves."""
+    shapes = [(256, 128), (160, 160), (384, 256)]
+    ctxs, rhs, ps, bs = make_batch(shapes, [16, 32, 16], [(0, 0, 0, 0)] * 3, nu=nu, sweeps_per_pass=8)
+    s, cyc, rr = ism.ism_solve_batched(ctxs, rhs, ps, 1e-8, 100000)
+    assert s == ism.ISM_OK and all(r <= 1e-8 for r in rr)
+    for k, (nx, ny) in enumerate(shapes):
+        q = dev64(np.zeros((ny, nx)))
+        s1, c1, r1 = ism.ism_solve(ctxs[k], rhs[k], q, 1e-8, 100000)
+        assert s1 == ism.ISM_OK and abs(c1 - cyc[k]) <= 2
+        assert rel(host(ps[k]), host(q)) <= 1e-9
