@@ -296,8 +296,11 @@ ism_status proj_rollout_grad(ism_ctx *ctx, const float *u0, const float *v0, con
  * graph on ctxs[0]'s stream: every launch covers the work items of all
  * unfinished problems (a finished problem drops out), so one set of
  * launches advances every problem by one cycle; per problem the arithmetic
- * and the decisions are those of ism_solve.  The graph is built on the first
- * call with a given list of contexts and reused while the list is unchanged.
+ * and the decisions are those of ism_solve.  The coarse solves run on the
+ * tensor cores (one CTA per problem) when every context has coarse_tc set and
+ * a coarse grid of at most 64 x 64, else on the CUDA cores.  The graph is
+ * built on the first call with a given list of contexts and reused while the
+ * list (and nu, sweeps_per_pass, coarse_tc) is unchanged.
  *   ctxs   host, n distinct contexts.  rhs, p: host arrays of n device pointers
  *          (as for ism_solve: p holds the initial guess and receives the result).
  *   max_cycles  cap on single-precision cycles per problem (>= 1).

@@ -1,6 +1,8 @@
-"""torch.autograd wrappers of the projection step and its hand-written adjoint.
+"""torch.autograd wrappers of the pressure solve, the projection step and
+their hand-written adjoints.
 
-Argument marshalling only: the forward calls ``proj_step`` and the backward
+Argument marshalling only: the forwards call ``ism_solve`` / ``proj_step``
+and the backwards ``ism_solve`` (the solve is symmetric) /
 ``proj_step_adjoint`` of the CUDA library (``include/ism.h``); no derivative
 is taken by torch.  ``rollout_grad`` calls the library's checkpointed rollout,
 which runs the whole forward/reverse sweep natively.
@@ -10,6 +12,35 @@ from __future__ import annotations
 import torch
 
 from . import ism
+
+
+class IsmSolve(torch.autograd.Function):
+    """p = S(rhs): the ISM pressure solve of A_f p = rhs (Sec. 3.4) to `tol`,
+    with the mean of rhs removed and p of zero mean when every face is
+    Neumann, i.e. S = Pi A_f^+ Pi with Pi the mean projector.  S is
+    symmetric, so the backward pass is the same solve applied to the
+    incoming gradient (the solver's iterations are not differentiated)."""
+
+    @staticmethod
+    def forward(fctx, ctx, rhs, tol, max_cycles):
+        p = torch.zeros_like(rhs, dtype=torch.float64)
+        ism.check(ism.ism_solve(ctx, rhs.detach().to(torch.float64).contiguous(), p, tol, max_cycles)[0],
+                  "ism_solve")
+        fctx.args = (ctx, float(tol), int(max_cycles))
+        return p
+
+    @staticmethod
+    def backward(fctx, gp):
+        ctx, tol, max_cycles = fctx.args
+        g = torch.zeros_like(gp, dtype=torch.float64)
+        ism.check(ism.ism_solve(ctx, gp.detach().to(torch.float64).contiguous(), g, tol, max_cycles)[0],
+                  "ism_solve (adjoint)")
+        return None, g, None, None
+
+
+def solve(ctx, rhs, tol=1e-8, max_cycles=100000):
+    """Differentiable pressure solve (FP64 in and out)."""
+    return IsmSolve.apply(ctx, rhs, tol, max_cycles)
 
 
 class ProjStep(torch.autograd.Function):

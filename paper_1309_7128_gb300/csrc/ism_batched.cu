@@ -61,6 +61,8 @@ struct Plan {
     // 1 = plain pass geometry, 2 = residual pass geometry
     std::vector<SweepArgs *> tab;   // per pass q (q < npass = nu / K)
     SweepArgs *tab_init = nullptr;  // the init pass (K = 0, residual)
+    void *ctc = nullptr;            // tensor-core coarse solve: per-problem arguments, or NULL
+    size_t ctc_smem = 0;
     int4 *work_in[3] = {}, *work_ed[3] = {};
     int nwork_in[3] = {}, nwork_ed[3] = {};
     int maxncx = 1;
@@ -83,6 +85,7 @@ void ism_batch_free(void *p)
     for (SweepArgs *t : P->tab)
         if (t) cudaFree(t);
     if (P->tab_init) cudaFree(P->tab_init);
+    if (P->ctc) cudaFree(P->ctc);
     for (int i = 0; i < 3; ++i) {
         if (P->work_in[i]) cudaFree(P->work_in[i]);
         if (P->work_ed[i]) cudaFree(P->work_ed[i]);
@@ -262,7 +265,7 @@ __global__ void k_b_gather(BDom *dom, const BState *bs, int *out, double *rel)
     const IsmState *st = dom[d].st;
     out[3 * d + 0] = st->cycles;
     out[3 * d + 1] = st->outer;
-    out[3 * d + 2] = st->done ? st->status : ISM_ERR_NOT_CONVERGED;
+    out[3 * d + 2] = st->tc_fail ? ISM_ERR_CUDA : (st->done ? st->status : ISM_ERR_NOT_CONVERGED);
     rel[d] = st->relres;
 }
 
@@ -328,6 +331,14 @@ static void pass_work(const std::vector<ism_ctx *> &cs, int K, bool resid, std::
     }
 }
 
+// Tensor cores for the coarse solves when every problem allows them.
+static bool batch_uses_tc(const std::vector<ism_ctx *> &cs)
+{
+    for (ism_ctx *c : cs)
+        if (!c->opt.coarse_tc || !ism_coarse_tc_supported(c)) return false;
+    return true;
+}
+
 static ism_status build_plan(Plan *P, const std::vector<ism_ctx *> &cs)
 {
     ism_ctx *c0 = cs[0];
@@ -364,6 +375,7 @@ static ism_status build_plan(Plan *P, const std::vector<ism_ctx *> &cs)
         cudaGetLastError();
         return ISM_ERR_NOMEM;
     }
+    if (batch_uses_tc(cs)) TRY(ism_coarse_tc_batch_table(cs.data(), P->n, &P->ctc, &P->ctc_smem));
     const int npass = P->nu / P->K;
     P->tab.assign(npass, nullptr);
     for (int q = 0; q < npass; ++q) {
@@ -454,8 +466,13 @@ static ism_status body(ism_ctx *c0, Plan *P, unsigned long long cond, long long 
     count += 2;
     TRY((launch_pass<false, true>(c0, P->tab_init, P->work_in[0], P->nwork_in[0], P->work_ed[0],
                                   P->nwork_ed[0], count)));
-    k_b_coarse1<<<P->ncrows, 256, csm, c0->ws>>>(P->dom, P->crows);
-    k_b_coarse2<<<P->ncrows, 256, csm, c0->ws>>>(P->dom, P->crows);
+    if (P->ctc) {
+        TRY(ism_launch_coarse_tc_batch(c0->ws, P->ctc, P->n, P->ctc_smem));
+        count -= 1;
+    } else {
+        k_b_coarse1<<<P->ncrows, 256, csm, c0->ws>>>(P->dom, P->crows);
+        k_b_coarse2<<<P->ncrows, 256, csm, c0->ws>>>(P->dom, P->crows);
+    }
     count += 2;
     for (int q = 0; q < npass; ++q) {
         const int g = q == npass - 1 ? 2 : 1;
@@ -512,6 +529,7 @@ static ism_status build_graph(ism_ctx *c0, Plan *P)
 static bool plan_matches(const Plan *P, const std::vector<ism_ctx *> &cs)
 {
     if (!P || (int)cs.size() != P->n || cs[0]->opt.nu != P->nu || cs[0]->opt.sweeps_per_pass != P->K) return false;
+    if ((P->ctc != nullptr) != batch_uses_tc(cs)) return false;
     for (size_t d = 0; d < cs.size(); ++d)
         if (cs[d]->uid != P->uids[d]) return false;
     return true;

@@ -25,6 +25,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ism_kernels.cuh"
@@ -93,6 +94,7 @@ struct CoarseTcArgs {
     int tcols;                // TMEM columns allocated
     const int *skip;
     IsmState *st;             // tc_fail is set when a wait runs out
+    int *consumed;            // set to 1 once R has been used (batched: first restriction), or NULL
 };
 
 __device__ __forceinline__ void put4(unsigned char *tile, int row, int k, int K, float a, float b, float c,
@@ -138,9 +140,8 @@ __device__ __forceinline__ void read_rows(uint32_t tmem, int Np, F f)
 }
 
 template <bool FROM_PARTS>
-__global__ void __launch_bounds__(CT_THREADS, 1) k_coarse_tc(CoarseTcArgs a)
+__device__ __forceinline__ void coarse_tc_body(const CoarseTcArgs &a)
 {
-    if (a.skip && *a.skip) return;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t bar_mma, bar_ld;
     __shared__ uint32_t tslot;
@@ -275,6 +276,23 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_coarse_tc(CoarseTcArgs a)
         float4 *rp = reinterpret_cast<float4 *>(a.rcpart);
         for (int i = t; i < ncx * ncy; i += CT_THREADS) rp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    if (ok && a.consumed && t == 0) *a.consumed = 1;
+}
+
+template <bool FROM_PARTS>
+__global__ void __launch_bounds__(CT_THREADS, 1) k_coarse_tc(CoarseTcArgs a)
+{
+    if (a.skip && *a.skip) return;
+    coarse_tc_body<FROM_PARTS>(a);
+}
+
+// Batched ensemble: one CTA per problem (argument table); problems outside
+// an inner solve return at once.
+__global__ void __launch_bounds__(CT_THREADS, 1) k_coarse_tc_batch(const CoarseTcArgs *__restrict__ tab)
+{
+    const CoarseTcArgs a = tab[blockIdx.x];
+    if (a.skip && *a.skip) return;
+    coarse_tc_body<true>(a);
 }
 
 }  // namespace
@@ -289,6 +307,49 @@ void ism_coarse_tc_prepare()
     const TcLayout L = tc_layout(CT_MAXC, CT_MAXC);
     cudaFuncSetAttribute(k_coarse_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
     cudaFuncSetAttribute(k_coarse_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+    cudaFuncSetAttribute(k_coarse_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+}
+
+static CoarseTcArgs coarse_tc_args(ism_ctx *ctx, const float *rc, float *ec, float *rcpart, const int *skip)
+{
+    CoarseTcArgs a;
+    a.R = rc;
+    a.cst = (const unsigned char *)ctx->tc_block;
+    a.E = ec;
+    a.rcpart = rcpart;
+    a.L = tc_layout(ctx->ncx, ctx->ncy);
+    a.tcols = a.L.Np <= 32 ? 32 : 64;
+    a.skip = skip;
+    a.st = ctx->st;
+    a.consumed = nullptr;
+    return a;
+}
+
+ism_status ism_coarse_tc_batch_table(ism_ctx *const *ctxs, int n, void **table, size_t *smem)
+{
+    std::vector<CoarseTcArgs> t(n);
+    size_t sm = 0;
+    for (int d = 0; d < n; ++d) {
+        ism_ctx *c = ctxs[d];
+        if (!ism_coarse_tc_supported(c)) return ISM_ERR_ARG;
+        t[d] = coarse_tc_args(c, c->rcpart, c->ec32, c->rcpart, &c->st->inner_done);
+        t[d].consumed = &c->st->skip_init;
+        sm = std::max(sm, (size_t)t[d].L.bytes);
+    }
+    if (cudaMalloc(table, n * sizeof(CoarseTcArgs)) != cudaSuccess) {
+        cudaGetLastError();
+        *table = nullptr;
+        return ISM_ERR_NOMEM;
+    }
+    ISM_CUDA_TRY(cudaMemcpy(*table, t.data(), n * sizeof(CoarseTcArgs), cudaMemcpyHostToDevice));
+    *smem = sm;
+    return ISM_OK;
+}
+
+ism_status ism_launch_coarse_tc_batch(cudaStream_t s, const void *table, int n, size_t smem)
+{
+    k_coarse_tc_batch<<<n, CT_THREADS, smem, s>>>((const CoarseTcArgs *)table);
+    return cudaGetLastError() == cudaSuccess ? ISM_OK : ISM_ERR_CUDA;
 }
 
 ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, const std::vector<double> &Qy,
@@ -333,15 +394,7 @@ ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, con
 ism_status ism_launch_coarse_tc(ism_ctx *ctx, const float *rc, bool from_parts, float *ec, float *rcpart,
                                 const int *skip)
 {
-    CoarseTcArgs a;
-    a.R = rc;
-    a.cst = (const unsigned char *)ctx->tc_block;
-    a.E = ec;
-    a.rcpart = rcpart;
-    a.L = tc_layout(ctx->ncx, ctx->ncy);
-    a.tcols = a.L.Np <= 32 ? 32 : 64;
-    a.skip = skip;
-    a.st = ctx->st;
+    const CoarseTcArgs a = coarse_tc_args(ctx, rc, ec, rcpart, skip);
     if (from_parts) k_coarse_tc<true><<<1, CT_THREADS, a.L.bytes, ctx->ws>>>(a);
     else k_coarse_tc<false><<<1, CT_THREADS, a.L.bytes, ctx->ws>>>(a);
     ISM_LAUNCH_CHECK(ctx);

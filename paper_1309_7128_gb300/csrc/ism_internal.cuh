@@ -146,3 +146,8 @@ ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, con
                                 const std::vector<double> &Minv);
 ism_status ism_launch_coarse_tc(ism_ctx *ctx, const float *rc, bool from_parts, float *ec, float *rcpart,
                                 const int *skip);
+// Batched ensemble: a device table of per-problem arguments (owned by the
+// caller, cudaFree) and the shared memory the launch needs; one CTA per
+// problem, problems outside an inner solve skip.
+ism_status ism_coarse_tc_batch_table(ism_ctx *const *ctxs, int n, void **table, size_t *smem);
+ism_status ism_launch_coarse_tc_batch(cudaStream_t s, const void *table, int n, size_t smem);

@@ -111,3 +111,20 @@ def test_batched_many_passes_per_cycle(nu):
         s1, c1, r1 = ism.ism_solve(ctxs[k], rhs[k], q, 1e-8, 100000)
         assert s1 == ism.ISM_OK and abs(c1 - cyc[k]) <= 2
         assert rel(host(ps[k]), host(q)) <= 1e-9
+
+
+def test_batched_tensor_core_and_cuda_core_coarse_agree():
+    """The ensemble with its coarse solves on the tensor cores (TF32, one CTA
+    per problem) and on the CUDA cores (FP32): both reach 1e-8 per problem
+    and agree to the refinement tolerance."""
+    shapes = batch_shapes(8, seed=5, lo=128, hi=512)
+    out = {}
+    for tcflag in (0, 1):
+        ctxs, rhs, ps, bs = make_batch(shapes, [16] * 8, [(0, 0, 0, 0)] * 7 + [(0, 1, 0, 0)], seed0=300,
+                                       coarse_tc=tcflag)
+        s, cyc, rr = ism.ism_solve_batched(ctxs, rhs, ps, 1e-8, 100000)
+        assert s == ism.ISM_OK and all(r <= 1e-8 for r in rr)
+        out[tcflag] = ([host(p) for p in ps], cyc)
+    for a, b in zip(out[0][0], out[1][0]):
+        assert rel(b, a) <= 1e-8
+    print("cycles CUDA cores", out[0][1], "tensor cores", out[1][1])
