@@ -103,7 +103,11 @@ const char *ism_status_str(ism_status s);
  *   nx, ny   fine cells; both multiples of `coarsen`, nx*ny <= 2^31.
  *   h        cell size (used by proj_step only; > 0).
  *   bc       host, 4 ints (ism_bc) for the west, east, south, north faces.
- *   coarsen  m in {8, 16, 32}: coarse cells are m x m blocks of fine cells.
+ *   coarsen  m in {8, 16, 32}: coarse cells are m x m blocks of fine cells;
+ *            0: the library picks 16 or 32 (those dividing nx and ny with at
+ *            least 2 coarse cells per direction) by timing two solves of an
+ *            internal test right-hand side to 1e-8 with each (synchronises;
+ *            about four solves of setup time).  ism_coarsening reports m.
  *   prec     ism_precision.
  *   stream   cudaStream_t to order all work on (NULL = legacy default stream).
  *   out      host; receives the new context.
@@ -146,6 +150,9 @@ ism_status ism_solve(ism_ctx *ctx, const double *rhs, double *p, double tol,
  * for the duration of the call.  Synchronises. */
 ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, int max_cycles,
                         ism_options *best);
+
+/* Coarsening factor m of a context (0 for NULL). */
+int ism_coarsening(const ism_ctx *ctx);
 
 /* Relative-residual history of the last solve: one entry per cycle (FP64)
  * or per refinement iteration (mixed), starting with the initial guess.
@@ -310,6 +317,17 @@ ism_status proj_rollout_grad(ism_ctx *ctx, const float *u0, const float *v0, con
 ism_status ism_solve_batched(int n, ism_ctx *const *ctxs, const double *const *rhs,
                              double *const *p, double tol, int max_cycles,
                              int *cycles_out, double *relres_out);
+
+/* ism_autotune_batched -- choose the sweeps per cycle of a batched ensemble
+ * (nu in {16, 32, 64, 128}, 8 sweeps per fused pass, the same for every
+ * problem as ism_solve_batched requires) and whether its coarse solves run on
+ * the tensor cores (coarse_tc), by timing ism_solve_batched on the given
+ * right-hand sides; p: host array of n device iterates, overwritten
+ * (zero initial guesses).  Sets the winner in every context (on failure the
+ * options are restored) and returns it in *nu_out (host, may be NULL).  No
+ * counterpart in the paper.  Synchronises. */
+ism_status ism_autotune_batched(int n, ism_ctx *const *ctxs, const double *const *rhs,
+                                double *const *p, double tol, int *nu_out);
 
 #ifdef __cplusplus
 }

@@ -261,8 +261,8 @@ static EigenHost build_eigen(const ism_ctx *ctx)
     return E;
 }
 
-extern "C" ism_status ism_setup(int nx, int ny, double h, const int bc[4], int coarsen,
-                                ism_precision prec, void *stream, ism_ctx **out)
+ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarsen, ism_precision prec,
+                           void *stream, ism_ctx **out)
 {
     if (!out || !bc) return ISM_ERR_ARG;
     if (coarsen != 8 && coarsen != 16 && coarsen != 32) return ISM_ERR_ARG;

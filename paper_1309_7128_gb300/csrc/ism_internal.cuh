@@ -122,6 +122,11 @@ struct ism_ctx {
         if (cudaGetLastError() != cudaSuccess) return ISM_ERR_CUDA;           \
     } while (0)
 
+// ism_setup for a given coarsening factor (8, 16, 32); ism_setup adds the
+// autotuned choice (coarsen = 0, ism_tune.cu).
+ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarsen, ism_precision prec,
+                           void *stream, ism_ctx **out);
+
 // Order ctx->ws after the caller's stream, and the caller's stream after ws.
 ism_status ism_enter(ism_ctx *ctx);
 ism_status ism_leave(ism_ctx *ctx);

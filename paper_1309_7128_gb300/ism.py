@@ -63,6 +63,8 @@ _SIGS = {
     "ism_residual_restrict_noalloc": (_I, [_I, _I, _I, C.POINTER(C.c_int), _VP, _VP, _VP, _VP, _VP]),
     "ism_solve_batched": (_I, [_I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _D, _I,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "ism_coarsening": (_I, [_VP]),
+    "ism_autotune_batched": (_I, [_I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _D, C.POINTER(C.c_int)]),
     "proj_step_adjoint": (_I, [_VP, _VP, _VP, _D, _D, _VP, _VP, _VP]),
     "ism_enstrophy": (_I, [_VP, _VP, _VP, C.POINTER(C.c_double), _VP, _VP]),
     "proj_rollout_grad": (_I, [_VP, _VP, _VP, _VP, _D, _D, _I, _I, C.POINTER(C.c_double),
@@ -139,7 +141,9 @@ def ism_setup(nx, ny, h, bc, coarsen, prec=ISM_FP64, stream=None):
     out = C.c_void_p()
     s = L.ism_setup(int(nx), int(ny), float(h), bca, int(coarsen), int(prec),
                     _stream(stream) if stream is not False else C.c_void_p(0), C.byref(out))
-    return s, (Ctx(out.value, nx, ny, coarsen, prec) if s == ISM_OK else None)
+    if s != ISM_OK:
+        return s, None
+    return s, Ctx(out.value, nx, ny, L.ism_coarsening(out), prec)
 
 
 def ism_get_options(ctx):
@@ -264,3 +268,19 @@ def proj_rollout_grad(ctx, u0, v0, p0, dt, nu, steps, every=20, gu=None, gv=None
     s = lib().proj_rollout_grad(ctx.handle, _ptr(u0), _ptr(v0), _ptr(p0), float(dt), float(nu),
                                 int(steps), int(every), C.byref(val), _ptr(gu), _ptr(gv), _ptr(gp))
     return s, val.value
+
+
+def ism_coarsening(ctx):
+    """Coarsening factor m of the context (as chosen by ism_setup)."""
+    return lib().ism_coarsening(ctx.handle)
+
+
+def ism_autotune_batched(ctxs, rhs, p, tol=1e-8):
+    """Returns (status, nu chosen for the ensemble)."""
+    n = len(ctxs)
+    ca = (C.c_void_p * n)(*[c.handle for c in ctxs])
+    ra = (C.c_void_p * n)(*[t.data_ptr() for t in rhs])
+    pa = (C.c_void_p * n)(*[t.data_ptr() for t in p])
+    nu = C.c_int(0)
+    s = lib().ism_autotune_batched(n, ca, ra, pa, float(tol), C.byref(nu))
+    return s, nu.value

@@ -36,6 +36,8 @@ def test_status_strings(L):
     (64, 64, 1.0, (0, 2, 0, 0), 16),     # bad face type
     (0, 64, 1.0, (0, 0, 0, 0), 16),      # empty grid
     (64 * 2048, 64, 1.0, (0, 0, 0, 0), 32),  # coarse grid wider than 1024
+    (100, 64, 1.0, (0, 0, 0, 0), 0),     # autotuned coarsening: neither 16 nor 32 divides nx
+    (64, 64, 0.0, (0, 0, 0, 0), 0),      # autotuned coarsening, h <= 0
 ])
 def test_setup_rejects_bad_arguments(L, args):
     nx, ny, h, bc, m = args

@@ -128,3 +128,18 @@ def test_batched_tensor_core_and_cuda_core_coarse_agree():
     for a, b in zip(out[0][0], out[1][0]):
         assert rel(b, a) <= 1e-8
     print("cycles CUDA cores", out[0][1], "tensor cores", out[1][1])
+
+
+def test_autotune_batched_sets_a_common_nu():
+    shapes = batch_shapes(6, seed=9, lo=128, hi=384)
+    ctxs, rhs, ps, bs = make_batch(shapes, [16] * 6, [(0, 0, 0, 0)] * 6, seed0=500)
+    s, nu = ism.ism_autotune_batched(ctxs, rhs, ps, 1e-8)
+    assert s == ism.ISM_OK and nu in (16, 32, 64, 128)
+    assert all(ism.ism_get_options(c).nu == nu for c in ctxs)
+    for p in ps:
+        p.zero_()
+    s, cyc, rr = ism.ism_solve_batched(ctxs, rhs, ps, 1e-8, 100000)
+    assert s == ism.ISM_OK and all(r <= 1e-8 for r in rr)
+    for k, (nx, ny) in enumerate(shapes):
+        p_ex, _, _ = O.OracleISM(nx, ny, 16, nu=nu).solve(bs[k], tol=1e-11)
+        assert rel(host(ps[k]), p_ex) <= 1e-9

@@ -178,3 +178,19 @@ def test_autotune_picks_a_working_candidate(prec):
     p = dev64(np.zeros((ny, nx)))
     s, c, r = ism.ism_solve(ctx, dev64(b), p, 1e-8, 100000)
     assert s == ism.ISM_OK and r <= 1e-8 and rel(host(p), p_ex) <= 1e-9
+
+
+@pytest.mark.parametrize("nx,ny,expect", [(512, 512, (16, 32)), (144, 96, (16,)), (96, 64, (16, 32))])
+def test_setup_chooses_coarsening(nx, ny, expect):
+    """coarsen = 0: the library times solves with 16h and 32h (those that
+    divide the grid) and keeps the faster; the context then solves to 1e-8."""
+    s, ctx = ism.ism_setup(nx, ny, 1.0 / nx, (0, 0, 0, 0), 0, ism.ISM_MIXED)
+    assert s == ism.ISM_OK
+    m = ism.ism_coarsening(ctx)
+    assert m in expect and ctx.m == m
+    b = smooth_rhs(nx, ny, 31)
+    p = dev64(np.zeros((ny, nx)))
+    st, cyc, rr = ism.ism_solve(ctx, dev64(b), p, 1e-8, 100000)
+    assert st == ism.ISM_OK and rr <= 1e-8
+    p_ex, _, _ = O.OracleISM(nx, ny, m, nu=ism.ism_get_options(ctx).nu).solve(b, tol=1e-11)
+    assert rel(host(p), p_ex) <= 1e-9
