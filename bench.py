@@ -295,7 +295,7 @@ def run_ours(args):
     sampler = ClockSampler(f"GPU-{gpu_id}" if gpu_id else str(local))
     _, cyc0, launches0 = ism.ism_last_counts(ctx)
     launches0 = ism.ism_last_counts(ctx)[2]
-    per_step, cycles, outers = [], [], []
+    per_step, cycles, outers, relres = [], [], [], []
     sampler.start()
     barrier(world)
     torch.cuda.synchronize()
@@ -312,6 +312,7 @@ def run_ours(args):
         o, c, _ = ism.ism_last_counts(ctx)
         cycles.append(c)
         outers.append(o)
+        relres.append(ism.ism_last_history(ctx, 64)[-1])
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
@@ -395,6 +396,7 @@ def run_ours(args):
                     "cycles_per_solve": fp64_cycles},
            "mixed_over_fp64": round(value / fp64_value, 2),
            "solve": {"cycles_per_solve": cycles, "refinements_per_solve": outers,
+                     "final_relres_max": max(relres),
                      "mcell_cycles_per_s": round(world * N_GRID * N_GRID * sum(cycles) / (total_ms / 1000.0) / 1e6, 1)},
            "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches)}
 
