@@ -159,3 +159,33 @@ def _dp_view(addr, ny, nx):
     class _Arr:
         __cuda_array_interface__ = {"shape": (ny, nx), "typestr": "<f8", "data": (addr, False), "version": 3}
     return torch.as_tensor(_Arr(), device="cuda:0")
+
+
+def test_cavity_re1000_steady_centrelines_against_table():
+    """Physics of the whole projection step (predictor, ISM pressure solve,
+    correction): the 256 x 256 lid-driven cavity at Re = 1000 run from rest
+    to t = 40 (close to steady) gives the centreline velocity extrema of the
+    paper's accuracy table (tests/golden/cavity_re1000_centrelines.json)
+    within the spread of the references printed there: within 2.5% of the
+    spectral values and of Ghia's, within 5% of the paper's own 512 x 512
+    result."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cavity_re1000_centrelines.json")))
+    n, nu = 256, 1e-3
+    h = 1.0 / n
+    dt = 0.9 * min(0.4 * h, 0.25 * h * h / nu, 2 * nu)
+    ctx = setup(n, n, 16, (0, 0, 0, 0), prec=ism.ISM_MIXED, h=h)
+    ism.check(ism.ism_set_flow(ctx, CAVITY, (0, 0, 0, 1.0), None, 1.0))
+    ism.check(ism.ism_proj_tol(ctx, 1e-8, 100000, True))
+    u = torch.zeros((n, n + 1), dtype=torch.float32, device="cuda:0")
+    v = torch.zeros((n + 1, n), dtype=torch.float32, device="cuda:0")
+    p = torch.zeros((n, n), dtype=torch.float32, device="cuda:0")
+    for _ in range(int(40.0 / dt)):
+        assert ism.proj_step(ctx, u, v, p, dt, nu) == ism.ISM_OK
+    uc, vc = host(u)[:, n // 2], host(v)[n // 2, :]
+    got = np.array([-uc.min(), vc.min(), vc.max()])
+    print("256^2 Re=1000 t=40 centreline extrema:", np.round(got, 4))
+    for ref, tol in (("Botella spectral 160x160", 0.025), ("Ghia 129x129", 0.025), ("paper 512x512", 0.05)):
+        want = np.array(gold["rows"][ref])
+        assert np.all(np.abs(got - want) <= tol * np.abs(want)), (ref, got, want)
