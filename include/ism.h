@@ -63,7 +63,9 @@ typedef enum {
 
 typedef enum {
     ISM_COARSE_ISM = 0,   /* interpolated nine-point coarse stencil, bilinear correction (Sec. 3.3) */
-    ISM_COARSE_ACM = 1    /* summed five-point coarse equations, constant correction (Sec. 3.2) */
+    ISM_COARSE_ACM = 1,   /* summed five-point coarse equations, constant correction (Sec. 3.2) */
+    ISM_COARSE_GMG = 2    /* five-point operator re-discretised on the coarse grid, bilinear
+                             correction (the comparator of Sec. 4.3.2) */
 } ism_coarse_kind;
 
 /* Velocity boundary kinds of the projection step, per face. */

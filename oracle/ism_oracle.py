@@ -137,8 +137,19 @@ def prolong_const_add(p, q, m):
 
 
 def coarse_operator(nx, ny, m, bc, kind="ism"):
-    """Dense coarse operator A_c (Sec. 3.3); kind 'ism' or 'acm'."""
+    """Dense coarse operator A_c; kind 'ism' (face-flux sums of the bilinear
+    interpolant, Sec. 3.3, Eq. 5-7), 'acm' (face-flux sums of the piecewise
+    constant interpolant, Sec. 3.2) or 'gmg' (the five-point operator
+    re-discretised on the coarse grid, the comparator of Sec. 3.3 / Table 5:
+    the fine operator's rule applied to coarse cells)."""
     nc = (nx // m) * (ny // m)
+    if kind == "gmg":
+        ncx, ncy = nx // m, ny // m
+        eye = np.eye(nc)
+        Ac = np.empty((nc, nc), dtype=np.float64)
+        for k in range(nc):
+            Ac[:, k] = apply_af(eye[k].reshape(ncy, ncx), bc).ravel()
+        return Ac
     Ac = np.empty((nc, nc), dtype=np.float64)
     rc = lib().or_coarse_operator(nx, ny, m, _bc(bc), 0 if kind == "ism" else 1, Ac)
     if rc != 0:
@@ -151,7 +162,9 @@ def coarse_operator(nx, ny, m, bc, kind="ism"):
 # --------------------------------------------------------------------------
 
 class OracleISM:
-    """Two-level ISM (kind='ism') or two-level ACM (kind='acm') solver.
+    """Two-level ISM (kind='ism'), ACM (kind='acm') or GMG (kind='gmg',
+    re-discretised five-point coarse operator with the bilinear correction)
+    solver.
 
     Sec. 3.3-3.4: aggressive m x m coarsening (16h / 32h), interpolated
     nine-point coarse stencil (ISM) or summed five-point coarse equations with
@@ -182,7 +195,7 @@ class OracleISM:
         return (-x).reshape(rc.shape)
 
     def _correct(self, p, ec):
-        if self.kind == "ism":
+        if self.kind != "acm":
             prolong_add(p, ec, self.m, self.bc)
         else:
             prolong_const_add(p, ec, self.m)

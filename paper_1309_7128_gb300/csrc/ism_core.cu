@@ -191,9 +191,11 @@ static ism_status upload_coarse(ism_ctx *ctx, const EigenHost &E)
         for (int k = 0; k < ncy; ++k) QyT[(size_t)k * ncy + i] = E.Qy[(size_t)i * ncy + k];
     for (int l = 0; l < ncy; ++l)
         for (int k = 0; k < ncx; ++k) {
-            double mu = (ctx->opt.kind == ISM_COARSE_ACM)
-                            ? ctx->m * ((E.lx[k] - 4.0) + (E.ly[l] - 4.0))
-                            : 0.25 * E.lx[k] * E.ly[l] - 4.0;
+            // eigenvalues of A_c in the separable basis: ISM 1/4 S_y x S_x - 4 I;
+            // five-point operators (S_x - 4 I) + (S_y - 4 I), times m for ACM
+            double mu = (ctx->opt.kind == ISM_COARSE_ISM) ? 0.25 * E.lx[k] * E.ly[l] - 4.0
+                                                          : (E.lx[k] - 4.0) + (E.ly[l] - 4.0);
+            if (ctx->opt.kind == ISM_COARSE_ACM) mu *= ctx->m;
             Minv[(size_t)l * ncx + k] = fabs(mu) < 1e-10 ? 0.0 : 1.0 / mu;
         }
     auto up = [&](double *d64, float *d32, const std::vector<double> &h) -> ism_status {
@@ -395,7 +397,7 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     if (!ctx || !o) return ISM_ERR_ARG;
     if (o->nu < 1 || o->nu > 256) return ISM_ERR_ARG;
     if (o->sweeps_per_pass < 1 || o->sweeps_per_pass > SMAXK || o->nu % o->sweeps_per_pass) return ISM_ERR_ARG;
-    if (o->kind != ISM_COARSE_ISM && o->kind != ISM_COARSE_ACM) return ISM_ERR_ARG;
+    if (o->kind != ISM_COARSE_ISM && o->kind != ISM_COARSE_ACM && o->kind != ISM_COARSE_GMG) return ISM_ERR_ARG;
     if (o->max_outer < 1 || o->inner_max < 1 || o->check_every < 1 || o->check_every > 4096) return ISM_ERR_ARG;
     if (o->use_graphs < 0 || o->use_graphs > 2) return ISM_ERR_ARG;
     if (o->coarse_tc < 0 || o->coarse_tc > 1) return ISM_ERR_ARG;

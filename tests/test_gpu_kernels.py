@@ -12,6 +12,7 @@ from tests.gpu_util import dev32, dev64, ensure_built, host, ism, setup
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(160, 96, 32), (96, 160, 16), (128, 64, 8), (256, 192, 32)]
+KINDS = {"ism": ism.ISM_COARSE_ISM, "acm": ism.ISM_COARSE_ACM, "gmg": ism.ISM_COARSE_GMG}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -78,7 +79,7 @@ def test_residual_restrict(nx, ny, m, bc):
 
 @pytest.mark.parametrize("nx,ny,m", SHAPES)
 @pytest.mark.parametrize("bc", ALL_BCS)
-@pytest.mark.parametrize("kind", ["ism", "acm"])
+@pytest.mark.parametrize("kind", ["ism", "acm", "gmg"])
 def test_coarse_solve(nx, ny, m, bc, kind):
     ncx, ncy = nx // m, ny // m
     rc = random_field(ncx, ncy, 7)
@@ -88,7 +89,7 @@ def test_coarse_solve(nx, ny, m, bc, kind):
     # FP64; FP32 on the CUDA cores; TF32 on the tensor cores (tcgen05): four
     # chained products of operands rounded to 2^-11 relative
     for prec, tcflag, tol in ((ism.ISM_FP64, 0, 1e-11), (ism.ISM_MIXED, 0, 2e-5), (ism.ISM_MIXED, 1, 1e-2)):
-        ctx = setup(nx, ny, m, bc, prec=prec, kind=0 if kind == "ism" else 1, coarse_tc=tcflag)
+        ctx = setup(nx, ny, m, bc, prec=prec, kind=KINDS[kind], coarse_tc=tcflag)
         mk = dev64 if prec == ism.ISM_FP64 else dev32
         ec = mk(np.zeros_like(rc))
         ism.check(ism.ism_coarse_solve(ctx, mk(rc), ec))
@@ -101,16 +102,16 @@ def test_coarse_solve(nx, ny, m, bc, kind):
 
 @pytest.mark.parametrize("nx,ny,m", SHAPES)
 @pytest.mark.parametrize("bc", ALL_BCS)
-@pytest.mark.parametrize("kind", ["ism", "acm"])
+@pytest.mark.parametrize("kind", ["ism", "acm", "gmg"])
 def test_prolong_add(nx, ny, m, bc, kind):
     q = random_field(nx // m, ny // m, 8)
     p = random_field(nx, ny, 9)
     ref = p.copy()
-    if kind == "ism":
+    if kind != "acm":                     # ISM and GMG share the bilinear correction
         O.prolong_add(ref, q, m, bc)
     else:
         O.prolong_const_add(ref, q, m)
-    ctx = setup(nx, ny, m, bc, kind=0 if kind == "ism" else 1)
+    ctx = setup(nx, ny, m, bc, kind=KINDS[kind])
     pd = dev64(p)
     ism.check(ism.ism_prolong_add(ctx, dev64(q), pd))
     np.testing.assert_allclose(host(pd), ref, rtol=0, atol=1e-14 * np.abs(ref).max())

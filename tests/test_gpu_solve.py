@@ -59,6 +59,22 @@ def test_fp64_acm_matches_oracle():
     assert rel(p, p_ref) <= 1e-12
 
 
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (0, 1, 0, 0)])
+def test_gmg_matches_oracle(bc):
+    """The GMG comparator (re-discretised five-point coarse operator,
+    bilinear correction): FP64 with the oracle's cycle count, mixed to the
+    refinement tolerance."""
+    nx, ny = 256, 192
+    b = smooth_rhs(nx, ny, 2) + (1e-6 if any(bc) else 0.0)
+    p_ref, c_ref, _ = O.OracleISM(nx, ny, 16, bc, kind="gmg").solve(b, tol=1e-8)
+    s, p, c, r, h, _ = gpu_solve(b, nx, ny, 16, bc, ism.ISM_FP64, kind=ism.ISM_COARSE_GMG)
+    assert s == ism.ISM_OK and c == c_ref
+    assert rel(p, p_ref) <= 1e-12
+    p_ex, _, _ = O.OracleISM(nx, ny, 16, bc, kind="gmg").solve(b, tol=1e-11)
+    s, p, c, r, h, _ = gpu_solve(b, nx, ny, 16, bc, ism.ISM_MIXED, kind=ism.ISM_COARSE_GMG)
+    assert s == ism.ISM_OK and r <= 1e-8 and rel(p, p_ex) <= 1e-9
+
+
 def test_config0_ism_beats_acm_on_gpu():
     b = smooth_rhs(256, 256, 0)
     c_ism = gpu_solve(b, 256, 256, 16, (0, 0, 0, 0), ism.ISM_FP64)[2]

@@ -206,6 +206,16 @@ def test_acm_coarse_operator_is_scaled_five_point(bc):
     np.testing.assert_allclose(Ac, m * dense_laplacian(ncx, ncy, bc), atol=1e-12)
 
 
+@pytest.mark.parametrize("bc", ALL_BCS)
+def test_gmg_coarse_operator_is_rediscretised_five_point(bc):
+    """GMG comparator: the five-point operator of the coarse grid (weight 1),
+    i.e. the ACM operator divided by m (two independent constructions)."""
+    m, ncx, ncy = 16, 5, 3
+    Ag = O.coarse_operator(ncx * m, ncy * m, m, bc, "gmg")
+    np.testing.assert_allclose(Ag, dense_laplacian(ncx, ncy, bc), atol=1e-12)
+    np.testing.assert_allclose(Ag, O.coarse_operator(ncx * m, ncy * m, m, bc, "acm") / m, atol=1e-12)
+
+
 @pytest.mark.parametrize("bc", [(0, 0, 0, 0), (0, 1, 0, 0)])
 def test_coarse_operator_equals_R_Af_P(bc):
     """The face-flux construction equals the product R A_f P of the block-sum
@@ -303,6 +313,22 @@ def test_ism_converges_in_fewer_cycles_than_acm():
     ism = O.OracleISM(256, 256, 16, kind="ism", nu=8).solve(b, tol=1e-8)[1]
     acm = O.OracleISM(256, 256, 16, kind="acm", nu=8).solve(b, tol=1e-8)[1]
     assert ism < acm / 2, (ism, acm)
+
+
+def test_ism_converges_at_least_as_fast_as_gmg():
+    """The interpolated nine-point coarse stencil against the re-discretised
+    five-point one (same restriction, bilinear correction and smoothing).
+    With the exact coarse solve of this cycle both take the same number of
+    cycles here and ISM's asymptotic factor is slightly smaller; the paper's
+    advantage of ISM (Sec. 4.3.2) is measured with its accommodative cycle
+    and iterative coarse solves, which this cycle does not use."""
+    b = smooth_rhs(256, 256, 0)
+    res = {}
+    for kind in ("ism", "gmg"):
+        p, c, h = O.OracleISM(256, 256, 16, kind=kind, nu=4).solve(b, tol=1e-8)
+        res[kind] = (c, (h[-1] / h[1]) ** (1.0 / (len(h) - 2)))
+    assert res["ism"][0] <= res["gmg"][0], res
+    assert res["ism"][1] <= res["gmg"][1], res
 
 
 def test_mixed_refinement_reaches_tolerance():
