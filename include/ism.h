@@ -64,8 +64,12 @@ typedef enum {
 typedef enum {
     ISM_COARSE_ISM = 0,   /* interpolated nine-point coarse stencil, bilinear correction (Sec. 3.3) */
     ISM_COARSE_ACM = 1,   /* summed five-point coarse equations, constant correction (Sec. 3.2) */
-    ISM_COARSE_GMG = 2    /* five-point operator re-discretised on the coarse grid, bilinear
+    ISM_COARSE_GMG = 2,   /* five-point operator re-discretised on the coarse grid, bilinear
                              correction (the comparator of Sec. 4.3.2) */
+    ISM_COARSE_ACMV = 3   /* additive correction as a deep V-cycle (Sec. 3.2, the paper's ACM
+                             comparator): 2 x 2 agglomeration levels down to the coarsening factor,
+                             piecewise-constant corrections, one red-black sweep per intermediate
+                             level, exact solve at the coarsest; FP64 contexts only */
 } ism_coarse_kind;
 
 /* Velocity boundary kinds of the projection step, per face. */

@@ -306,6 +306,65 @@ class OracleISM:
         return p, outer, inner_total, hist
 
 
+class OracleACMV:
+    """The additive correction multigrid of Sec. 3.2 as a deep V-cycle (the
+    paper's comparator, Sec. 4.3): coarse equations are sums of 2 x 2 blocks
+    of the finer equations (agglomeration), the correction is piecewise
+    constant, levels go from h down to the coarsening factor m = 2^L.
+
+    Cycle (reading: correction scheme, no pre-smoothing, one post-smoothing
+    sweep per intermediate level, exact solve at the coarsest level):
+    r_0 = b - A_f p; r_{l+1} = R_2 r_l; e_L = A_L^+ r_L;
+    for l = L-1 .. 1: e_l = P_2 e_{l+1}, one red-black sweep on A_l e_l = r_l;
+    p += P_2 e_1; nu sweeps on A_f p = b; mean of p removed when all faces
+    are Neumann.  A_l = 2^l x (five-point operator of level l) (the
+    agglomerated operator), so a sweep on level l is a five-point sweep with
+    right-hand side r_l / 2^l."""
+
+    def __init__(self, nx, ny, m, bc=(0, 0, 0, 0), nu=8):
+        if nx % m or ny % m or m & (m - 1) or m < 2:
+            raise ValueError("m must be a power of two dividing the grid")
+        self.nx, self.ny, self.m, self.nu = nx, ny, m, nu
+        self.L = m.bit_length() - 1
+        self.bc = _bc(bc)
+        self.singular = not np.any(self.bc)
+        self.top = OracleISM(nx, ny, m, bc, kind="acm", nu=nu)     # exact level-L solve of A_L = m x five-point
+
+    def cycle(self, p, b):
+        r = residual(p, b, self.bc)
+        rs = [r]
+        for _ in range(self.L):
+            rs.append(restrict(rs[-1], 2))
+        e = self.top.coarse_solve(rs[self.L])
+        for lev in range(self.L - 1, 0, -1):
+            el = np.zeros_like(rs[lev])
+            prolong_const_add(el, e, 2)
+            rbgs_sweep(el, rs[lev] / float(2 ** lev), self.bc)
+            e = el
+        prolong_const_add(p, e, 2)
+        for _ in range(self.nu):
+            rbgs_sweep(p, b, self.bc)
+        if self.singular:
+            p -= p.mean()
+
+    def solve(self, b, p0=None, tol=1e-8, max_cycles=10000):
+        """FP64 solve.  Returns (p, cycles, relres_history)."""
+        b = self.top.prepare_rhs(b)
+        p = np.zeros_like(b) if p0 is None else np.array(p0, dtype=np.float64, order="C", copy=True)
+        if self.singular:
+            p -= p.mean()
+        bn = np.linalg.norm(b)
+        if bn == 0.0:
+            return np.zeros_like(b), 0, [0.0]
+        hist = [np.linalg.norm(residual(p, b, self.bc)) / bn]
+        cycles = 0
+        while hist[-1] > tol and cycles < max_cycles:
+            self.cycle(p, b)
+            cycles += 1
+            hist.append(np.linalg.norm(residual(p, b, self.bc)) / bn)
+        return p, cycles, hist
+
+
 # --------------------------------------------------------------------------
 # projection time step (Sec. 2.2-2.3, Eq. 3-4)
 # --------------------------------------------------------------------------

@@ -195,7 +195,7 @@ static ism_status upload_coarse(ism_ctx *ctx, const EigenHost &E)
             // five-point operators (S_x - 4 I) + (S_y - 4 I), times m for ACM
             double mu = (ctx->opt.kind == ISM_COARSE_ISM) ? 0.25 * E.lx[k] * E.ly[l] - 4.0
                                                           : (E.lx[k] - 4.0) + (E.ly[l] - 4.0);
-            if (ctx->opt.kind == ISM_COARSE_ACM) mu *= ctx->m;
+            if (ctx->opt.kind == ISM_COARSE_ACM || ctx->opt.kind == ISM_COARSE_ACMV) mu *= ctx->m;
             Minv[(size_t)l * ncx + k] = fabs(mu) < 1e-10 ? 0.0 : 1.0 / mu;
         }
     auto up = [&](double *d64, float *d32, const std::vector<double> &h) -> ism_status {
@@ -240,6 +240,10 @@ extern "C" void ism_destroy(ism_ctx *ctx)
                     ctx->tc_block};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (int l = 0; l < 6; ++l) {
+        if (ctx->lvl_r[l]) cudaFree(ctx->lvl_r[l]);
+        if (ctx->lvl_e[l]) cudaFree(ctx->lvl_e[l]);
+    }
     for (int K = 0; K <= SMAXK; ++K)
         for (int r = 0; r < 2; ++r)
             if (ctx->plans[K][r].edge) cudaFree(ctx->plans[K][r].edge);
@@ -397,13 +401,25 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     if (!ctx || !o) return ISM_ERR_ARG;
     if (o->nu < 1 || o->nu > 256) return ISM_ERR_ARG;
     if (o->sweeps_per_pass < 1 || o->sweeps_per_pass > SMAXK || o->nu % o->sweeps_per_pass) return ISM_ERR_ARG;
-    if (o->kind != ISM_COARSE_ISM && o->kind != ISM_COARSE_ACM && o->kind != ISM_COARSE_GMG) return ISM_ERR_ARG;
+    if (o->kind < ISM_COARSE_ISM || o->kind > ISM_COARSE_ACMV) return ISM_ERR_ARG;
+    if (o->kind == ISM_COARSE_ACMV && ctx->prec != ISM_FP64) return ISM_ERR_ARG;
     if (o->max_outer < 1 || o->inner_max < 1 || o->check_every < 1 || o->check_every > 4096) return ISM_ERR_ARG;
     if (o->use_graphs < 0 || o->use_graphs > 2) return ISM_ERR_ARG;
     if (o->coarse_tc < 0 || o->coarse_tc > 1) return ISM_ERR_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
     const int kind_changed = o->kind != ctx->opt.kind;
     cudaStreamSynchronize(ctx->ws);
+    if (o->kind == ISM_COARSE_ACMV && !ctx->lvl_r[1]) {
+        // levels 1 .. L-1 of the V-cycle (level l: (nx >> l) x (ny >> l))
+        for (int l = 1; (1 << l) < ctx->m; ++l) {
+            const size_t b = (size_t)(ctx->nx >> l) * (ctx->ny >> l) * 8;
+            if (cudaMalloc((void **)&ctx->lvl_r[l], b) != cudaSuccess ||
+                cudaMalloc((void **)&ctx->lvl_e[l], b) != cudaSuccess) {
+                cudaGetLastError();
+                return ISM_ERR_NOMEM;
+            }
+        }
+    }
     ctx->opt = *o;
     free_graphs(ctx);
     if (kind_changed) return upload_coarse(ctx, build_eigen(ctx));
@@ -584,8 +600,57 @@ static ism_status launch_sweep32(ism_ctx *ctx, SweepArgs a, bool prolong, bool r
 
 // One FP64 cycle; every kernel returns at once when st->done is set.  cond:
 // while-node handle that the residual's control sets (0 outside such a node).
+// Residual, its 2 x 2 block sums (level 1 of the V-cycle) and the control.
+static ism_status launch_resid2(ism_ctx *ctx, int ctl_mode, unsigned long long cond)
+{
+    const int ncx = ctx->nx / 2, ncy = ctx->ny / 2;
+    k_resid2<double><<<row_grid(ncx, ncy, 128), 128, 0, ctx->ws>>>(
+        ctx->p64[0], ctx->b64, ctx->lvl_r[1], ctx->partials, ctx->nx, ctx->ny, ctx->bcmask, &ctx->st->done,
+        ctx->st, ctl_mode, cond);
+    ISM_LAUNCH_CHECK(ctx);
+    return ISM_OK;
+}
+
+// One cycle of the deep additive-correction V-cycle (FP64, see ISM_COARSE_ACMV).
+static ism_status acmv_cycle(ism_ctx *ctx, unsigned long long cond)
+{
+    const int *skip = &ctx->st->done;
+    int L = 0;
+    while ((1 << L) < ctx->m) ++L;
+    // down: r_{l+1} = R_2 r_l (r_1 comes from the previous residual), r_L -> rc64
+    for (int l = 1; l < L; ++l) {
+        const int nxl = ctx->nx >> l, nyl = ctx->ny >> l;
+        double *out = (l + 1 < L) ? ctx->lvl_r[l + 1] : ctx->rc64;
+        k_restrict2<double><<<row_grid(nxl / 2, nyl / 2, 128), 128, 0, ctx->ws>>>(ctx->lvl_r[l], out, nxl, nyl, skip);
+        ISM_LAUNCH_CHECK(ctx);
+    }
+    // coarsest: A_L = m x five-point, exact
+    TRY((launch_coarse<double, false>(ctx, ctx->rc64, ctx->ec64, ctx->T64, skip)));
+    // up: e_l = P_2 e_{l+1}, one sweep on (2^l five-point) e_l = r_l
+    for (int l = L - 1; l >= 1; --l) {
+        const int nxl = ctx->nx >> l, nyl = ctx->ny >> l;
+        const double *ec = (l + 1 < L) ? ctx->lvl_e[l + 1] : ctx->ec64;
+        k_inject2<double><<<row_grid(nxl, nyl, 128), 128, 0, ctx->ws>>>(ctx->lvl_e[l], ec, nxl, nyl, skip);
+        ISM_LAUNCH_CHECK(ctx);
+        const dim3 g = row_grid((nxl + 1) / 2, nyl, 128);
+        for (int col = 0; col < 2; ++col) {
+            k_rbgs_colour<double><<<g, 128, 0, ctx->ws>>>(ctx->lvl_e[l], ctx->lvl_r[l], nxl, nyl, ctx->bcmask, col,
+                                                           skip, 1.0 / (double)(1 << l));
+            ISM_LAUNCH_CHECK(ctx);
+        }
+    }
+    // p = p - mean + P_2 e_1, nu sweeps, residual (next r_1) with the control
+    k_prolong<double><<<row_grid(ctx->nx, ctx->ny, 128), 128, 0, ctx->ws>>>(
+        ctx->p64[0], ctx->lvl_e[1], ctx->nx, ctx->ny, 2, ctx->nx / 2, ctx->ny / 2, ctx->bcmask, ISM_COARSE_ACM,
+        ctx->st, ctx->singular, skip);
+    ISM_LAUNCH_CHECK(ctx);
+    TRY(launch_sweeps<double>(ctx, ctx->p64[0], ctx->b64, ctx->opt.nu, skip));
+    return launch_resid2(ctx, CTL_FP64_AFTER, cond);
+}
+
 static ism_status fp64_cycle(ism_ctx *ctx, unsigned long long cond = 0)
 {
+    if (ctx->opt.kind == ISM_COARSE_ACMV) return acmv_cycle(ctx, cond);
     const int *skip = &ctx->st->done;
     TRY((launch_coarse<double, false>(ctx, ctx->rc64, ctx->ec64, ctx->T64, skip)));
     k_prolong<double><<<row_grid(ctx->nx, ctx->ny, 128), 128, 0, ctx->ws>>>(
@@ -840,7 +905,8 @@ static ism_status build_cond_mixed(ism_ctx *ctx)
 
 static ism_status solve_fp64(ism_ctx *ctx)
 {
-    TRY(launch_resid<double>(ctx, ctx->p64[0], ctx->b64, ctx->rc64, nullptr, CTL_FP64_INIT));
+    if (ctx->opt.kind == ISM_COARSE_ACMV) TRY(launch_resid2(ctx, CTL_FP64_INIT, 0));
+    else TRY(launch_resid<double>(ctx, ctx->p64[0], ctx->b64, ctx->rc64, nullptr, CTL_FP64_INIT));
     TRY(read_state(ctx));
     if (!ctx->st_host->done) {
         if (ctx->opt.use_graphs == 2) {

@@ -68,6 +68,7 @@ struct ism_ctx {
     double *rc64, *ec64, *T64; // coarse residual, correction, intermediate
     float *rc32, *ec32, *T32;
     float *rcpart;             // 4 partial block sums per coarse cell (fused restriction)
+    double *lvl_r[6], *lvl_e[6];   // deep V-cycle (ISM_COARSE_ACMV): residual / correction of levels 1..L-1
     void *tc_block;            // tensor-core coarse solve: constant operand tiles (TF32), or NULL
     size_t tc_bytes;
     double *partials;          // ISM_NQ * max_blocks

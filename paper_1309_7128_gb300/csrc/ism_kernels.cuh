@@ -263,7 +263,7 @@ __device__ __forceinline__ T prolong_value(const T *__restrict__ q, int x, int y
 // colour is free.  Grid: (ceil(ceil(nx/2)/blockDim), ny).
 template <typename T>
 __global__ void k_rbgs_colour(T *__restrict__ p, const T *__restrict__ b, int nx, int ny,
-                              int bcmask, int colour, const int *skip)
+                              int bcmask, int colour, const int *skip, T scale = (T)1)
 {
     if (skip && *skip) return;
     const int j = blockIdx.y;
@@ -276,7 +276,64 @@ __global__ void k_rbgs_colour(T *__restrict__ p, const T *__restrict__ b, int nx
     if (i < nx - 1) s += p[idx + 1];
     if (j > 0) s += p[idx - nx];
     if (j < ny - 1) s += p[idx + nx];
-    p[idx] = (s - b[idx]) * inv_diag<T>(diag_count(i, j, nx, ny, bcmask));
+    p[idx] = (s - scale * b[idx]) * inv_diag<T>(diag_count(i, j, nx, ny, bcmask));
+}
+
+// ---- deep additive-correction V-cycle (2 x 2 agglomeration levels)
+
+// out = 2 x 2 block sums of in (nx, ny even), sum order of the oracle.
+template <typename T>
+__global__ void k_restrict2(const T *__restrict__ in, T *__restrict__ out, int nx, int ny, const int *skip)
+{
+    if (skip && *skip) return;
+    const int J = blockIdx.y, I = blockIdx.x * blockDim.x + threadIdx.x, ncx = nx >> 1;
+    if (I >= ncx) return;
+    const T *r0 = in + (size_t)(2 * J) * nx + 2 * I, *r1 = r0 + nx;
+    out[(size_t)J * ncx + I] = ((r0[0] + r0[1]) + r1[0]) + r1[1];
+}
+
+// e = P e_c (piecewise constant over 2 x 2 blocks; overwrites e)
+template <typename T>
+__global__ void k_inject2(T *__restrict__ e, const T *__restrict__ ec, int nx, int ny, const int *skip)
+{
+    if (skip && *skip) return;
+    const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nx) return;
+    e[(size_t)j * nx + i] = ec[(size_t)(j >> 1) * (nx >> 1) + (i >> 1)];
+}
+
+// Residual r = b - A_f p, its 2 x 2 block sums and the partial sums
+// (||r||^2, sum p, sum p^2), with the fused control; one thread per block.
+template <typename T>
+__global__ void k_resid2(const T *__restrict__ p, const T *__restrict__ b, T *__restrict__ rc,
+                         double *partials, int nx, int ny, int bcmask, const int *skip, IsmState *ctl_st,
+                         int ctl_mode, unsigned long long cond)
+{
+    if (skip && *skip) return;
+    const int J = blockIdx.y, I = blockIdx.x * blockDim.x + threadIdx.x, ncx = nx >> 1;
+    double r2 = 0.0, ps = 0.0, p2 = 0.0;
+    if (I < ncx) {
+        T acc = 0;
+        for (int k = 0; k < 4; ++k) {                 // (2I, 2J), (2I+1, 2J), (2I, 2J+1), (2I+1, 2J+1)
+            const int i = 2 * I + (k & 1), j = 2 * J + (k >> 1);
+            const size_t idx = (size_t)j * nx + i;
+            const T pc = p[idx];
+            T s = 0;
+            if (i > 0) s += p[idx - 1];
+            if (i < nx - 1) s += p[idx + 1];
+            if (j > 0) s += p[idx - nx];
+            if (j < ny - 1) s += p[idx + nx];
+            const T r = b[idx] - (s - (T)diag_count(i, j, nx, ny, bcmask) * pc);
+            acc += r;
+            r2 += (double)r * (double)r;
+            ps += (double)pc;
+            p2 += (double)pc * (double)pc;
+        }
+        rc[(size_t)J * ncx + I] = acc;
+    }
+    double v[3] = {r2, ps, p2};
+    block_partials<3>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    if (ctl_mode >= 0) ctl_last_block(ctl_st, partials, gridDim.x * gridDim.y, 3, ctl_mode, cond);
 }
 
 // Residual r = b - A_f p, its m x m block sums (restriction) and the partial

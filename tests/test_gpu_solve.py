@@ -75,6 +75,22 @@ def test_gmg_matches_oracle(bc):
     assert s == ism.ISM_OK and r <= 1e-8 and rel(p, p_ex) <= 1e-9
 
 
+@pytest.mark.parametrize("nx,ny,m,bc", [(256, 256, 16, (0, 0, 0, 0)), (256, 128, 8, (0, 1, 0, 0)),
+                                         (512, 256, 32, (1, 1, 1, 1))])
+def test_deep_acm_vcycle_matches_oracle(nx, ny, m, bc):
+    """The deep additive-correction V-cycle (FP64) with the oracle's cycle
+    count and field to 1e-12; mixed contexts reject it."""
+    b = smooth_rhs(nx, ny, 6) + (1e-6 if any(bc) else 0.0)
+    p_ref, c_ref, h_ref = O.OracleACMV(nx, ny, m, bc, nu=8).solve(b, tol=1e-8)
+    s, p, c, r, h, _ = gpu_solve(b, nx, ny, m, bc, ism.ISM_FP64, kind=ism.ISM_COARSE_ACMV, nu=8)
+    assert s == ism.ISM_OK and c == c_ref
+    assert rel(p, p_ref) <= 1e-12
+    ctx = setup(nx, ny, m, bc, prec=ism.ISM_MIXED)
+    o = ism.ism_get_options(ctx)
+    o.kind = ism.ISM_COARSE_ACMV
+    assert ism.ism_set_options(ctx, o) == ism.ISM_ERR_ARG
+
+
 def test_config0_ism_beats_acm_on_gpu():
     b = smooth_rhs(256, 256, 0)
     c_ism = gpu_solve(b, 256, 256, 16, (0, 0, 0, 0), ism.ISM_FP64)[2]

@@ -331,6 +331,39 @@ def test_ism_converges_at_least_as_fast_as_gmg():
     assert res["ism"][1] <= res["gmg"][1], res
 
 
+def test_deep_acm_with_one_level_is_the_two_level_acm():
+    """The V-cycle with m = 2 (one agglomeration level) performs exactly the
+    two-level ACM cycle with m = 2."""
+    b = smooth_rhs(64, 48, 3)
+    pv, cv, hv = O.OracleACMV(64, 48, 2, nu=2).solve(b, tol=1e-8)
+    pa, ca, ha = O.OracleISM(64, 48, 2, kind="acm", nu=2).solve(b, tol=1e-8)
+    assert cv == ca and np.array_equal(pv, pa)
+
+
+def test_deep_acm_converges_between_ism_and_two_level_acm():
+    """Sec. 4.3 compares ISM with the deep ACM V-cycle: ISM needs far fewer
+    cycles; smoothing on the intermediate levels makes the V-cycle beat the
+    two-level ACM with the same coarsest level (256^2, 16h, nu = 8)."""
+    b = smooth_rhs(256, 256, 0)
+    ism = O.OracleISM(256, 256, 16, kind="ism", nu=8).solve(b, tol=1e-8)[1]
+    acmv = O.OracleACMV(256, 256, 16, nu=8).solve(b, tol=1e-8)[1]
+    acm = O.OracleISM(256, 256, 16, kind="acm", nu=8).solve(b, tol=1e-8)[1]
+    assert 2 * ism < acmv < acm, (ism, acmv, acm)
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (0, 1, 0, 0), (1, 1, 1, 1)])
+def test_deep_acm_exact_solution_is_fixed_point(bc):
+    nx, ny = 64, 32
+    s = O.OracleACMV(nx, ny, 8, bc, nu=2)
+    p = random_field(nx, ny, 4)
+    if not any(bc):
+        p -= p.mean()
+    b = O.apply_af(p, bc)
+    q = p.copy()
+    s.cycle(q, b)
+    assert np.abs(q - p).max() <= 1e-12 * np.abs(p).max()
+
+
 def test_mixed_refinement_reaches_tolerance():
     nx = ny = 128
     b = smooth_rhs(nx, ny, 12)
