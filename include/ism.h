@@ -94,8 +94,16 @@ typedef struct {
     int use_graphs;       /* 0: plain launches; 1: CUDA graphs of check_every cycles; 2 (default):
                              the whole solve as one graph with device-side while loops */
     int coarse_tc;        /* mixed: 1 (default) runs the single-precision coarse solve on the tensor
-                             cores (tcgen05, TF32 operands, FP32 accumulation) when ncx, ncy <= 128;
+                             cores (tcgen05, TF32 operands, FP32 accumulation) when ncx, ncy <= 64;
                              0 on the CUDA cores in FP32.  Ignored by the FP64 path. */
+    int cycle;            /* 0 (default): the correction-scheme cycle above.  1: the paper's
+                             accommodative strategy (Sec. 4.3.1), FP64 contexts with the ISM coarse
+                             operator only: Gauss-Seidel on the coarse equations until max |r_c| <=
+                             accom_tol_c, bilinear correction, red-black sweeps on the fine grid until
+                             max |r| <= tol (ism_solve's tol is then an absolute maximum norm and
+                             max_cycles caps the fine sweeps). */
+    double accom_tol_c;   /* cycle 1: coarse criterion (absolute maximum norm, default 1e-5) */
+    int accom_max_coarse; /* cycle 1: cap on coarse Gauss-Seidel iterations (default 100000) */
 } ism_options;
 
 typedef struct ism_ctx ism_ctx;
@@ -166,7 +174,8 @@ int ism_coarsening(const ism_ctx *ctx);
 int ism_last_history(const ism_ctx *ctx, double *hist, int cap);
 
 /* Counters of the last solve (host, any may be NULL): refinement iterations
- * (mixed; 0 for FP64), single-precision or FP64 cycles, kernel launches. */
+ * (mixed; 0 for FP64; coarse Gauss-Seidel iterations with cycle 1),
+ * single-precision or FP64 cycles (fine sweeps with cycle 1), kernel launches. */
 ism_status ism_last_counts(const ism_ctx *ctx, int *outer, int *cycles, long long *launches);
 
 /* ---------------- kernel-level entry points (one step of the cycle) ------

@@ -3,13 +3,13 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` import this package.  It shares no code with the CUDA library.
 """
-from .ism_oracle import (OracleISM, OracleACMV, build, lib, apply_af, residual, rbgs_sweep,
+from .ism_oracle import (OracleISM, OracleACMV, OracleAccommodative, build, lib, apply_af, residual, rbgs_sweep,
                          restrict, prolong_add, prolong_const_add,
                          coarse_operator, predictor, divergence, correct,
                          proj_step, VEL_NOSLIP, VEL_FREESLIP, VEL_INFLOW,
                          VEL_OUTFLOW, pressure_bc)
 
-__all__ = ["OracleISM", "OracleACMV", "build", "lib", "apply_af", "residual", "rbgs_sweep",
+__all__ = ["OracleISM", "OracleACMV", "OracleAccommodative", "build", "lib", "apply_af", "residual", "rbgs_sweep",
            "restrict", "prolong_add", "prolong_const_add", "coarse_operator",
            "predictor", "divergence", "correct", "proj_step", "VEL_NOSLIP",
            "VEL_FREESLIP", "VEL_INFLOW", "VEL_OUTFLOW", "pressure_bc"]

@@ -249,6 +249,54 @@ int or_coarse_operator(int nx, int ny, int m, const int *bc, int kind, double *A
 }
 
 /* ------------------------------------------------------------------------ */
+/* Gauss-Seidel on the coarse equations A_c e = r (the paper's iterative      */
+/* coarse solve, Sec. 4.3.1), four-colour ordering of the nine-point stencil: */
+/* colour (I mod 2) + 2 (J mod 2), colours 0..3 in turn; the matrix is the    */
+/* assembled dense A_c (nc x nc), its nine neighbours taken in the order      */
+/* dJ = -1..1, dI = -1..1.  Runs full iterations until max |r - A_c e| <=     */
+/* tol (checked after each iteration) or `cap` iterations; returns the count. */
+/* ------------------------------------------------------------------------ */
+int or_coarse_gs4(int ncx, int ncy, const double *Ac, const double *r, double *e,
+                  double tol, int cap)
+{
+    const size_t nc = (size_t)ncx * ncy;
+    int it = 0;
+    for (;;) {
+        double mx = 0.0;
+        for (int J = 0; J < ncy; ++J)
+            for (int I = 0; I < ncx; ++I) {
+                const size_t row = (size_t)J * ncx + I;
+                double s = 0.0;
+                for (int dJ = -1; dJ <= 1; ++dJ)
+                    for (int dI = -1; dI <= 1; ++dI) {
+                        const int K = J + dJ, L = I + dI;
+                        if (K < 0 || K >= ncy || L < 0 || L >= ncx) continue;
+                        const size_t col = (size_t)K * ncx + L;
+                        s += Ac[row * nc + col] * e[col];
+                    }
+                const double d = fabs(r[row] - s);
+                if (d > mx) mx = d;
+            }
+        if (mx <= tol || it >= cap) return it;
+        for (int colour = 0; colour < 4; ++colour)
+            for (int J = colour >> 1; J < ncy; J += 2)
+                for (int I = colour & 1; I < ncx; I += 2) {
+                    const size_t row = (size_t)J * ncx + I;
+                    double s = 0.0;
+                    for (int dJ = -1; dJ <= 1; ++dJ)
+                        for (int dI = -1; dI <= 1; ++dI) {
+                            const int K = J + dJ, L = I + dI;
+                            if ((dI == 0 && dJ == 0) || K < 0 || K >= ncy || L < 0 || L >= ncx) continue;
+                            const size_t col = (size_t)K * ncx + L;
+                            s += Ac[row * nc + col] * e[col];
+                        }
+                    e[row] = (r[row] - s) / Ac[row * nc + row];
+                }
+        ++it;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Single-precision emulation of the inner solver of the mixed path.          */
 /* Same steps as above in float arithmetic; sums of the restriction and of    */
 /* norms are accumulated in double.                                           */

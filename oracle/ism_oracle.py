@@ -67,6 +67,7 @@ def lib():
                 "or_prolong_add": [i, i, i, _ip, _dp, _dp],
                 "or_prolong_const_add": [i, i, i, _dp, _dp],
                 "or_coarse_operator": [i, i, i, _ip, i, _dp],
+                "or_coarse_gs4": [i, i, _dp, _dp, _dp, C.c_double, i],
                 "or_residual_f32": [i, i, _ip, _fp, _fp, _fp],
                 "or_rbgs_sweep_f32": [i, i, _ip, _fp, _fp],
                 "or_restrict_f32": [i, i, i, _fp, _dp],
@@ -78,7 +79,7 @@ def lib():
             for name, args in sig.items():
                 f = getattr(L, name)
                 f.argtypes = args
-                f.restype = C.c_int if name == "or_coarse_operator" else None
+                f.restype = C.c_int if name in ("or_coarse_operator", "or_coarse_gs4") else None
             _lib = L
     return _lib
 
@@ -363,6 +364,51 @@ class OracleACMV:
             cycles += 1
             hist.append(np.linalg.norm(residual(p, b, self.bc)) / bn)
         return p, cycles, hist
+
+
+class OracleAccommodative:
+    """The paper's accommodative strategy for one pressure solve (Sec. 4.3.1),
+    in its simplest form: iterate on the coarse grid first, prolongate when
+    the coarse residual is small enough, then iterate on the fine grid until
+    the fine criterion holds.  Readings: the coarse equations are the ISM
+    equations A_c e = R r (sums of fine equations) solved by four-colour
+    Gauss-Seidel from e = 0 until max |R r - A_c e| <= tol_c; the correction
+    is bilinear (Eq. 5); the fine iteration is red-black Gauss-Seidel until
+    max |b - A_f p| <= tol_f; both criteria are absolute maximum norms (the
+    paper's 1e-6 with h = 1); one coarse-then-fine pass per solve."""
+
+    def __init__(self, nx, ny, m, bc=(0, 0, 0, 0)):
+        self.nx, self.ny, self.m = nx, ny, m
+        self.bc = _bc(bc)
+        self.singular = not np.any(self.bc)
+        self.Ac = np.ascontiguousarray(coarse_operator(nx, ny, m, self.bc, "ism"))
+
+    def solve(self, b, p0=None, tol_f=1e-6, tol_c=1e-5, cap_c=100000, cap_f=1000000):
+        """Returns (p, coarse iterations, fine sweeps, final max |r|)."""
+        b = np.array(b, dtype=np.float64, order="C", copy=True)
+        if self.singular:
+            b -= b.mean()
+        p = np.zeros_like(b) if p0 is None else np.array(p0, dtype=np.float64, order="C", copy=True)
+        if self.singular:
+            p -= p.mean()
+        r = residual(p, b, self.bc)
+        if np.abs(r).max() <= tol_f:
+            return p, 0, 0, float(np.abs(r).max())
+        rc = np.ascontiguousarray(restrict(r, self.m))
+        ec = np.zeros_like(rc)
+        nc_it = lib().or_coarse_gs4(rc.shape[1], rc.shape[0], self.Ac, rc, ec, float(tol_c), int(cap_c))
+        prolong_add(p, ec, self.m, self.bc)
+        if self.singular:
+            p -= p.mean()
+        nf = 0
+        mx = float(np.abs(residual(p, b, self.bc)).max())
+        while mx > tol_f and nf < cap_f:
+            rbgs_sweep(p, b, self.bc)
+            nf += 1
+            mx = float(np.abs(residual(p, b, self.bc)).max())
+        if self.singular:
+            p -= p.mean()
+        return p, nc_it, nf, mx
 
 
 # --------------------------------------------------------------------------

@@ -1,0 +1,242 @@
+// ism_accom.cu -- the paper's accommodative strategy for one pressure solve
+// (Sec. 4.3.1), FP64: iterate on the coarse grid first, prolongate when the
+// coarse residual is small enough, then iterate on the fine grid until the
+// fine criterion holds (one coarse-then-fine pass).
+//
+//   r = b - A_f p; r_c = R r (m x m block sums)
+//   e_c = 0; four-colour Gauss-Seidel on the nine-point ISM equations
+//        A_c e_c = r_c until max |r_c - A_c e_c| <= tol_c
+//   p += P e_c (bilinear, Eq. 5), mean removed when every face is Neumann
+//   red-black sweeps on A_f p = b until max |b - A_f p| <= tol
+//
+// The coarse iteration runs in one CTA (the coarse grid is small); its sums
+// are rounded at every step (no contraction) in the neighbour order of the
+// oracle.  A_c comes from its closed form (Sec. 3.3, Eq. 5-7):
+// A_c = 1/4 (S_y x S_x) - 4 I with S = tridiag(1, 2, 1), end diagonal 3 at
+// a Neumann end and 1 at a Dirichlet-0 end.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "ism_kernels.cuh"
+
+// defined in ism_core.cu
+__global__ void k_ctl(IsmState *st, const double *partials, int nblk, int nq, int mode,
+                      unsigned long long cond);
+__global__ void k_rhs_stats(const double *__restrict__ x, double *__restrict__ y, long long n,
+                            const IsmState *st, int mode, int sub_mean, double *partials);
+__global__ void k_finalize(const double *in, const double *in_alt, double *out, long long n,
+                           const IsmState *st, int sub_mean);
+
+namespace {
+
+constexpr int AC_THREADS = 1024;
+
+__device__ __forceinline__ double s_entry(int I, int Ip, int n, int lo_dir, int hi_dir)
+{
+    if (I != Ip) return (I - Ip == 1 || Ip - I == 1) ? 1.0 : 0.0;
+    if (n == 1) return (lo_dir ? 1.0 : 3.0) + (hi_dir ? 1.0 : 3.0) - 2.0;
+    if (I == 0) return lo_dir ? 1.0 : 3.0;
+    if (I == n - 1) return hi_dir ? 1.0 : 3.0;
+    return 2.0;
+}
+
+// coefficient of e[J + dJ][I + dI] in row (I, J) of A_c
+__device__ __forceinline__ double ac_coef(int I, int J, int dI, int dJ, int ncx, int ncy, int bcmask)
+{
+    const double sx = s_entry(I, I + dI, ncx, bcmask & 1, bcmask & 2);
+    const double sy = s_entry(J, J + dJ, ncy, bcmask & 4, bcmask & 8);
+    double a = __dmul_rn(0.25, __dmul_rn(sx, sy));
+    if (dI == 0 && dJ == 0) a = __dadd_rn(a, -4.0);
+    return a;
+}
+
+// row sum over the nine neighbours (dJ = -1..1, dI = -1..1), optionally
+// without the centre
+__device__ __forceinline__ double row_sum(const double *e, int I, int J, int ncx, int ncy, int bcmask,
+                                          bool centre)
+{
+    double s = 0.0;
+    for (int dJ = -1; dJ <= 1; ++dJ)
+        for (int dI = -1; dI <= 1; ++dI) {
+            const int K = J + dJ, L = I + dI;
+            if ((!centre && dI == 0 && dJ == 0) || K < 0 || K >= ncy || L < 0 || L >= ncx) continue;
+            s = __dadd_rn(s, __dmul_rn(ac_coef(I, J, dI, dJ, ncx, ncy, bcmask), e[(size_t)K * ncx + L]));
+        }
+    return s;
+}
+
+// One CTA: e = 0, then Gauss-Seidel iterations until the criterion or the
+// cap; the iteration count goes to st->outer.
+__global__ void __launch_bounds__(AC_THREADS, 1)
+k_coarse_gs4(const double *__restrict__ r, double *__restrict__ e, int ncx, int ncy, int bcmask, double tol,
+             int cap, IsmState *st)
+{
+    if (st->done) return;
+    __shared__ double red[32];
+    __shared__ int stop;
+    const int t = threadIdx.x, nc = ncx * ncy;
+    for (int k = t; k < nc; k += AC_THREADS) e[k] = 0.0;
+    __syncthreads();
+    int it = 0;
+    for (;;) {
+        double mx = 0.0;
+        for (int k = t; k < nc; k += AC_THREADS) {
+            const int I = k % ncx, J = k / ncx;
+            const double d = fabs(__dadd_rn(r[k], -row_sum(e, I, J, ncx, ncy, bcmask, true)));
+            mx = fmax(mx, d);
+        }
+        for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULLMASK, mx, o));
+        if ((t & 31) == 0) red[t >> 5] = mx;
+        __syncthreads();
+        if (t == 0) {
+            double m2 = 0.0;
+            for (int w = 0; w < AC_THREADS / 32; ++w) m2 = fmax(m2, red[w]);
+            stop = (m2 <= tol || it >= cap);
+        }
+        __syncthreads();
+        if (stop) break;
+        for (int colour = 0; colour < 4; ++colour) {
+            const int I0 = colour & 1, J0 = colour >> 1;
+            const int hx = (ncx - I0 + 1) / 2, hy = (ncy - J0 + 1) / 2;
+            for (int k = t; k < hx * hy; k += AC_THREADS) {
+                const int I = I0 + 2 * (k % hx), J = J0 + 2 * (k / hx);
+                const double s = row_sum(e, I, J, ncx, ncy, bcmask, false);
+                e[(size_t)J * ncx + I] =
+                    __ddiv_rn(__dadd_rn(r[(size_t)J * ncx + I], -s), ac_coef(I, J, 0, 0, ncx, ncy, bcmask));
+            }
+            __syncthreads();
+        }
+        ++it;
+    }
+    if (t == 0) st->outer = it;
+}
+
+// max |b - A_f p| per block, then (last block) the fine criterion: counts a
+// sweep unless `initial`, sets done / status.
+__global__ void k_resmax(const double *__restrict__ p, const double *__restrict__ b, double *partials, int nx,
+                         int ny, int bcmask, IsmState *st, double tol, int cap, int initial)
+{
+    if (st->done) return;
+    __shared__ double red[32];
+    __shared__ int am_last;
+    double mx = 0.0;
+    const long long n = (long long)nx * ny;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k % nx), j = (int)(k / nx);
+        double s = 0.0;
+        if (i > 0) s += p[k - 1];
+        if (i < nx - 1) s += p[k + 1];
+        if (j > 0) s += p[k - nx];
+        if (j < ny - 1) s += p[k + nx];
+        const double r = b[k] - (s - (double)diag_count(i, j, nx, ny, bcmask) * p[k]);
+        mx = fmax(mx, fabs(r));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULLMASK, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m2 = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m2 = fmax(m2, red[w]);
+        partials[blockIdx.x] = m2;
+        __threadfence();
+        am_last = (atomicAdd(&st->ticket, 1u) == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last || threadIdx.x != 0) return;
+    __threadfence();
+    double m2 = 0.0;
+    for (int k = 0; k < (int)gridDim.x; ++k) m2 = fmax(m2, __ldcg(partials + k));
+    st->ticket = 0;
+    if (!initial) st->cycles++;
+    st->relres = m2;
+    if (!isfinite(m2)) { st->status = ISM_ERR_NONFINITE; st->done = 1; }
+    else if (m2 <= tol) { st->status = ISM_OK; st->done = 1; }
+    else if (!initial && st->cycles >= cap) { st->status = ISM_ERR_NOT_CONVERGED; st->done = 1; }
+}
+
+}  // namespace
+
+#define TRY(x)                                                                   \
+    do {                                                                         \
+        ism_status _s = (x);                                                     \
+        if (_s != ISM_OK) return _s;                                             \
+    } while (0)
+
+// p -= mean(p) (all faces Neumann): sums, mean into st->mean, subtraction
+static ism_status remove_mean(ism_ctx *ctx, double *p)
+{
+    const int G = 4 * 152;
+    k_rhs_stats<<<G, 256, 0, ctx->ws>>>(p, nullptr, ctx->n, ctx->st, 0, 0, ctx->partials);
+    ISM_LAUNCH_CHECK(ctx);
+    k_ctl<<<1, 256, 0, ctx->ws>>>(ctx->st, ctx->partials, G, 1, 0 /* mean */, 0);
+    ISM_LAUNCH_CHECK(ctx);
+    k_finalize<<<G, 256, 0, ctx->ws>>>(p, nullptr, p, ctx->n, ctx->st, 1);
+    ISM_LAUNCH_CHECK(ctx);
+    return ISM_OK;
+}
+
+// Solve with cycle = 1 on the internal buffers (b64 prepared, p64[0] the
+// initial guess); ism_solve_internal's contract.
+ism_status ism_solve_accommodative(ism_ctx *ctx, double tol, int max_sweeps)
+{
+    const int G = 2 * 152, T = 256;
+    IsmState h;
+    ISM_CUDA_TRY(cudaMemcpyAsync(&h, ctx->st, offsetof(IsmState, hist), cudaMemcpyDeviceToHost, ctx->ws));
+    ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+    if (!h.done) {
+        // initial guess: mean removed (all Neumann), its criterion
+        if (ctx->singular) TRY(remove_mean(ctx, ctx->p64[0]));
+        k_resmax<<<G, T, 0, ctx->ws>>>(ctx->p64[0], ctx->b64, ctx->partials, ctx->nx, ctx->ny, ctx->bcmask, ctx->st,
+                                       tol, max_sweeps, 1);
+        ISM_LAUNCH_CHECK(ctx);
+        // restriction, coarse iteration, bilinear correction
+        const int th = std::min(256, ctx->m * ctx->m);
+        k_resid<double><<<dim3(ctx->ncx, ctx->ncy), th, 0, ctx->ws>>>(ctx->p64[0], ctx->b64, ctx->rc64, ctx->partials,
+                                                                     ctx->nx, ctx->ny, ctx->m, ctx->bcmask,
+                                                                     &ctx->st->done);
+        ISM_LAUNCH_CHECK(ctx);
+        k_coarse_gs4<<<1, AC_THREADS, 0, ctx->ws>>>(ctx->rc64, ctx->ec64, ctx->ncx, ctx->ncy, ctx->bcmask,
+                                                    ctx->opt.accom_tol_c, ctx->opt.accom_max_coarse, ctx->st);
+        ISM_LAUNCH_CHECK(ctx);
+        k_prolong<double><<<dim3((ctx->nx + 127) / 128, ctx->ny), 128, 0, ctx->ws>>>(
+            ctx->p64[0], ctx->ec64, ctx->nx, ctx->ny, ctx->m, ctx->ncx, ctx->ncy, ctx->bcmask, ISM_COARSE_ISM,
+            ctx->st, 0, &ctx->st->done);
+        ISM_LAUNCH_CHECK(ctx);
+        if (ctx->singular) TRY(remove_mean(ctx, ctx->p64[0]));
+        // fine sweeps in chunks, the criterion after every sweep
+        const int hx = (ctx->nx + 1) / 2;
+        const dim3 gs((hx + 127) / 128, ctx->ny);
+        const int C = ctx->opt.check_every;
+        for (;;) {
+            for (int c = 0; c < C; ++c) {
+                for (int col = 0; col < 2; ++col) {
+                    k_rbgs_colour<double><<<gs, 128, 0, ctx->ws>>>(ctx->p64[0], ctx->b64, ctx->nx, ctx->ny,
+                                                                   ctx->bcmask, col, &ctx->st->done);
+                    ISM_LAUNCH_CHECK(ctx);
+                }
+                k_resmax<<<G, T, 0, ctx->ws>>>(ctx->p64[0], ctx->b64, ctx->partials, ctx->nx, ctx->ny, ctx->bcmask,
+                                               ctx->st, tol, max_sweeps, 0);
+                ISM_LAUNCH_CHECK(ctx);
+            }
+            ISM_CUDA_TRY(cudaMemcpyAsync(&h, ctx->st, offsetof(IsmState, hist), cudaMemcpyDeviceToHost, ctx->ws));
+            ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+            if (h.done) break;
+        }
+    }
+    // mean removal of the result (all Neumann); zeros for a zero right-hand side
+    if (ctx->singular) TRY(remove_mean(ctx, ctx->p64[0]));
+    else {
+        k_finalize<<<4 * 152, 256, 0, ctx->ws>>>(ctx->p64[0], nullptr, ctx->p64[0], ctx->n, ctx->st, 0);
+        ISM_LAUNCH_CHECK(ctx);
+    }
+    ISM_CUDA_TRY(cudaMemcpyAsync(&h, ctx->st, offsetof(IsmState, hist), cudaMemcpyDeviceToHost, ctx->ws));
+    ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+    ctx->last_cycles = h.cycles;
+    ctx->last_outer = h.outer;
+    ctx->last_relres = h.relres;
+    ctx->last_status = h.status;
+    ctx->last_nhist = 0;
+    return (ism_status)h.status;
+}

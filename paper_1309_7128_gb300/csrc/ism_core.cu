@@ -139,6 +139,9 @@ static void default_options(ism_options *o, int prec)
     o->check_every = 16;
     o->use_graphs = 2;
     o->coarse_tc = prec == ISM_MIXED ? 1 : 0;
+    o->cycle = 0;
+    o->accom_tol_c = 1e-5;
+    o->accom_max_coarse = 100000;
 }
 
 static const double kPi = 3.14159265358979323846;
@@ -406,6 +409,9 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     if (o->max_outer < 1 || o->inner_max < 1 || o->check_every < 1 || o->check_every > 4096) return ISM_ERR_ARG;
     if (o->use_graphs < 0 || o->use_graphs > 2) return ISM_ERR_ARG;
     if (o->coarse_tc < 0 || o->coarse_tc > 1) return ISM_ERR_ARG;
+    if (o->cycle < 0 || o->cycle > 1) return ISM_ERR_ARG;
+    if (o->cycle == 1 && (ctx->prec != ISM_FP64 || o->kind != ISM_COARSE_ISM)) return ISM_ERR_ARG;
+    if (!(o->accom_tol_c > 0.0) || o->accom_max_coarse < 1) return ISM_ERR_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
     const int kind_changed = o->kind != ctx->opt.kind;
     cudaStreamSynchronize(ctx->ws);
@@ -976,6 +982,7 @@ ism_status ism_solve_internal(ism_ctx *ctx, double tol, int max_cycles)
         ctx->last_nhist = 0;
         return (ism_status)stt;
     }
+    if (ctx->opt.cycle == 1) return ism_solve_accommodative(ctx, tol, max_cycles);
     ism_status s = ctx->prec == ISM_FP64 ? solve_fp64(ctx) : solve_mixed(ctx);
     if (s != ISM_OK) return s;
     const IsmState *hs = ctx->st_host;

@@ -135,6 +135,8 @@ ism_status ism_leave(ism_ctx *ctx);
 // Solve on internal buffers: b64 holds the right-hand side (mean removed),
 // p64[0] the initial guess; on return p64[0] holds the solution.
 ism_status ism_solve_internal(ism_ctx *ctx, double tol, int max_cycles);
+// The accommodative strategy (cycle = 1, ism_accom.cu) on the same buffers.
+ism_status ism_solve_accommodative(ism_ctx *ctx, double tol, int max_sweeps);
 // Copy user rhs into b64 (removing the mean when singular) and compute ||b||.
 ism_status ism_prepare_rhs(ism_ctx *ctx, const double *rhs);
 

@@ -91,6 +91,32 @@ def test_deep_acm_vcycle_matches_oracle(nx, ny, m, bc):
     assert ism.ism_set_options(ctx, o) == ism.ISM_ERR_ARG
 
 
+@pytest.mark.parametrize("nx,ny,m,bc", [(256, 192, 16, (0, 0, 0, 0)), (128, 128, 8, (0, 1, 0, 0)),
+                                         (160, 96, 32, (1, 1, 1, 1))])
+def test_accommodative_strategy_matches_oracle(nx, ny, m, bc):
+    """The paper's accommodative strategy (cycle = 1, FP64): the same number
+    of coarse Gauss-Seidel iterations as the oracle (the coarse arithmetic is
+    rounded step by step in the oracle's order), the same number of fine
+    sweeps up to one, the criterion met, the field to 1e-10."""
+    b = smooth_rhs(nx, ny, 12) + (1e-6 if any(bc) else 0.0)
+    tol_f, tol_c = 1e-7, 1e-6
+    p_ref, nc_ref, nf_ref, mx_ref = O.OracleAccommodative(nx, ny, m, bc).solve(b, tol_f=tol_f, tol_c=tol_c)
+    ctx = setup(nx, ny, m, bc, prec=ism.ISM_FP64, cycle=1, accom_tol_c=tol_c)
+    p = dev64(np.zeros((ny, nx)))
+    s, nf, mx = ism.ism_solve(ctx, dev64(b), p, tol_f, 1000000)
+    outer, cycles, _ = ism.ism_last_counts(ctx)
+    print(f"{nx}x{ny}/{m}: coarse {outer} vs {nc_ref}, fine {cycles} vs {nf_ref}")
+    assert s == ism.ISM_OK and mx <= tol_f
+    assert outer == nc_ref and abs(cycles - nf_ref) <= 1
+    assert rel(host(p), p_ref) <= 1e-10
+    # options: FP64 with the ISM coarse operator only
+    for prec, kind in ((ism.ISM_MIXED, 0), (ism.ISM_FP64, ism.ISM_COARSE_ACM)):
+        c2 = setup(nx, ny, m, bc, prec=prec)
+        o = ism.ism_get_options(c2)
+        o.cycle, o.kind = 1, kind
+        assert ism.ism_set_options(c2, o) == ism.ISM_ERR_ARG
+
+
 def test_config0_ism_beats_acm_on_gpu():
     b = smooth_rhs(256, 256, 0)
     c_ism = gpu_solve(b, 256, 256, 16, (0, 0, 0, 0), ism.ISM_FP64)[2]

@@ -364,6 +364,44 @@ def test_deep_acm_exact_solution_is_fixed_point(bc):
     assert np.abs(q - p).max() <= 1e-12 * np.abs(p).max()
 
 
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (0, 1, 0, 0), (1, 1, 1, 1)])
+def test_coarse_gauss_seidel_converges_to_the_exact_coarse_solution(bc):
+    """The iterative coarse solve of the accommodative strategy (four-colour
+    Gauss-Seidel on the assembled nine-point A_c) reaches the exact coarse
+    solution (LU of A_c) as its tolerance goes to zero."""
+    nx, ny, m = 96, 64, 8
+    s = O.OracleISM(nx, ny, m, bc)
+    rc = random_field(nx // m, ny // m, 5)
+    if not any(bc):
+        rc -= rc.mean()
+    ec = np.zeros_like(rc)
+    Ac = np.ascontiguousarray(s.Ac)
+    it = O.lib().or_coarse_gs4(nx // m, ny // m, Ac, np.ascontiguousarray(rc), ec, 1e-13, 100000)
+    assert 0 < it < 100000
+    ex = s.coarse_solve(rc)
+    if not any(bc):
+        ec -= ec.mean()
+        ex -= ex.mean()
+    assert np.abs(ec - ex).max() <= 1e-11 * np.abs(ex).max()
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (0, 1, 0, 0)])
+def test_accommodative_solve_meets_the_maximum_norm_criterion(bc):
+    nx, ny, m = 128, 96, 16
+    b = smooth_rhs(nx, ny, 8) + (1e-6 if any(bc) else 0.0)
+    s = O.OracleAccommodative(nx, ny, m, bc)
+    p, nc, nf, mx = s.solve(b, tol_f=1e-7, tol_c=1e-6)
+    bb = b - b.mean() if not any(bc) else b
+    assert mx <= 1e-7 and np.abs(O.residual(p, bb, bc)).max() <= 1e-7
+    assert nc > 0 and nf > 0
+    # looser coarse criterion: fewer coarse iterations
+    _, nc2, _, _ = s.solve(b, tol_f=1e-7, tol_c=1e-3)
+    assert nc2 < nc
+    # an exact initial guess needs no iteration
+    q, nc3, nf3, _ = s.solve(b, p0=p, tol_f=2 * mx, tol_c=1e-6)
+    assert nc3 == 0 and nf3 == 0
+
+
 def test_mixed_refinement_reaches_tolerance():
     nx = ny = 128
     b = smooth_rhs(nx, ny, 12)
