@@ -18,12 +18,16 @@
  *   cell-centred field p[j*nx + i], cell (i, j), i along x, j along y;
  *   face order bc[0..3] = west, east, south, north;
  *   bc = 0: homogeneous Neumann wall (no flux through the face);
- *   bc = 1: Dirichlet p = 0 on the face (ghost value -p_c).
+ *   bc = 1: Dirichlet p = 0 on the face (ghost value -p_c);
+ *   bc = 2: periodic, given on both faces of an axis (west and east, or
+ *           south and north): the neighbour across the face is the cell at
+ *           the other end of the row / column.
  *   The fine operator is the finite-volume flux sum of the five-point
  *   Laplacian (Sec. 3.3: the Gauss theorem turns the cell integral into face
  *   fluxes), in units where a face flux is (p_neighbour - p_cell):
  *       (A_f p)_c = sum over faces of flux,
- *   a Neumann face contributing 0 and a Dirichlet-0 face (-p_c - p_c).
+ *   a Neumann face contributing 0, a Dirichlet-0 face (-p_c - p_c) and a
+ *   periodic face the flux to the wrapped neighbour.
  *   The equation solved is A_f p = b.
  */
 #include <math.h>
@@ -36,6 +40,9 @@
 #define F_S 2
 #define F_N 3
 
+#define BC_DIR 1
+#define BC_PER 2
+
 #define AT(a, i, j) (a)[(size_t)(j) * (size_t)nx + (size_t)(i)]
 
 /* ------------------------------------------------------------------------ */
@@ -47,10 +54,18 @@ static double cell_flux_sum(int nx, int ny, const int *bc, const double *p,
 {
     double pc = AT(p, i, j);
     double s = 0.0;
-    if (i > 0) s += AT(p, i - 1, j) - pc; else if (bc[F_W]) s += -pc - pc;
-    if (i < nx - 1) s += AT(p, i + 1, j) - pc; else if (bc[F_E]) s += -pc - pc;
-    if (j > 0) s += AT(p, i, j - 1) - pc; else if (bc[F_S]) s += -pc - pc;
-    if (j < ny - 1) s += AT(p, i, j + 1) - pc; else if (bc[F_N]) s += -pc - pc;
+    if (i > 0) s += AT(p, i - 1, j) - pc;
+    else if (bc[F_W] == BC_PER) s += AT(p, nx - 1, j) - pc;
+    else if (bc[F_W] == BC_DIR) s += -pc - pc;
+    if (i < nx - 1) s += AT(p, i + 1, j) - pc;
+    else if (bc[F_E] == BC_PER) s += AT(p, 0, j) - pc;
+    else if (bc[F_E] == BC_DIR) s += -pc - pc;
+    if (j > 0) s += AT(p, i, j - 1) - pc;
+    else if (bc[F_S] == BC_PER) s += AT(p, i, ny - 1) - pc;
+    else if (bc[F_S] == BC_DIR) s += -pc - pc;
+    if (j < ny - 1) s += AT(p, i, j + 1) - pc;
+    else if (bc[F_N] == BC_PER) s += AT(p, i, 0) - pc;
+    else if (bc[F_N] == BC_DIR) s += -pc - pc;
     return s;
 }
 
@@ -74,9 +89,11 @@ void or_residual(int nx, int ny, const int *bc, const double *p,
 /* ------------------------------------------------------------------------ */
 /* Red-black Gauss-Seidel sweep, Sec. 3.1: the point update solves the cell's */
 /* own equation for p_c with the neighbours held fixed:                       */
-/*   p_c = (sum of interior neighbours - b_c) / d_c,                          */
-/*   d_c = (#interior neighbours) + 2 (#Dirichlet-0 faces).                   */
-/* Red cells ((i + j) even) are updated first, then black.                    */
+/*   p_c = (sum of neighbours - b_c) / d_c,                                   */
+/*   d_c = (#neighbours) + 2 (#Dirichlet-0 faces),                            */
+/* a periodic face's wrapped cell counting as a neighbour.  Red cells         */
+/* ((i + j) even) are updated first, then black; a periodic axis has an even  */
+/* number of cells, so wrapped neighbours have the other colour.              */
 /* ------------------------------------------------------------------------ */
 
 static void gs_colour(int nx, int ny, const int *bc, double *p, const double *b,
@@ -87,10 +104,18 @@ static void gs_colour(int nx, int ny, const int *bc, double *p, const double *b,
             if (((i + j) & 1) != colour) continue;
             double s = 0.0;
             int d = 0;
-            if (i > 0) { s += AT(p, i - 1, j); d += 1; } else if (bc[F_W]) d += 2;
-            if (i < nx - 1) { s += AT(p, i + 1, j); d += 1; } else if (bc[F_E]) d += 2;
-            if (j > 0) { s += AT(p, i, j - 1); d += 1; } else if (bc[F_S]) d += 2;
-            if (j < ny - 1) { s += AT(p, i, j + 1); d += 1; } else if (bc[F_N]) d += 2;
+            if (i > 0) { s += AT(p, i - 1, j); d += 1; }
+            else if (bc[F_W] == BC_PER) { s += AT(p, nx - 1, j); d += 1; }
+            else if (bc[F_W] == BC_DIR) d += 2;
+            if (i < nx - 1) { s += AT(p, i + 1, j); d += 1; }
+            else if (bc[F_E] == BC_PER) { s += AT(p, 0, j); d += 1; }
+            else if (bc[F_E] == BC_DIR) d += 2;
+            if (j > 0) { s += AT(p, i, j - 1); d += 1; }
+            else if (bc[F_S] == BC_PER) { s += AT(p, i, ny - 1); d += 1; }
+            else if (bc[F_S] == BC_DIR) d += 2;
+            if (j < ny - 1) { s += AT(p, i, j + 1); d += 1; }
+            else if (bc[F_N] == BC_PER) { s += AT(p, i, 0); d += 1; }
+            else if (bc[F_N] == BC_DIR) d += 2;
             AT(p, i, j) = (s - AT(b, i, j)) / (double)d;
         }
     }
@@ -127,17 +152,18 @@ void or_restrict(int nx, int ny, int m, const double *r, double *rc)
 /* from Q11.  Outside the hull of coarse centres the rule near the boundary is */
 /* a mirror ghost centre at distance m beyond the edge centre (the paper      */
 /* leaves this rule open): even (Q_ghost = Q_edge) at a Neumann face, odd      */
-/* (Q_ghost = -Q_edge) at a Dirichlet-0 face.                                 */
+/* (Q_ghost = -Q_edge) at a Dirichlet-0 face; across a periodic face the      */
+/* ghost is the coarse centre at the other end (the periodic extension).      */
 /* ------------------------------------------------------------------------ */
 
 static double coarse_or_ghost(int ncx, int ncy, const int *bc, const double *q,
                               int I, int J)
 {
     double sgn = 1.0;
-    if (I < 0) { I = 0; if (bc[F_W]) sgn = -sgn; }
-    if (I >= ncx) { I = ncx - 1; if (bc[F_E]) sgn = -sgn; }
-    if (J < 0) { J = 0; if (bc[F_S]) sgn = -sgn; }
-    if (J >= ncy) { J = ncy - 1; if (bc[F_N]) sgn = -sgn; }
+    if (I < 0) { if (bc[F_W] == BC_PER) I += ncx; else { I = 0; if (bc[F_W] == BC_DIR) sgn = -sgn; } }
+    if (I >= ncx) { if (bc[F_E] == BC_PER) I -= ncx; else { I = ncx - 1; if (bc[F_E] == BC_DIR) sgn = -sgn; } }
+    if (J < 0) { if (bc[F_S] == BC_PER) J += ncy; else { J = 0; if (bc[F_S] == BC_DIR) sgn = -sgn; } }
+    if (J >= ncy) { if (bc[F_N] == BC_PER) J -= ncy; else { J = ncy - 1; if (bc[F_N] == BC_DIR) sgn = -sgn; } }
     return sgn * q[(size_t)J * ncx + I];
 }
 
@@ -197,19 +223,23 @@ static double face_sums(int nx, int ny, int m, const int *bc, const double *p,
     double s = 0.0;
     for (int j = y0; j < y1; ++j) {                     /* west face */
         if (x0 > 0) s += AT(p, x0 - 1, j) - AT(p, x0, j);
-        else if (bc[F_W]) s += -AT(p, x0, j) - AT(p, x0, j);
+        else if (bc[F_W] == BC_PER) s += AT(p, nx - 1, j) - AT(p, x0, j);
+        else if (bc[F_W] == BC_DIR) s += -AT(p, x0, j) - AT(p, x0, j);
     }
     for (int j = y0; j < y1; ++j) {                     /* east face */
         if (x1 < nx) s += AT(p, x1, j) - AT(p, x1 - 1, j);
-        else if (bc[F_E]) s += -AT(p, x1 - 1, j) - AT(p, x1 - 1, j);
+        else if (bc[F_E] == BC_PER) s += AT(p, 0, j) - AT(p, x1 - 1, j);
+        else if (bc[F_E] == BC_DIR) s += -AT(p, x1 - 1, j) - AT(p, x1 - 1, j);
     }
     for (int i = x0; i < x1; ++i) {                     /* south face */
         if (y0 > 0) s += AT(p, i, y0 - 1) - AT(p, i, y0);
-        else if (bc[F_S]) s += -AT(p, i, y0) - AT(p, i, y0);
+        else if (bc[F_S] == BC_PER) s += AT(p, i, ny - 1) - AT(p, i, y0);
+        else if (bc[F_S] == BC_DIR) s += -AT(p, i, y0) - AT(p, i, y0);
     }
     for (int i = x0; i < x1; ++i) {                     /* north face */
         if (y1 < ny) s += AT(p, i, y1) - AT(p, i, y1 - 1);
-        else if (bc[F_N]) s += -AT(p, i, y1 - 1) - AT(p, i, y1 - 1);
+        else if (bc[F_N] == BC_PER) s += AT(p, i, 0) - AT(p, i, y1 - 1);
+        else if (bc[F_N] == BC_DIR) s += -AT(p, i, y1 - 1) - AT(p, i, y1 - 1);
     }
     return s;
 }
@@ -226,9 +256,13 @@ int or_coarse_operator(int nx, int ny, int m, const int *bc, int kind, double *A
             int col = JJ * ncx + JI;
             q[col] = 1.0;
             /* the interpolant of e_J vanishes outside coarse cells JI-1..JI+1,
-               JJ-1..JJ+1 (the hat spans from centre to neighbouring centre) */
+               JJ-1..JJ+1 (the hat spans from centre to neighbouring centre);
+               along a periodic axis the hat wraps, so the whole axis is
+               swept there */
             int bi0 = JI - 1 < 0 ? 0 : JI - 1, bi1 = JI + 1 >= ncx ? ncx - 1 : JI + 1;
             int bj0 = JJ - 1 < 0 ? 0 : JJ - 1, bj1 = JJ + 1 >= ncy ? ncy - 1 : JJ + 1;
+            if (bc[F_W] == BC_PER) { bi0 = 0; bi1 = ncx - 1; }
+            if (bc[F_S] == BC_PER) { bj0 = 0; bj1 = ncy - 1; }
             for (int j = bj0 * m; j < (bj1 + 1) * m; ++j)
                 for (int i = bi0 * m; i < (bi1 + 1) * m; ++i)
                     AT(p, i, j) = (kind == 0) ? bilinear_at(nx, ny, m, bc, q, i, j)
@@ -255,9 +289,18 @@ int or_coarse_operator(int nx, int ny, int m, const int *bc, int kind, double *A
 /* assembled dense A_c (nc x nc), its nine neighbours taken in the order      */
 /* dJ = -1..1, dI = -1..1.  Runs full iterations until max |r - A_c e| <=     */
 /* tol (checked after each iteration) or `cap` iterations; returns the count. */
+/* per: bit 0 x periodic, bit 1 y periodic: the neighbours wrap around that   */
+/* axis (which then has an even number >= 4 of coarse cells, so the nine are  */
+/* distinct and the four colours stay independent).                            */
 /* ------------------------------------------------------------------------ */
+static int gs4_wrap(int K, int n, int periodic)
+{
+    if (!periodic) return K;
+    return K < 0 ? K + n : (K >= n ? K - n : K);
+}
+
 int or_coarse_gs4(int ncx, int ncy, const double *Ac, const double *r, double *e,
-                  double tol, int cap)
+                  double tol, int cap, int per)
 {
     const size_t nc = (size_t)ncx * ncy;
     int it = 0;
@@ -269,7 +312,7 @@ int or_coarse_gs4(int ncx, int ncy, const double *Ac, const double *r, double *e
                 double s = 0.0;
                 for (int dJ = -1; dJ <= 1; ++dJ)
                     for (int dI = -1; dI <= 1; ++dI) {
-                        const int K = J + dJ, L = I + dI;
+                        const int K = gs4_wrap(J + dJ, ncy, per & 2), L = gs4_wrap(I + dI, ncx, per & 1);
                         if (K < 0 || K >= ncy || L < 0 || L >= ncx) continue;
                         const size_t col = (size_t)K * ncx + L;
                         s += Ac[row * nc + col] * e[col];
@@ -285,7 +328,7 @@ int or_coarse_gs4(int ncx, int ncy, const double *Ac, const double *r, double *e
                     double s = 0.0;
                     for (int dJ = -1; dJ <= 1; ++dJ)
                         for (int dI = -1; dI <= 1; ++dI) {
-                            const int K = J + dJ, L = I + dI;
+                            const int K = gs4_wrap(J + dJ, ncy, per & 2), L = gs4_wrap(I + dI, ncx, per & 1);
                             if ((dI == 0 && dJ == 0) || K < 0 || K >= ncy || L < 0 || L >= ncx) continue;
                             const size_t col = (size_t)K * ncx + L;
                             s += Ac[row * nc + col] * e[col];
@@ -307,10 +350,18 @@ static float cell_flux_sum_f(int nx, int ny, const int *bc, const float *p,
 {
     float pc = AT(p, i, j);
     float s = 0.0f;
-    if (i > 0) s += AT(p, i - 1, j) - pc; else if (bc[F_W]) s += -pc - pc;
-    if (i < nx - 1) s += AT(p, i + 1, j) - pc; else if (bc[F_E]) s += -pc - pc;
-    if (j > 0) s += AT(p, i, j - 1) - pc; else if (bc[F_S]) s += -pc - pc;
-    if (j < ny - 1) s += AT(p, i, j + 1) - pc; else if (bc[F_N]) s += -pc - pc;
+    if (i > 0) s += AT(p, i - 1, j) - pc;
+    else if (bc[F_W] == BC_PER) s += AT(p, nx - 1, j) - pc;
+    else if (bc[F_W] == BC_DIR) s += -pc - pc;
+    if (i < nx - 1) s += AT(p, i + 1, j) - pc;
+    else if (bc[F_E] == BC_PER) s += AT(p, 0, j) - pc;
+    else if (bc[F_E] == BC_DIR) s += -pc - pc;
+    if (j > 0) s += AT(p, i, j - 1) - pc;
+    else if (bc[F_S] == BC_PER) s += AT(p, i, ny - 1) - pc;
+    else if (bc[F_S] == BC_DIR) s += -pc - pc;
+    if (j < ny - 1) s += AT(p, i, j + 1) - pc;
+    else if (bc[F_N] == BC_PER) s += AT(p, i, 0) - pc;
+    else if (bc[F_N] == BC_DIR) s += -pc - pc;
     return s;
 }
 
@@ -330,10 +381,18 @@ static void gs_colour_f(int nx, int ny, const int *bc, float *p, const float *b,
             if (((i + j) & 1) != colour) continue;
             float s = 0.0f;
             int d = 0;
-            if (i > 0) { s += AT(p, i - 1, j); d += 1; } else if (bc[F_W]) d += 2;
-            if (i < nx - 1) { s += AT(p, i + 1, j); d += 1; } else if (bc[F_E]) d += 2;
-            if (j > 0) { s += AT(p, i, j - 1); d += 1; } else if (bc[F_S]) d += 2;
-            if (j < ny - 1) { s += AT(p, i, j + 1); d += 1; } else if (bc[F_N]) d += 2;
+            if (i > 0) { s += AT(p, i - 1, j); d += 1; }
+            else if (bc[F_W] == BC_PER) { s += AT(p, nx - 1, j); d += 1; }
+            else if (bc[F_W] == BC_DIR) d += 2;
+            if (i < nx - 1) { s += AT(p, i + 1, j); d += 1; }
+            else if (bc[F_E] == BC_PER) { s += AT(p, 0, j); d += 1; }
+            else if (bc[F_E] == BC_DIR) d += 2;
+            if (j > 0) { s += AT(p, i, j - 1); d += 1; }
+            else if (bc[F_S] == BC_PER) { s += AT(p, i, ny - 1); d += 1; }
+            else if (bc[F_S] == BC_DIR) d += 2;
+            if (j < ny - 1) { s += AT(p, i, j + 1); d += 1; }
+            else if (bc[F_N] == BC_PER) { s += AT(p, i, 0); d += 1; }
+            else if (bc[F_N] == BC_DIR) d += 2;
             AT(p, i, j) = (s - AT(b, i, j)) / (float)d;
         }
     }

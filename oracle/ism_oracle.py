@@ -67,7 +67,7 @@ def lib():
                 "or_prolong_add": [i, i, i, _ip, _dp, _dp],
                 "or_prolong_const_add": [i, i, i, _dp, _dp],
                 "or_coarse_operator": [i, i, i, _ip, i, _dp],
-                "or_coarse_gs4": [i, i, _dp, _dp, _dp, C.c_double, i],
+                "or_coarse_gs4": [i, i, _dp, _dp, _dp, C.c_double, i, i],
                 "or_residual_f32": [i, i, _ip, _fp, _fp, _fp],
                 "or_rbgs_sweep_f32": [i, i, _ip, _fp, _fp],
                 "or_restrict_f32": [i, i, i, _fp, _dp],
@@ -84,9 +84,33 @@ def lib():
     return _lib
 
 
+BC_NEUMANN, BC_DIRICHLET0, BC_PERIODIC = 0, 1, 2
+
+
+def _faces(k):
+    return np.ascontiguousarray(np.asarray(k, dtype=np.int32).reshape(4))
+
+
 def _bc(bc):
-    a = np.ascontiguousarray(np.asarray(bc, dtype=np.int32).reshape(4))
+    """Pressure face types (west, east, south, north): 0 Neumann,
+    1 Dirichlet-0, 2 periodic (on both faces of an axis)."""
+    a = _faces(bc)
+    if ((a[0] == BC_PERIODIC) != (a[1] == BC_PERIODIC)) or ((a[2] == BC_PERIODIC) != (a[3] == BC_PERIODIC)):
+        raise ValueError("a periodic face needs its opposite face periodic too")
+    if np.any((a < 0) | (a > 2)):
+        raise ValueError("face type must be 0, 1 or 2")
     return a
+
+
+def is_singular(bc):
+    """A_f is singular (null space: constants) iff no face is Dirichlet."""
+    return not np.any(_bc(bc) == BC_DIRICHLET0)
+
+
+def periodic_axes(bc):
+    """bit 0: x periodic, bit 1: y periodic."""
+    a = _bc(bc)
+    return int(a[0] == BC_PERIODIC) | (int(a[2] == BC_PERIODIC) << 1)
 
 
 def _c64(a):
@@ -179,7 +203,7 @@ class OracleISM:
         self.bc = _bc(bc)
         self.kind = kind
         self.nu = nu
-        self.singular = not np.any(self.bc)
+        self.singular = is_singular(self.bc)
         self.Ac = coarse_operator(nx, ny, m, self.bc, kind)
         nc = self.Ac.shape[0]
         M = -self.Ac
@@ -328,7 +352,7 @@ class OracleACMV:
         self.nx, self.ny, self.m, self.nu = nx, ny, m, nu
         self.L = m.bit_length() - 1
         self.bc = _bc(bc)
-        self.singular = not np.any(self.bc)
+        self.singular = is_singular(self.bc)
         self.top = OracleISM(nx, ny, m, bc, kind="acm", nu=nu)     # exact level-L solve of A_L = m x five-point
 
     def cycle(self, p, b):
@@ -380,7 +404,7 @@ class OracleAccommodative:
     def __init__(self, nx, ny, m, bc=(0, 0, 0, 0)):
         self.nx, self.ny, self.m = nx, ny, m
         self.bc = _bc(bc)
-        self.singular = not np.any(self.bc)
+        self.singular = is_singular(self.bc)
         self.Ac = np.ascontiguousarray(coarse_operator(nx, ny, m, self.bc, "ism"))
 
     def solve(self, b, p0=None, tol_f=1e-6, tol_c=1e-5, cap_c=100000, cap_f=1000000):
@@ -396,7 +420,8 @@ class OracleAccommodative:
             return p, 0, 0, float(np.abs(r).max())
         rc = np.ascontiguousarray(restrict(r, self.m))
         ec = np.zeros_like(rc)
-        nc_it = lib().or_coarse_gs4(rc.shape[1], rc.shape[0], self.Ac, rc, ec, float(tol_c), int(cap_c))
+        nc_it = lib().or_coarse_gs4(rc.shape[1], rc.shape[0], self.Ac, rc, ec, float(tol_c), int(cap_c),
+                                    periodic_axes(self.bc))
         prolong_add(p, ec, self.m, self.bc)
         if self.singular:
             p -= p.mean()
@@ -419,7 +444,7 @@ def predictor(u, v, p, h, dt, nu, vel_bc, wall_u=(0, 0, 0, 0), u_in=None, conv_u
     ny, nx = p.shape
     us = np.empty((ny, nx + 1)); vs = np.empty((ny + 1, nx))
     uin = np.zeros(ny) if u_in is None else _c64(u_in)
-    lib().or_predictor(nx, ny, h, dt, nu, _bc(vel_bc), _c64(np.asarray(wall_u, float)),
+    lib().or_predictor(nx, ny, h, dt, nu, _faces(vel_bc), _c64(np.asarray(wall_u, float)),
                        uin, conv_u, _c64(u), _c64(v), _c64(p), us, vs)
     return us, vs
 
@@ -435,7 +460,7 @@ def correct(u, v, p, dp, h, dt, vel_bc):
     ny, nx = p.shape
     for a in (u, v, p):
         assert a.dtype == np.float64 and a.flags.c_contiguous
-    lib().or_correct(nx, ny, h, dt, _bc(vel_bc), _c64(dp), u, v, p)
+    lib().or_correct(nx, ny, h, dt, _faces(vel_bc), _c64(dp), u, v, p)
 
 
 def pressure_bc(vel_bc):

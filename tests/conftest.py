@@ -14,3 +14,5 @@ def pytest_configure(config):
 
 
 ALL_BCS = [(0, 0, 0, 0), (0, 1, 0, 0), (1, 1, 1, 1), (1, 0, 0, 1), (0, 0, 1, 0)]
+# periodic axes (face type 2 on both faces of the axis), alone and with walls
+PERIODIC_BCS = [(2, 2, 2, 2), (2, 2, 0, 0), (2, 2, 1, 0), (0, 1, 2, 2), (1, 1, 2, 2)]

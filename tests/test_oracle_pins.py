@@ -376,7 +376,7 @@ def test_coarse_gauss_seidel_converges_to_the_exact_coarse_solution(bc):
         rc -= rc.mean()
     ec = np.zeros_like(rc)
     Ac = np.ascontiguousarray(s.Ac)
-    it = O.lib().or_coarse_gs4(nx // m, ny // m, Ac, np.ascontiguousarray(rc), ec, 1e-13, 100000)
+    it = O.lib().or_coarse_gs4(nx // m, ny // m, Ac, np.ascontiguousarray(rc), ec, 1e-13, 100000, 0)
     assert 0 < it < 100000
     ex = s.coarse_solve(rc)
     if not any(bc):
