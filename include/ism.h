@@ -54,7 +54,12 @@ typedef enum {
     ISM_ERR_NOMEM = 5           /* device or host allocation failed */
 } ism_status;
 
-typedef enum { ISM_BC_NEUMANN = 0, ISM_BC_DIRICHLET0 = 1 } ism_bc;
+/* Pressure face types.  ISM_BC_PERIODIC is given on both faces of an axis
+ * (west and east, or south and north): the neighbour across the face is the
+ * cell at the other end of the row / column, and the bilinear correction
+ * interpolates across it between the last and the first coarse centre.  The
+ * paper's cases have walls only; periodic axes extend the same operators. */
+typedef enum { ISM_BC_NEUMANN = 0, ISM_BC_DIRICHLET0 = 1, ISM_BC_PERIODIC = 2 } ism_bc;
 
 typedef enum {
     ISM_FP64 = 0,   /* every step in IEEE double */
@@ -101,7 +106,8 @@ typedef struct {
                              operator only: Gauss-Seidel on the coarse equations until max |r_c| <=
                              accom_tol_c, bilinear correction, red-black sweeps on the fine grid until
                              max |r| <= tol (ism_solve's tol is then an absolute maximum norm and
-                             max_cycles caps the fine sweeps). */
+                             max_cycles caps the fine sweeps).  A periodic axis then needs an even
+                             number of coarse cells. */
     double accom_tol_c;   /* cycle 1: coarse criterion (absolute maximum norm, default 1e-5) */
     int accom_max_coarse; /* cycle 1: cap on coarse Gauss-Seidel iterations (default 100000) */
 } ism_options;
@@ -116,7 +122,11 @@ const char *ism_status_str(ism_status s);
  * tile/coarsening size).
  *   nx, ny   fine cells; both multiples of `coarsen`, nx*ny <= 2^31.
  *   h        cell size (used by proj_step only; > 0).
- *   bc       host, 4 ints (ism_bc) for the west, east, south, north faces.
+ *   bc       host, 4 ints (ism_bc) for the west, east, south, north faces;
+ *            ISM_BC_PERIODIC on both faces of an axis or on neither, and
+ *            then at least 4 coarse cells along that axis.  A_f is singular
+ *            (constants) when no face is Dirichlet-0: the solve then works
+ *            on the mean-free subspace.
  *   coarsen  m in {8, 16, 32}: coarse cells are m x m blocks of fine cells;
  *            0: the library picks 16 or 32 (those dividing nx and ny with at
  *            least 2 coarse cells per direction) by timing two solves of an
@@ -224,8 +234,9 @@ ism_status ism_residual_restrict_noalloc(int nx, int ny, int coarsen, const int 
  * faces are Neumann); rc, ec: device, (ny/m)*(nx/m) values of T. */
 ism_status ism_coarse_solve(ism_ctx *ctx, const void *rc, void *ec);
 
-/* p += P e_c (bilinear, Eq. 5, mirror ghost centres beyond the boundary;
- * constant per block for ISM_COARSE_ACM). */
+/* p += P e_c (bilinear, Eq. 5, mirror ghost centres beyond a wall, the
+ * periodic extension across a periodic face; constant per block for
+ * ISM_COARSE_ACM). */
 ism_status ism_prolong_add(ism_ctx *ctx, const void *ec, void *p);
 
 /* Measurement helper: run `reps` smoothing passes of `sweeps` sweeps each
@@ -241,7 +252,9 @@ ism_status ism_time_pass(ism_ctx *ctx, void *p, const void *b, int sweeps, int r
 /* Velocity boundary setup for proj_step.
  *   vel_bc  host, 4 ints (ism_vel_bc).  INFLOW only on the west face,
  *           OUTFLOW only on the east face; the pressure boundary given to
- *           ism_setup must be Dirichlet-0 exactly on OUTFLOW faces.
+ *           ism_setup must be Dirichlet-0 exactly on OUTFLOW faces and have
+ *           no periodic face (the projection step has walls only), else
+ *           ISM_ERR_ARG.
  *   wall_u  host, 4 doubles: tangential wall speed of NOSLIP faces.
  *   u_in    device, ny floats: west inflow profile (NULL if no inflow);
  *           read at every proj_step, so the caller may update it.

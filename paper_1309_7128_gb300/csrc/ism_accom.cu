@@ -13,7 +13,10 @@
 // are rounded at every step (no contraction) in the neighbour order of the
 // oracle.  A_c comes from its closed form (Sec. 3.3, Eq. 5-7):
 // A_c = 1/4 (S_y x S_x) - 4 I with S = tridiag(1, 2, 1), end diagonal 3 at
-// a Neumann end and 1 at a Dirichlet-0 end.
+// a Neumann end and 1 at a Dirichlet-0 end, circulant on a periodic axis
+// (whose neighbours then wrap; such an axis has an even number >= 4 of
+// coarse cells, so the nine neighbours are distinct and the four colours
+// independent).
 #include <math.h>
 #include <string.h>
 
@@ -33,20 +36,22 @@ namespace {
 
 constexpr int AC_THREADS = 1024;
 
-__device__ __forceinline__ double s_entry(int I, int Ip, int n, int lo_dir, int hi_dir)
+// S[I][I + d] for |d| <= 1 (d != 0: a neighbour that exists)
+__device__ __forceinline__ double s_entry(int I, int d, int n, int lo_dir, int hi_dir, bool periodic)
 {
-    if (I != Ip) return (I - Ip == 1 || Ip - I == 1) ? 1.0 : 0.0;
+    if (d != 0) return 1.0;
+    if (periodic) return 2.0;
     if (n == 1) return (lo_dir ? 1.0 : 3.0) + (hi_dir ? 1.0 : 3.0) - 2.0;
     if (I == 0) return lo_dir ? 1.0 : 3.0;
     if (I == n - 1) return hi_dir ? 1.0 : 3.0;
     return 2.0;
 }
 
-// coefficient of e[J + dJ][I + dI] in row (I, J) of A_c
+// coefficient of e[J + dJ][I + dI] (wrapped on a periodic axis) in row (I, J) of A_c
 __device__ __forceinline__ double ac_coef(int I, int J, int dI, int dJ, int ncx, int ncy, int bcmask)
 {
-    const double sx = s_entry(I, I + dI, ncx, bcmask & 1, bcmask & 2);
-    const double sy = s_entry(J, J + dJ, ncy, bcmask & 4, bcmask & 8);
+    const double sx = s_entry(I, dI, ncx, bcmask & 1, bcmask & 2, (bcmask & ISM_PER_X) != 0);
+    const double sy = s_entry(J, dJ, ncy, bcmask & 4, bcmask & 8, (bcmask & ISM_PER_Y) != 0);
     double a = __dmul_rn(0.25, __dmul_rn(sx, sy));
     if (dI == 0 && dJ == 0) a = __dadd_rn(a, -4.0);
     return a;
@@ -60,7 +65,9 @@ __device__ __forceinline__ double row_sum(const double *e, int I, int J, int ncx
     double s = 0.0;
     for (int dJ = -1; dJ <= 1; ++dJ)
         for (int dI = -1; dI <= 1; ++dI) {
-            const int K = J + dJ, L = I + dI;
+            int K = J + dJ, L = I + dI;
+            if (bcmask & ISM_PER_Y) K = K < 0 ? K + ncy : (K >= ncy ? K - ncy : K);
+            if (bcmask & ISM_PER_X) L = L < 0 ? L + ncx : (L >= ncx ? L - ncx : L);
             if ((!centre && dI == 0 && dJ == 0) || K < 0 || K >= ncy || L < 0 || L >= ncx) continue;
             s = __dadd_rn(s, __dmul_rn(ac_coef(I, J, dI, dJ, ncx, ncy, bcmask), e[(size_t)K * ncx + L]));
         }
@@ -125,11 +132,7 @@ __global__ void k_resmax(const double *__restrict__ p, const double *__restrict_
     const long long n = (long long)nx * ny;
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(k % nx), j = (int)(k / nx);
-        double s = 0.0;
-        if (i > 0) s += p[k - 1];
-        if (i < nx - 1) s += p[k + 1];
-        if (j > 0) s += p[k - nx];
-        if (j < ny - 1) s += p[k + nx];
+        const double s = nb_sum<double>([&](long long q) -> double { return p[q]; }, k, i, j, nx, ny, bcmask);
         const double r = b[k] - (s - (double)diag_count(i, j, nx, ny, bcmask) * p[k]);
         mx = fmax(mx, fabs(r));
     }

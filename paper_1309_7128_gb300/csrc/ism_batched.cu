@@ -190,11 +190,7 @@ __global__ void k_b_refine(BDom *dom, const int2 *chunks, BState *bs)
             return v;
         };
         const double pc = P(idx);
-        double s = 0.0;
-        if (i > 0) s += P(idx - 1);
-        if (i < nx - 1) s += P(idx + 1);
-        if (j > 0) s += P(idx - nx);
-        if (j < ny - 1) s += P(idx + nx);
+        const double s = nb_sum<double>(P, idx, i, j, nx, ny, D.bcmask);
         const double r = D.b64[idx] - (s - (double)diag_count(i, j, nx, ny, D.bcmask) * pc);
         if (UPDATE) p_out[idx] = pc;
         D.r32[idx] = (float)r;

@@ -80,11 +80,7 @@ __global__ void k_refine(double *p0, double *p1,
             return v;
         };
         const double pc = P(idx);
-        double s = 0.0;
-        if (i > 0) s += P(idx - 1);
-        if (i < nx - 1) s += P(idx + 1);
-        if (j > 0) s += P(idx - nx);
-        if (j < ny - 1) s += P(idx + nx);
+        const double s = nb_sum<double>(P, (long long)idx, i, j, nx, ny, bcmask);
         const double r = b[idx] - (s - (double)diag_count(i, j, nx, ny, bcmask) * pc);
         if (UPDATE) p_out[idx] = pc;
         r32[idx] = (float)r;
@@ -154,11 +150,35 @@ static const double kPi = 3.14159265358979323846;
 //   D-D: sin(theta (i+1/2)), theta = pi (k+1) / n      (DST-II)
 //   N-D: cos(theta (i+1/2)), theta = pi (k+1/2) / n    (DCT-IV)
 //   D-N: sin(theta (i+1/2)), theta = pi (k+1/2) / n    (DST-IV)
-// Q[i*n + k] is component i of unit eigenvector k.
-static void s_eigen(int n, int lo_dir, int hi_dir, std::vector<double> &Q, std::vector<double> &lam)
+// On a periodic axis S is circulant, diagonalised by the real Fourier modes
+// (n even): column 0 the constant, columns 2t-1, 2t (t = 1..n/2-1)
+// cos(theta i), sin(theta i) with theta = 2 pi t / n, column n-1 (-1)^i;
+// eigenvalue 2 + 2 cos(theta) (0 for the last).
+// Q[i*n + k] is component i of unit eigenvector k.  lo, hi: ism_bc of the
+// two ends.
+static void s_eigen(int n, int lo, int hi, std::vector<double> &Q, std::vector<double> &lam)
 {
     Q.assign((size_t)n * n, 0.0);
     lam.assign(n, 0.0);
+    if (lo == ISM_BC_PERIODIC) {
+        for (int k = 0; k < n; ++k) {
+            const int t = (k + 1) / 2;                 // frequency of column k
+            const double th = 2.0 * kPi * t / n;
+            lam[k] = 2.0 + 2.0 * cos(th);
+            double nrm = 0.0;
+            for (int i = 0; i < n; ++i) {
+                const double v = (k == 0) ? 1.0 : (k == n - 1) ? ((i & 1) ? -1.0 : 1.0)
+                                 : (k & 1) ? cos(th * i) : sin(th * i);
+                Q[(size_t)i * n + k] = v;
+                nrm += v * v;
+            }
+            nrm = 1.0 / sqrt(nrm);
+            for (int i = 0; i < n; ++i) Q[(size_t)i * n + k] *= nrm;
+        }
+        lam[n - 1] = 0.0;                              // 2 + 2 cos(pi), exactly
+        return;
+    }
+    const int lo_dir = lo == ISM_BC_DIRICHLET0, hi_dir = hi == ISM_BC_DIRICHLET0;
     for (int k = 0; k < n; ++k) {
         double th;
         bool use_sin = lo_dir != 0;
@@ -279,8 +299,10 @@ ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarse
     if ((long long)nx * ny > (1LL << 31) || nx > (1 << 20) || ny > (1 << 20)) return ISM_ERR_ARG;
     if (nx / coarsen > 1024 || ny / coarsen > 1024) return ISM_ERR_ARG;
     if (!(h > 0.0) || !isfinite(h)) return ISM_ERR_ARG;
-    for (int f = 0; f < 4; ++f)
-        if (bc[f] != ISM_BC_NEUMANN && bc[f] != ISM_BC_DIRICHLET0) return ISM_ERR_ARG;
+    const int mask = ism_bc_mask(bc);
+    if (mask < 0) return ISM_ERR_ARG;
+    if ((mask & ISM_PER_X) && nx / coarsen < 4) return ISM_ERR_ARG;
+    if ((mask & ISM_PER_Y) && ny / coarsen < 4) return ISM_ERR_ARG;
     if (prec != ISM_FP64 && prec != ISM_MIXED) return ISM_ERR_ARG;
 
     ism_ctx *ctx = (ism_ctx *)calloc(1, sizeof(ism_ctx));
@@ -292,12 +314,9 @@ ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarse
     ctx->ncy = ny / coarsen;
     ctx->n = (long long)nx * ny;
     ctx->h = h;
-    ctx->bcmask = 0;
-    for (int f = 0; f < 4; ++f) {
-        ctx->bc[f] = bc[f];
-        if (bc[f]) ctx->bcmask |= 1 << f;
-    }
-    ctx->singular = ctx->bcmask == 0;
+    ctx->bcmask = mask;
+    for (int f = 0; f < 4; ++f) ctx->bc[f] = bc[f];
+    ctx->singular = (mask & 15) == 0;
     {
         static unsigned long long next_uid = 1;
         ctx->uid = __atomic_fetch_add(&next_uid, 1ULL, __ATOMIC_RELAXED);
@@ -411,6 +430,9 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     if (o->coarse_tc < 0 || o->coarse_tc > 1) return ISM_ERR_ARG;
     if (o->cycle < 0 || o->cycle > 1) return ISM_ERR_ARG;
     if (o->cycle == 1 && (ctx->prec != ISM_FP64 || o->kind != ISM_COARSE_ISM)) return ISM_ERR_ARG;
+    // the four-colour coarse Gauss-Seidel needs an even coarse count along a periodic axis
+    if (o->cycle == 1 && (((ctx->bcmask & ISM_PER_X) && (ctx->ncx & 1)) || ((ctx->bcmask & ISM_PER_Y) && (ctx->ncy & 1))))
+        return ISM_ERR_ARG;
     if (!(o->accom_tol_c > 0.0) || o->accom_max_coarse < 1) return ISM_ERR_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
     const int kind_changed = o->kind != ctx->opt.kind;

@@ -47,8 +47,8 @@ struct ism_ctx {
     long long n;               // nx * ny
     double h;
     int bc[4];
-    int bcmask;                // bit f set: face f is Dirichlet-0
-    int singular;              // all faces Neumann
+    int bcmask;                // ism_bc_mask(bc)
+    int singular;              // no Dirichlet-0 face (A_f 1 = 0)
     int prec;
     ism_options opt;
     cudaStream_t user_stream;  // ordering stream given by the caller
@@ -125,6 +125,24 @@ struct ism_ctx {
 
 // ism_setup for a given coarsening factor (8, 16, 32); ism_setup adds the
 // autotuned choice (coarsen = 0, ism_tune.cu).
+// Face mask of the kernels: bit f (W, E, S, N = 0..3) set when face f is
+// Dirichlet-0; ISM_PER_X / ISM_PER_Y when the x / y axis is periodic (face
+// type ISM_BC_PERIODIC on both of its faces).  -1 for an invalid bc.
+constexpr int ISM_PER_X = 16, ISM_PER_Y = 32;
+inline int ism_bc_mask(const int bc[4])
+{
+    int mask = 0;
+    for (int f = 0; f < 4; ++f) {
+        if (bc[f] != ISM_BC_NEUMANN && bc[f] != ISM_BC_DIRICHLET0 && bc[f] != ISM_BC_PERIODIC) return -1;
+        if (bc[f] == ISM_BC_DIRICHLET0) mask |= 1 << f;
+    }
+    if ((bc[0] == ISM_BC_PERIODIC) != (bc[1] == ISM_BC_PERIODIC)) return -1;
+    if ((bc[2] == ISM_BC_PERIODIC) != (bc[3] == ISM_BC_PERIODIC)) return -1;
+    if (bc[0] == ISM_BC_PERIODIC) mask |= ISM_PER_X;
+    if (bc[2] == ISM_BC_PERIODIC) mask |= ISM_PER_Y;
+    return mask;
+}
+
 ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarsen, ism_precision prec,
                            void *stream, ism_ctx **out);
 

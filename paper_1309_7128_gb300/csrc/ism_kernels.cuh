@@ -2,10 +2,12 @@
 // and ism_batched.cu; everything here is internal).
 //
 // Fine-grid conventions: row-major (i fastest), face order W, E, S, N,
-// bcmask bit f set when face f is Dirichlet-0.  The five-point flux sum is
+// bcmask bit f set when face f is Dirichlet-0, ISM_PER_X / ISM_PER_Y when an
+// axis is periodic.  The five-point flux sum is
 //   (A_f p)_c = sum_nb p_nb - d_c p_c,
-//   d_c = (#in-domain neighbours) + 2 (#Dirichlet-0 faces of the cell),
-// so the Gauss-Seidel point update is p_c = (sum_nb p_nb - b_c) / d_c.
+//   d_c = (#neighbours) + 2 (#Dirichlet-0 faces of the cell),
+// the cell at the other end of a periodic row / column counting as a
+// neighbour, so the Gauss-Seidel point update is p_c = (sum_nb p_nb - b_c) / d_c.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,16 +27,43 @@ template <typename T> __device__ __forceinline__ T inv_diag(int d);
 template <> __device__ __forceinline__ double inv_diag<double>(int d) { return c_invd64[d]; }
 template <> __device__ __forceinline__ float inv_diag<float>(int d) { return c_invd32[d]; }
 
-// d_c: each boundary face of the cell removes its neighbour (-1) and, when
-// Dirichlet-0, adds the ghost's 2 p_c (+2): net +1 (Dirichlet) or -1 (Neumann).
+// d_c: each wall face of the cell removes its neighbour (-1) and, when
+// Dirichlet-0, adds the ghost's 2 p_c (+2): net +1 (Dirichlet) or -1
+// (Neumann); a periodic face keeps its (wrapped) neighbour.
 __device__ __forceinline__ int diag_count(int x, int y, int nx, int ny, int bcmask)
 {
     int d = 4;
-    if (x == 0) d += (bcmask & 1) ? 1 : -1;
-    if (x == nx - 1) d += (bcmask & 2) ? 1 : -1;
-    if (y == 0) d += (bcmask & 4) ? 1 : -1;
-    if (y == ny - 1) d += (bcmask & 8) ? 1 : -1;
+    if (!(bcmask & ISM_PER_X)) {
+        if (x == 0) d += (bcmask & 1) ? 1 : -1;
+        if (x == nx - 1) d += (bcmask & 2) ? 1 : -1;
+    }
+    if (!(bcmask & ISM_PER_Y)) {
+        if (y == 0) d += (bcmask & 4) ? 1 : -1;
+        if (y == ny - 1) d += (bcmask & 8) ? 1 : -1;
+    }
     return d;
+}
+
+// sum of the neighbour values of cell (x, y) at linear index idx, P(k) giving
+// the value at index k: in-domain neighbours, and across a periodic face the
+// cell at the other end of the row / column
+template <typename T, typename F>
+__device__ __forceinline__ T nb_sum(F P, long long idx, int x, int y, int nx, int ny, int bcmask)
+{
+    const long long wrap_y = (long long)(ny - 1) * nx;
+    T s = (T)0;
+    if (x > 0) s += P(idx - 1); else if (bcmask & ISM_PER_X) s += P(idx + (nx - 1));
+    if (x < nx - 1) s += P(idx + 1); else if (bcmask & ISM_PER_X) s += P(idx - (nx - 1));
+    if (y > 0) s += P(idx - nx); else if (bcmask & ISM_PER_Y) s += P(idx + wrap_y);
+    if (y < ny - 1) s += P(idx + nx); else if (bcmask & ISM_PER_Y) s += P(idx - wrap_y);
+    return s;
+}
+
+// v mod n in [0, n) for any int v
+__device__ __forceinline__ int wrap_mod(int v, int n)
+{
+    const int r = v % n;
+    return r < 0 ? r + n : r;
 }
 
 // ----------------------------------------------------------------- reductions
@@ -229,10 +258,18 @@ __device__ __forceinline__ T coarse_ghost(const T *__restrict__ q, int I, int J,
                                           int ncy, int bcmask)
 {
     bool neg = false;
-    if (I < 0) { I = 0; neg ^= (bcmask & 1) != 0; }
-    if (I >= ncx) { I = ncx - 1; neg ^= (bcmask & 2) != 0; }
-    if (J < 0) { J = 0; neg ^= (bcmask & 4) != 0; }
-    if (J >= ncy) { J = ncy - 1; neg ^= (bcmask & 8) != 0; }
+    if (bcmask & ISM_PER_X) {
+        I = wrap_mod(I, ncx);
+    } else {
+        if (I < 0) { I = 0; neg ^= (bcmask & 1) != 0; }
+        if (I >= ncx) { I = ncx - 1; neg ^= (bcmask & 2) != 0; }
+    }
+    if (bcmask & ISM_PER_Y) {
+        J = wrap_mod(J, ncy);
+    } else {
+        if (J < 0) { J = 0; neg ^= (bcmask & 4) != 0; }
+        if (J >= ncy) { J = ncy - 1; neg ^= (bcmask & 8) != 0; }
+    }
     T v = q[(size_t)J * ncx + I];
     return neg ? -v : v;
 }
@@ -271,11 +308,7 @@ __global__ void k_rbgs_colour(T *__restrict__ p, const T *__restrict__ b, int nx
     const int i = 2 * t + ((colour + j) & 1);
     if (i >= nx) return;
     const size_t idx = (size_t)j * nx + i;
-    T s = (T)0;
-    if (i > 0) s += p[idx - 1];
-    if (i < nx - 1) s += p[idx + 1];
-    if (j > 0) s += p[idx - nx];
-    if (j < ny - 1) s += p[idx + nx];
+    const T s = nb_sum<T>([&](long long k) -> T { return p[k]; }, (long long)idx, i, j, nx, ny, bcmask);
     p[idx] = (s - scale * b[idx]) * inv_diag<T>(diag_count(i, j, nx, ny, bcmask));
 }
 
@@ -318,11 +351,7 @@ __global__ void k_resid2(const T *__restrict__ p, const T *__restrict__ b, T *__
             const int i = 2 * I + (k & 1), j = 2 * J + (k >> 1);
             const size_t idx = (size_t)j * nx + i;
             const T pc = p[idx];
-            T s = 0;
-            if (i > 0) s += p[idx - 1];
-            if (i < nx - 1) s += p[idx + 1];
-            if (j > 0) s += p[idx - nx];
-            if (j < ny - 1) s += p[idx + nx];
+            const T s = nb_sum<T>([&](long long q) -> T { return p[q]; }, (long long)idx, i, j, nx, ny, bcmask);
             const T r = b[idx] - (s - (T)diag_count(i, j, nx, ny, bcmask) * pc);
             acc += r;
             r2 += (double)r * (double)r;
@@ -351,11 +380,7 @@ __global__ void k_resid(const T *__restrict__ p, const T *__restrict__ b, T *__r
         const int i = I * m + (k % m), j = J * m + (k / m);
         const size_t idx = (size_t)j * nx + i;
         const T pc = p[idx];
-        T s = (T)0;
-        if (i > 0) s += p[idx - 1];
-        if (i < nx - 1) s += p[idx + 1];
-        if (j > 0) s += p[idx - nx];
-        if (j < ny - 1) s += p[idx + nx];
+        const T s = nb_sum<T>([&](long long q) -> T { return p[q]; }, (long long)idx, i, j, nx, ny, bcmask);
         const T r = b[idx] - (s - (T)diag_count(i, j, nx, ny, bcmask) * pc);
         acc += r;
         r2 += r * r;

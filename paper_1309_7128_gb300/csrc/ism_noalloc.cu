@@ -68,11 +68,8 @@ extern "C" ism_status ism_residual_restrict_noalloc(int nx, int ny, int coarsen,
     if (nx <= 0 || ny <= 0 || nx % coarsen || ny % coarsen) return ISM_ERR_ARG;
     const int ncx = nx / coarsen, ncy = ny / coarsen;
     if ((long long)ncx * ncy > ISM_NOALLOC_MAX_COARSE) return ISM_ERR_ARG;
-    int bcmask = 0;
-    for (int f = 0; f < 4; ++f) {
-        if (bc[f] != ISM_BC_NEUMANN && bc[f] != ISM_BC_DIRICHLET0) return ISM_ERR_ARG;
-        if (bc[f]) bcmask |= 1 << f;
-    }
+    const int bcmask = ism_bc_mask(bc);
+    if (bcmask < 0) return ISM_ERR_ARG;
     double *scratch = nullptr;
     ism_status s = scratch_address(&scratch);
     if (s != ISM_OK) return s;

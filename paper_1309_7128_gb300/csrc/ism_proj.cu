@@ -159,8 +159,9 @@ extern "C" ism_status ism_set_flow(ism_ctx *ctx, const int vel_bc[4], const doub
         if (vel_bc[f] < ISM_VEL_NOSLIP || vel_bc[f] > ISM_VEL_OUTFLOW) return ISM_ERR_ARG;
         if (vel_bc[f] == ISM_VEL_INFLOW && f != 0) return ISM_ERR_ARG;
         if (vel_bc[f] == ISM_VEL_OUTFLOW && f != 1) return ISM_ERR_ARG;
-        // pressure is Dirichlet-0 exactly on outflow faces
+        // pressure is Dirichlet-0 exactly on outflow faces; walls only
         if ((vel_bc[f] == ISM_VEL_OUTFLOW) != (ctx->bc[f] == ISM_BC_DIRICHLET0)) return ISM_ERR_ARG;
+        if (ctx->bc[f] == ISM_BC_PERIODIC) return ISM_ERR_ARG;
         if (!isfinite(wall_u[f])) return ISM_ERR_ARG;
     }
     if (vel_bc[0] == ISM_VEL_INFLOW && !u_in) return ISM_ERR_ARG;

@@ -24,7 +24,11 @@
 // equals the sum over in-domain neighbours).  CTAs whose region lies strictly
 // inside the domain take a path with divisor 4 everywhere and the right-hand
 // side pre-scaled by 1/4; CTAs touching the boundary compute each cell's
-// divisor d = 4 +- 1 per boundary face (Neumann -1, Dirichlet-0 +1).
+// divisor d = 4 +- 1 per boundary face (Neumann -1, Dirichlet-0 +1).  Along
+// a periodic axis the boundary CTAs load the region's out-of-domain rows /
+// columns from the other end of the domain (index mod n) and update them like
+// any other cell: they are copies, and the error front argument above holds
+// unchanged.
 //
 // Options fused into the pass:
 //  PROLONG: add P e_c - mean while loading.  P e_c is evaluated in the
@@ -83,6 +87,7 @@ __device__ __forceinline__ const float2 *bplane(const float *row, int qp, int la
 __device__ __forceinline__ float row_adj(int y, int ny, int bcmask)
 {
     float d = 0.0f;
+    if (bcmask & ISM_PER_Y) return d;
     if (y == 0) d += (bcmask & 4) ? 1.0f : -1.0f;
     if (y == ny - 1) d += (bcmask & 8) ? 1.0f : -1.0f;
     return d;
@@ -188,8 +193,11 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
     float *__restrict__ pout = in ? a.e0 : a.e1;
     float *bs = bsm + ry0 * SRW;           // this warp's b rows (two colour planes per row)
     // nx % 4 == 0 and cx % 4 == 0: a thread's 4 columns are all in or all out
-    const bool colin = (unsigned)cx < (unsigned)nx;
-    const bool colvalid = colin && (SNC * lane >= Hc) && (SNC * lane < Hc + TW);
+    const bool per_x = EDGE && (a.bcmask & ISM_PER_X), per_y = EDGE && (a.bcmask & ISM_PER_Y);
+    const bool coldom = (unsigned)cx < (unsigned)nx;
+    const bool colin = coldom || per_x;    // columns loaded and updated
+    const bool colvalid = coldom && (SNC * lane >= Hc) && (SNC * lane < Hc + TW);
+    const int cxl = per_x ? wrap_mod(cx, nx) : cx;   // column loaded from
 
     // divisor part from the W/E faces and its reciprocal (edge launch)
     float idq[SNC], rq[SNC];
@@ -197,18 +205,18 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
     for (int q = 0; q < SNC; ++q) {
         const int x = cx + q;
         float d = 4.0f;
-        if (x == 0) d += (a.bcmask & 1) ? 1.0f : -1.0f;
-        if (x == nx - 1) d += (a.bcmask & 2) ? 1.0f : -1.0f;
+        if (!per_x && x == 0) d += (a.bcmask & 1) ? 1.0f : -1.0f;
+        if (!per_x && x == nx - 1) d += (a.bcmask & 2) ? 1.0f : -1.0f;
         idq[q] = d;
         rq[q] = __frcp_rn(d);
     }
     EdgeRows er;
     {
         const int yw = y0 + ry0;                     // global row of the warp's row 0
-        er.rlo = max(0, -yw);
-        er.rhi = min(SRR, ny - yw);
-        er.rs = (yw <= 0 && 0 < yw + SRR) ? -yw : -1;
-        er.rn = (yw <= ny - 1 && ny - 1 < yw + SRR) ? ny - 1 - yw : -1;
+        er.rlo = per_y ? 0 : max(0, -yw);
+        er.rhi = per_y ? SRR : min(SRR, ny - yw);
+        er.rs = (!per_y && yw <= 0 && 0 < yw + SRR) ? -yw : -1;
+        er.rn = (!per_y && yw <= ny - 1 && ny - 1 < yw + SRR) ? ny - 1 - yw : -1;
         const float adjS = (a.bcmask & 4) ? 1.0f : -1.0f;
         const float adjN = (a.bcmask & 8) ? 1.0f : -1.0f;
 #pragma unroll
@@ -229,31 +237,41 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
     int Jg0 = 0, nrow = 0, Ic0 = 0, ncol = 0;
     float *esm = gsm + SGROWS * SRW;
     if (PROLONG) {
-        Jg0 = acm ? max(0, (y0 - 1) >> lm) : max(0, ((y0 - 1 - hm + m) >> lm) - 1);
-        const int Jg1 = min(a.ncy - 1, acm ? (y0 + SRH) >> lm : ((y0 + SRH - hm + m) >> lm));
+        // along a periodic axis the coarse indices are not clamped: they run
+        // over the periodic extension and wrap when e_c is read
+        Jg0 = acm ? (y0 - 1) >> lm : ((y0 - 1 - hm + m) >> lm) - 1;
+        int Jg1 = acm ? (y0 + SRH) >> lm : ((y0 + SRH - hm + m) >> lm);
+        if (!per_y) { Jg0 = max(0, Jg0); Jg1 = min(a.ncy - 1, Jg1); }
         nrow = Jg1 - Jg0 + 1;
-        // (a) columns Ic0..Ic1: the bilinear neighbours of the in-domain columns
-        const int xs = max(x0, 0), xe = min(x0 + SRW, nx) - 1;
-        Ic0 = acm ? (xs >> lm) : max(0, ((xs - hm + m) >> lm) - 1);
-        const int Ic1 = acm ? min(a.ncx - 1, xe >> lm) : min(a.ncx - 1, ((xe - hm + m) >> lm));
+        // (a) columns Ic0..Ic1: the bilinear neighbours of the loaded columns
+        const int xs = per_x ? x0 : max(x0, 0), xe = (per_x ? x0 + SRW : min(x0 + SRW, nx)) - 1;
+        Ic0 = acm ? (xs >> lm) : ((xs - hm + m) >> lm) - 1;
+        int Ic1 = acm ? xe >> lm : ((xe - hm + m) >> lm);
+        if (!per_x) { Ic0 = max(0, Ic0); Ic1 = min(a.ncx - 1, Ic1); }
         ncol = Ic1 - Ic0 + 1;
         for (int t = threadIdx.x; t < nrow * ncol; t += STHREADS) {
             const int jr = t / ncol, c = t - jr * ncol;
-            esm[t] = a.E[(size_t)(Jg0 + jr) * a.ncx + Ic0 + c];
+            const int J = per_y ? wrap_mod(Jg0 + jr, a.ncy) : Jg0 + jr;
+            const int I = per_x ? wrap_mod(Ic0 + c, a.ncx) : Ic0 + c;
+            esm[t] = a.E[(size_t)J * a.ncx + I];
         }
     }
 #pragma unroll
     for (int r = 0; r < SRR + 2; ++r) {
-        const int y = y0 + ry0 + r - 1;
+        int y = y0 + ry0 + r - 1;
+        bool rowin = (unsigned)y < (unsigned)ny;
+        if (per_y && !rowin) { y = wrap_mod(y, ny); rowin = true; }   // periodic copy
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if ((unsigned)y < (unsigned)ny && colin) v = *reinterpret_cast<const float4 *>(pin + (size_t)y * nx + cx);
+        if (rowin && colin) v = *reinterpret_cast<const float4 *>(pin + (size_t)y * nx + cxl);
         P[r][0] = v.x; P[r][1] = v.y; P[r][2] = v.z; P[r][3] = v.w;
     }
 #pragma unroll
     for (int r = 0; r < SRR; ++r) {
-        const int y = y0 + ry0 + r;
+        int y = y0 + ry0 + r;
+        bool rowin = (unsigned)y < (unsigned)ny;
+        if (per_y && !rowin) { y = wrap_mod(y, ny); rowin = true; }
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if ((unsigned)y < (unsigned)ny && colin) v = *reinterpret_cast<const float4 *>(a.b + (size_t)y * nx + cx);
+        if (rowin && colin) v = *reinterpret_cast<const float4 *>(a.b + (size_t)y * nx + cxl);
         if (!edge) { v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f; }
         float2 *row = reinterpret_cast<float2 *>(bs + r * SRW);
         row[lane] = make_float2(v.x, v.z);
@@ -267,7 +285,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         for (int t = threadIdx.x; t < nrow * 32; t += STHREADS) {
             const int jr = t >> 5, l = t & 31, xb = x0 + SNC * l;
             float g[SNC] = {0.f, 0.f, 0.f, 0.f};
-            if ((unsigned)xb < (unsigned)nx) {
+            if ((unsigned)xb < (unsigned)nx || per_x) {
                 const float *er = esm + jr * ncol - Ic0;      // er[I] = e_c[Jg0 + jr][I], Ic0 <= I <= Ic1
 #pragma unroll
                 for (int q = 0; q < SNC; ++q) {
@@ -277,8 +295,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
                     } else {
                         const int I0 = ((x - hm + m) >> lm) - 1;
                         const float tx = ((float)(x - I0 * m - hm) + 0.5f) * invm;
-                        const float qa = I0 < 0 ? ((a.bcmask & 1) ? -er[0] : er[0]) : er[I0];
-                        const float qb = I0 + 1 >= ncx ? ((a.bcmask & 2) ? -er[ncx - 1] : er[ncx - 1]) : er[I0 + 1];
+                        float qa, qb;
+                        if (per_x) {
+                            qa = er[I0];
+                            qb = er[I0 + 1];
+                        } else {
+                            qa = I0 < 0 ? ((a.bcmask & 1) ? -er[0] : er[0]) : er[I0];
+                            qb = I0 + 1 >= ncx ? ((a.bcmask & 2) ? -er[ncx - 1] : er[ncx - 1]) : er[I0 + 1];
+                        }
                         g[q] = (1.0f - tx) * qa + tx * qb;
                     }
                 }
@@ -291,7 +315,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
 #pragma unroll
         for (int r = 0; r < SRR + 2; ++r) {
             const int y = y0 + ry0 + r - 1;
-            if ((unsigned)y < (unsigned)ny && colin) {
+            if (((unsigned)y < (unsigned)ny || per_y) && colin) {
                 float4 ga, gb;
                 float wa, wb;
                 if (acm) {
@@ -304,8 +328,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
                     const float ty = ((float)(y - J0 * m - hm) + 0.5f) * invm;
                     int Ja = J0, Jb = J0 + 1;
                     float sa = 1.f, sb = 1.f;
-                    if (Ja < 0) { Ja = 0; if (a.bcmask & 4) sa = -1.f; }
-                    if (Jb >= a.ncy) { Jb = a.ncy - 1; if (a.bcmask & 8) sb = -1.f; }
+                    if (!per_y && Ja < 0) { Ja = 0; if (a.bcmask & 4) sa = -1.f; }
+                    if (!per_y && Jb >= a.ncy) { Jb = a.ncy - 1; if (a.bcmask & 8) sb = -1.f; }
                     ga = gs4[(Ja - Jg0) * 32];
                     gb = gs4[(Jb - Jg0) * 32];
                     wa = sa * (1.0f - ty);

@@ -50,12 +50,13 @@ extern "C" ism_status ism_setup(int nx, int ny, double h, const int bc[4], int c
     // the argument checks of ism_setup_fixed that do not depend on m, first
     if (!out || !bc || nx <= 0 || ny <= 0 || !(h > 0.0) || !isfinite(h)) return ISM_ERR_ARG;
     if ((long long)nx * ny > (1LL << 31) || nx > (1 << 20) || ny > (1 << 20)) return ISM_ERR_ARG;
-    for (int f = 0; f < 4; ++f)
-        if (bc[f] != ISM_BC_NEUMANN && bc[f] != ISM_BC_DIRICHLET0) return ISM_ERR_ARG;
+    const int mask = ism_bc_mask(bc);
+    if (mask < 0) return ISM_ERR_ARG;
     if (prec != ISM_FP64 && prec != ISM_MIXED) return ISM_ERR_ARG;
     std::vector<int> cand;
+    const int minx = (mask & ISM_PER_X) ? 4 : 2, miny = (mask & ISM_PER_Y) ? 4 : 2;
     for (int m : {16, 32})
-        if (nx % m == 0 && ny % m == 0 && nx / m >= 2 && ny / m >= 2 && nx / m <= 1024 && ny / m <= 1024)
+        if (nx % m == 0 && ny % m == 0 && nx / m >= minx && ny / m >= miny && nx / m <= 1024 && ny / m <= 1024)
             cand.push_back(m);
     if (cand.empty()) return ISM_ERR_ARG;
     if (cand.size() == 1) return ism_setup_fixed(nx, ny, h, bc, cand[0], prec, stream, out);

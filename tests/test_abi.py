@@ -33,7 +33,12 @@ def test_status_strings(L):
     (100, 64, 1.0, (0, 0, 0, 0), 16),    # nx not a multiple of m
     (64, 64, 1.0, (0, 0, 0, 0), 12),     # m not in {8, 16, 32}
     (64, 64, 0.0, (0, 0, 0, 0), 16),     # h <= 0
-    (64, 64, 1.0, (0, 2, 0, 0), 16),     # bad face type
+    (64, 64, 1.0, (0, 3, 0, 0), 16),     # bad face type
+    (64, 64, 1.0, (0, 2, 0, 0), 16),     # periodic east face without a periodic west face
+    (64, 64, 1.0, (0, 0, 2, 1), 16),     # periodic south face, Dirichlet north face
+    (48, 64, 1.0, (2, 2, 0, 0), 16),     # periodic axis with 3 coarse cells
+    (64, 96, 1.0, (0, 0, 2, 2), 32),     # periodic axis with 3 coarse cells
+    (96, 48, 1.0, (0, 0, 2, 2), 0),      # autotuned: no m leaves 4 coarse cells on the periodic axis
     (0, 64, 1.0, (0, 0, 0, 0), 16),      # empty grid
     (64 * 2048, 64, 1.0, (0, 0, 0, 0), 32),  # coarse grid wider than 1024
     (100, 64, 1.0, (0, 0, 0, 0), 0),     # autotuned coarsening: neither 16 nor 32 divides nx
