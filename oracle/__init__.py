@@ -8,10 +8,10 @@ from .ism_oracle import (OracleISM, OracleACMV, OracleAccommodative, build, lib,
                          coarse_operator, predictor, divergence, correct,
                          proj_step, VEL_NOSLIP, VEL_FREESLIP, VEL_INFLOW,
                          VEL_OUTFLOW, pressure_bc, BC_NEUMANN, BC_DIRICHLET0,
-                         BC_PERIODIC, is_singular, periodic_axes)
+                         BC_PERIODIC, is_singular, periodic_axes, ncoarse)
 
 __all__ = ["OracleISM", "OracleACMV", "OracleAccommodative", "build", "lib", "apply_af", "residual", "rbgs_sweep",
            "restrict", "prolong_add", "prolong_const_add", "coarse_operator",
            "predictor", "divergence", "correct", "proj_step", "VEL_NOSLIP",
            "VEL_FREESLIP", "VEL_INFLOW", "VEL_OUTFLOW", "pressure_bc",
-           "BC_NEUMANN", "BC_DIRICHLET0", "BC_PERIODIC", "is_singular", "periodic_axes"]
+           "BC_NEUMANN", "BC_DIRICHLET0", "BC_PERIODIC", "is_singular", "periodic_axes", "ncoarse"]

@@ -29,6 +29,11 @@
  *   a Neumann face contributing 0, a Dirichlet-0 face (-p_c - p_c) and a
  *   periodic face the flux to the wrapped neighbour.
  *   The equation solved is A_f p = b.
+ *
+ * Coarse cells (Sec. 3.3): coarse cell I along an axis of n fine cells covers
+ * fine cells [I m, min(n, (I + 1) m)); when n is not a multiple of m the last
+ * coarse cell is narrower (the paper pads the grid and lets the interpolation
+ * rectangles differ in size), nc = ceil(n / m).
  */
 #include <math.h>
 #include <stddef.h>
@@ -127,19 +132,22 @@ void or_rbgs_sweep(int nx, int ny, const int *bc, double *p, const double *b)
     gs_colour(nx, ny, bc, p, b, 1);
 }
 
+static int ncoarse(int n, int m) { return (n + m - 1) / m; }
+static int block_end(int I, int n, int m) { return (I + 1) * m < n ? (I + 1) * m : n; }
+
 /* ------------------------------------------------------------------------ */
 /* Restriction, Sec. 3.2-3.3: the coarse right-hand side is the sum of the    */
-/* fine equations over the m x m block (agglomeration, as in ACM).            */
+/* fine equations over the coarse cell (agglomeration, as in ACM).            */
 /* ------------------------------------------------------------------------ */
 
 void or_restrict(int nx, int ny, int m, const double *r, double *rc)
 {
-    int ncx = nx / m, ncy = ny / m;
+    int ncx = ncoarse(nx, m), ncy = ncoarse(ny, m);
     for (int J = 0; J < ncy; ++J)
         for (int I = 0; I < ncx; ++I) {
             double s = 0.0;
-            for (int j = J * m; j < (J + 1) * m; ++j)
-                for (int i = I * m; i < (I + 1) * m; ++i)
+            for (int j = J * m; j < block_end(J, ny, m); ++j)
+                for (int i = I * m; i < block_end(I, nx, m); ++i)
                     s += AT(r, i, j);
             rc[(size_t)J * ncx + I] = s;
         }
@@ -148,13 +156,33 @@ void or_restrict(int nx, int ny, int m, const double *r, double *rc)
 /* ------------------------------------------------------------------------ */
 /* Bilinear interpolation from coarse centres, Eq. 5.                          */
 /* Q11, Q21, Q12, Q22 are the corner values of the interpolation rectangle    */
-/* (Delta_x = Delta_y = m fine cells), (x, y) the fine-cell centre measured   */
-/* from Q11.  Outside the hull of coarse centres the rule near the boundary is */
-/* a mirror ghost centre at distance m beyond the edge centre (the paper      */
-/* leaves this rule open): even (Q_ghost = Q_edge) at a Neumann face, odd      */
+/* (Delta_x, Delta_y: the distances between neighbouring coarse centres, m    */
+/* fine cells except next to a narrower last coarse cell), (x, y) the         */
+/* fine-cell centre measured from Q11.  Outside the hull of coarse centres    */
+/* the rule near the boundary is a ghost centre mirrored across the wall      */
+/* (distance m beyond the edge centre when the edge cell is m wide; the paper */
+/* leaves this rule open): even (Q_ghost = Q_edge) at a Neumann face, odd     */
 /* (Q_ghost = -Q_edge) at a Dirichlet-0 face; across a periodic face the      */
 /* ghost is the coarse centre at the other end (the periodic extension).      */
 /* ------------------------------------------------------------------------ */
+
+/* fine coordinate of coarse centre I along an axis of n fine cells; I = -1
+   and I = nc give the ghost centres */
+static double centre(int I, int n, int m, int periodic)
+{
+    int nc = ncoarse(n, m);
+    if (I < 0) return periodic ? centre(I + nc, n, m, 0) - n : -centre(0, n, m, 0);
+    if (I >= nc) return periodic ? centre(I - nc, n, m, 0) + n : 2.0 * n - centre(nc - 1, n, m, 0);
+    return 0.5 * (double)(I * m + block_end(I, n, m));
+}
+
+/* the coarse centre at or before fine centre i + 1/2 (possibly a ghost) */
+static int left_centre(int i, int n, int m, int periodic)
+{
+    int I = i / m;
+    if (centre(I, n, m, periodic) > (double)i + 0.5) --I;
+    return I;
+}
 
 static double coarse_or_ghost(int ncx, int ncy, const int *bc, const double *q,
                               int I, int J)
@@ -171,15 +199,16 @@ static double coarse_or_ghost(int ncx, int ncy, const int *bc, const double *q,
 static double bilinear_at(int nx, int ny, int m, const int *bc, const double *q,
                           int i, int j)
 {
-    int ncx = nx / m, ncy = ny / m;
+    int ncx = ncoarse(nx, m), ncy = ncoarse(ny, m);
+    int px = bc[F_W] == BC_PER, py = bc[F_S] == BC_PER;
     /* lower-left corner of the interpolation rectangle: the coarse centre at
-       or left of / below the fine centre; coarse centre I sits at fine
-       coordinate (I + 1/2) m. */
-    int I0 = (int)floor(((double)i + 0.5) / m - 0.5);
-    int J0 = (int)floor(((double)j + 0.5) / m - 0.5);
-    double Dx = (double)m, Dy = (double)m;
-    double x = ((double)i + 0.5) - ((double)I0 + 0.5) * m;
-    double y = ((double)j + 0.5) - ((double)J0 + 0.5) * m;
+       or left of / below the fine centre */
+    int I0 = left_centre(i, nx, m, px);
+    int J0 = left_centre(j, ny, m, py);
+    double cx0 = centre(I0, nx, m, px), cy0 = centre(J0, ny, m, py);
+    double Dx = centre(I0 + 1, nx, m, px) - cx0, Dy = centre(J0 + 1, ny, m, py) - cy0;
+    double x = ((double)i + 0.5) - cx0;
+    double y = ((double)j + 0.5) - cy0;
     double Q11 = coarse_or_ghost(ncx, ncy, bc, q, I0, J0);
     double Q21 = coarse_or_ghost(ncx, ncy, bc, q, I0 + 1, J0);
     double Q12 = coarse_or_ghost(ncx, ncy, bc, q, I0, J0 + 1);
@@ -199,7 +228,7 @@ void or_prolong_add(int nx, int ny, int m, const int *bc, const double *q, doubl
 /* p += q[block] (piecewise-constant correction of ACM, Sec. 3.2) */
 void or_prolong_const_add(int nx, int ny, int m, const double *q, double *p)
 {
-    int ncx = nx / m;
+    int ncx = ncoarse(nx, m);
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
             AT(p, i, j) += q[(size_t)(j / m) * ncx + (i / m)];
@@ -219,7 +248,7 @@ void or_prolong_const_add(int nx, int ny, int m, const double *q, double *p)
 static double face_sums(int nx, int ny, int m, const int *bc, const double *p,
                         int KI, int KJ)
 {
-    int x0 = KI * m, x1 = x0 + m, y0 = KJ * m, y1 = y0 + m;
+    int x0 = KI * m, x1 = block_end(KI, nx, m), y0 = KJ * m, y1 = block_end(KJ, ny, m);
     double s = 0.0;
     for (int j = y0; j < y1; ++j) {                     /* west face */
         if (x0 > 0) s += AT(p, x0 - 1, j) - AT(p, x0, j);
@@ -246,7 +275,7 @@ static double face_sums(int nx, int ny, int m, const int *bc, const double *p,
 
 int or_coarse_operator(int nx, int ny, int m, const int *bc, int kind, double *Ac)
 {
-    int ncx = nx / m, ncy = ny / m, nc = ncx * ncy;
+    int ncx = ncoarse(nx, m), ncy = ncoarse(ny, m), nc = ncx * ncy;
     double *p = (double *)calloc((size_t)nx * ny, sizeof(double));
     double *q = (double *)calloc((size_t)nc, sizeof(double));
     if (!p || !q) { free(p); free(q); return -1; }
@@ -263,16 +292,16 @@ int or_coarse_operator(int nx, int ny, int m, const int *bc, int kind, double *A
             int bj0 = JJ - 1 < 0 ? 0 : JJ - 1, bj1 = JJ + 1 >= ncy ? ncy - 1 : JJ + 1;
             if (bc[F_W] == BC_PER) { bi0 = 0; bi1 = ncx - 1; }
             if (bc[F_S] == BC_PER) { bj0 = 0; bj1 = ncy - 1; }
-            for (int j = bj0 * m; j < (bj1 + 1) * m; ++j)
-                for (int i = bi0 * m; i < (bi1 + 1) * m; ++i)
+            for (int j = bj0 * m; j < block_end(bj1, ny, m); ++j)
+                for (int i = bi0 * m; i < block_end(bi1, nx, m); ++i)
                     AT(p, i, j) = (kind == 0) ? bilinear_at(nx, ny, m, bc, q, i, j)
                                               : q[(size_t)(j / m) * ncx + (i / m)];
             for (int KJ = bj0; KJ <= bj1; ++KJ)
                 for (int KI = bi0; KI <= bi1; ++KI)
                     Ac[(size_t)(KJ * ncx + KI) * nc + col] =
                         face_sums(nx, ny, m, bc, p, KI, KJ);
-            for (int j = bj0 * m; j < (bj1 + 1) * m; ++j)
-                for (int i = bi0 * m; i < (bi1 + 1) * m; ++i)
+            for (int j = bj0 * m; j < block_end(bj1, ny, m); ++j)
+                for (int i = bi0 * m; i < block_end(bi1, nx, m); ++i)
                     AT(p, i, j) = 0.0;
             q[col] = 0.0;
         }
@@ -406,12 +435,12 @@ void or_rbgs_sweep_f32(int nx, int ny, const int *bc, float *p, const float *b)
 
 void or_restrict_f32(int nx, int ny, int m, const float *r, double *rc)
 {
-    int ncx = nx / m, ncy = ny / m;
+    int ncx = ncoarse(nx, m), ncy = ncoarse(ny, m);
     for (int J = 0; J < ncy; ++J)
         for (int I = 0; I < ncx; ++I) {
             double s = 0.0;
-            for (int j = J * m; j < (J + 1) * m; ++j)
-                for (int i = I * m; i < (I + 1) * m; ++i)
+            for (int j = J * m; j < block_end(J, ny, m); ++j)
+                for (int i = I * m; i < block_end(I, nx, m); ++i)
                     s += (double)AT(r, i, j);
             rc[(size_t)J * ncx + I] = s;
         }

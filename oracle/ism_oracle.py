@@ -102,6 +102,12 @@ def _bc(bc):
     return a
 
 
+def ncoarse(n, m):
+    """Coarse cells along an axis of n fine cells: ceil(n / m), the last one
+    narrower when m does not divide n."""
+    return -(-n // m)
+
+
 def is_singular(bc):
     """A_f is singular (null space: constants) iff no face is Dirichlet."""
     return not np.any(_bc(bc) == BC_DIRICHLET0)
@@ -144,7 +150,7 @@ def rbgs_sweep(p, b, bc):
 
 def restrict(r, m):
     ny, nx = r.shape
-    rc = np.empty((ny // m, nx // m), dtype=np.float64)
+    rc = np.empty((ncoarse(ny, m), ncoarse(nx, m)), dtype=np.float64)
     lib().or_restrict(nx, ny, m, _c64(r), rc)
     return rc
 
@@ -167,8 +173,10 @@ def coarse_operator(nx, ny, m, bc, kind="ism"):
     constant interpolant, Sec. 3.2) or 'gmg' (the five-point operator
     re-discretised on the coarse grid, the comparator of Sec. 3.3 / Table 5:
     the fine operator's rule applied to coarse cells)."""
-    nc = (nx // m) * (ny // m)
+    nc = ncoarse(nx, m) * ncoarse(ny, m)
     if kind == "gmg":
+        if nx % m or ny % m:
+            raise ValueError("the re-discretised coarse operator needs uniform coarse cells")
         ncx, ncy = nx // m, ny // m
         eye = np.eye(nc)
         Ac = np.empty((nc, nc), dtype=np.float64)
@@ -197,8 +205,11 @@ class OracleISM:
     """
 
     def __init__(self, nx, ny, m, bc=(0, 0, 0, 0), kind="ism", nu=8):
-        if nx % m or ny % m:
-            raise ValueError("grid must be a multiple of the coarsening factor")
+        if kind == "gmg" and (nx % m or ny % m):
+            raise ValueError("the GMG comparator needs a grid that is a multiple of the coarsening factor")
+        bca = _bc(bc)
+        if (bca[0] == BC_PERIODIC and nx % m) or (bca[2] == BC_PERIODIC and ny % m):
+            raise ValueError("a periodic axis must be a multiple of the coarsening factor")
         self.nx, self.ny, self.m = nx, ny, m
         self.bc = _bc(bc)
         self.kind = kind
@@ -270,7 +281,7 @@ class OracleISM:
         nx, ny, m = self.nx, self.ny, self.m
         rin = np.empty_like(e)
         L.or_residual_f32(nx, ny, self.bc, e, r32, rin)
-        rc = np.empty((ny // m, nx // m), dtype=np.float64)
+        rc = np.empty((ncoarse(ny, m), ncoarse(nx, m)), dtype=np.float64)
         L.or_restrict_f32(nx, ny, m, rin, rc)
         ec = self.coarse_solve(rc)
         L.or_prolong_add_f32(nx, ny, m, self.bc, np.ascontiguousarray(ec), e)
