@@ -352,7 +352,8 @@ ism_status ism_launch_coarse_tc_batch(cudaStream_t s, const void *table, int n, 
     return cudaGetLastError() == cudaSuccess ? ISM_OK : ISM_ERR_CUDA;
 }
 
-ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, const std::vector<double> &Qy,
+ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, const std::vector<double> &QxT,
+                                const std::vector<double> &Qy, const std::vector<double> &QyT,
                                 const std::vector<double> &Minv)
 {
     const int ncx = ctx->ncx, ncy = ctx->ncy;
@@ -365,13 +366,13 @@ ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, con
     };
     for (int l = 0; l < ncy; ++l)
         for (int k = 0; k < ncy; ++k) {
-            put_h(L.cA1, l, k, L.Ky, Qy[(size_t)k * ncy + l]);   // Qy^T[l][k]
+            put_h(L.cA1, l, k, L.Ky, QyT[(size_t)l * ncy + k]);  // QyT[l][k]
             put_h(L.cA3, l, k, L.Ky, Qy[(size_t)l * ncy + k]);   // Qy[l][k]
         }
     for (int n = 0; n < ncx; ++n)
         for (int k = 0; k < ncx; ++k) {
             put_h(L.cB2, n, k, L.Kx, Qx[(size_t)k * ncx + n]);   // B[n][k] = Qx[k][n]: product T1 Qx
-            put_h(L.cB4, n, k, L.Kx, Qx[(size_t)n * ncx + k]);   // B[n][k] = Qx^T[k][n]: product T3 Qx^T
+            put_h(L.cB4, n, k, L.Kx, QxT[(size_t)k * ncx + n]);  // B[n][k] = QxT[k][n]: product T3 QxT
         }
     for (size_t i = 0; i < (size_t)ncx * ncy; ++i) {
         const float f = (float)Minv[i];

@@ -197,30 +197,101 @@ static void s_eigen(int n, int lo, int hi, std::vector<double> &Q, std::vector<d
     }
 }
 
+// The coarse solve e_c = A_c^+ r_c in the four-product form
+// E = Qy [(QyT R Qx) . Minv] QxT (R, E: ncy x ncx row-major).
 struct EigenHost {
-    std::vector<double> Qx, Qy, lx, ly;
+    std::vector<double> Qx, QxT, Qy, QyT, Minv;
 };
 
-// Eigenvalues of A_c on (Qy x Qx): ISM A_c = 1/4 (S_y x S_x) - 4 I
-// (closed form of summing the Eq. 6-7 face fluxes), ACM A_c = m (T_y (+) T_x)
-// with T = S - 4 I, the five-point coarse operator of the summed equations.
-static ism_status upload_coarse(ism_ctx *ctx, const EigenHost &E)
+static void transpose(const std::vector<double> &A, int n, std::vector<double> &At)
 {
+    At.resize((size_t)n * n);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) At[(size_t)k * n + i] = A[(size_t)i * n + k];
+}
+
+// Uniform coarse cells: eigenvalues of A_c on the orthonormal (Qy x Qx):
+// ISM A_c = 1/4 (S_y x S_x) - 4 I (closed form of summing the Eq. 6-7 face
+// fluxes), ACM A_c = m (T_y (+) T_x) with T = S - 4 I (the five-point coarse
+// operator of the summed equations), GMG the same without the factor m.
+static EigenHost eigen_uniform(const ism_ctx *ctx, int kind)
+{
+    EigenHost E;
+    std::vector<double> lx, ly;
+    s_eigen(ctx->ncx, ctx->bc[0], ctx->bc[1], E.Qx, lx);
+    s_eigen(ctx->ncy, ctx->bc[2], ctx->bc[3], E.Qy, ly);
     const int ncx = ctx->ncx, ncy = ctx->ncy;
-    std::vector<double> QxT((size_t)ncx * ncx), QyT((size_t)ncy * ncy), Minv((size_t)ncx * ncy);
-    for (int i = 0; i < ncx; ++i)
-        for (int k = 0; k < ncx; ++k) QxT[(size_t)k * ncx + i] = E.Qx[(size_t)i * ncx + k];
-    for (int i = 0; i < ncy; ++i)
-        for (int k = 0; k < ncy; ++k) QyT[(size_t)k * ncy + i] = E.Qy[(size_t)i * ncy + k];
+    transpose(E.Qx, ncx, E.QxT);
+    transpose(E.Qy, ncy, E.QyT);
+    E.Minv.resize((size_t)ncx * ncy);
     for (int l = 0; l < ncy; ++l)
         for (int k = 0; k < ncx; ++k) {
-            // eigenvalues of A_c in the separable basis: ISM 1/4 S_y x S_x - 4 I;
-            // five-point operators (S_x - 4 I) + (S_y - 4 I), times m for ACM
-            double mu = (ctx->opt.kind == ISM_COARSE_ISM) ? 0.25 * E.lx[k] * E.ly[l] - 4.0
-                                                          : (E.lx[k] - 4.0) + (E.ly[l] - 4.0);
-            if (ctx->opt.kind == ISM_COARSE_ACM || ctx->opt.kind == ISM_COARSE_ACMV) mu *= ctx->m;
-            Minv[(size_t)l * ncx + k] = fabs(mu) < 1e-10 ? 0.0 : 1.0 / mu;
+            double mu = (kind == ISM_COARSE_ISM) ? 0.25 * lx[k] * ly[l] - 4.0 : (lx[k] - 4.0) + (ly[l] - 4.0);
+            if (kind == ISM_COARSE_ACM || kind == ISM_COARSE_ACMV) mu *= ctx->m;
+            E.Minv[(size_t)l * ncx + k] = fabs(mu) < 1e-10 ? 0.0 : 1.0 / mu;
         }
+    return E;
+}
+
+// 1-D factor T V = W V diag(lam), L = (W V)^-1 of one axis (see ism_pencil.cu).
+// A periodic axis (a multiple of m) in closed form: V = Q (Fourier basis of S),
+// W = m (S + 4 I) / 8 and T = (S - 4 I) / m for ISM, W = m I and T = S - 4 I
+// for ACM, so lam = t / w and L = diag(1 / w) Q^T.
+static bool axis_factor(const ism_ctx *ctx, int n, int lo, int hi, int kind, IsmAxisFactor &F)
+{
+    if (lo != ISM_BC_PERIODIC) return ism_axis_factor(n, ctx->m, lo, hi, kind, F);
+    const int nc = n / ctx->m;
+    const double m = ctx->m;
+    std::vector<double> s;
+    s_eigen(nc, lo, hi, F.V, s);
+    F.lam.resize(nc);
+    F.L.resize((size_t)nc * nc);
+    for (int k = 0; k < nc; ++k) {
+        const double w = (kind == ISM_COARSE_ISM) ? m * (s[k] + 4.0) / 8.0 : m;
+        const double t = (kind == ISM_COARSE_ISM) ? (s[k] - 4.0) / m : s[k] - 4.0;
+        F.lam[k] = t / w;
+        for (int i = 0; i < nc; ++i) F.L[(size_t)k * nc + i] = F.V[(size_t)i * nc + k] / w;
+    }
+    return true;
+}
+
+// A narrower last coarse cell along an axis: A_c = W_y x T_x + T_y x W_x, so
+// A_c^+ = (V_y x V_x) diag(1 / (lam_y + lam_x)) (L_y x L_x) with the null mode
+// (every face Neumann or periodic: lam_y + lam_x = 0 for the constants) dropped.
+static bool eigen_general(const ism_ctx *ctx, int kind, EigenHost &E)
+{
+    IsmAxisFactor fx, fy;
+    if (!axis_factor(ctx, ctx->nx, ctx->bc[0], ctx->bc[1], kind, fx) ||
+        !axis_factor(ctx, ctx->ny, ctx->bc[2], ctx->bc[3], kind, fy))
+        return false;
+    const int ncx = ctx->ncx, ncy = ctx->ncy;
+    transpose(fx.L, ncx, E.Qx);   // R Qx = R L_x^T
+    transpose(fx.V, ncx, E.QxT);
+    E.Qy = fy.V;
+    E.QyT = fy.L;
+    double mx = 0.0;
+    for (int l = 0; l < ncy; ++l)
+        for (int k = 0; k < ncx; ++k) mx = std::max(mx, fabs(fy.lam[l] + fx.lam[k]));
+    E.Minv.resize((size_t)ncx * ncy);
+    for (int l = 0; l < ncy; ++l)
+        for (int k = 0; k < ncx; ++k) {
+            const double mu = fy.lam[l] + fx.lam[k];
+            E.Minv[(size_t)l * ncx + k] = fabs(mu) <= 1e-12 * mx ? 0.0 : 1.0 / mu;
+        }
+    return true;
+}
+
+static ism_status build_eigen(const ism_ctx *ctx, int kind, EigenHost &E)
+{
+    if (!ctx->ragged) {
+        E = eigen_uniform(ctx, kind);
+        return ISM_OK;
+    }
+    return eigen_general(ctx, kind, E) ? ISM_OK : ISM_ERR_ARG;
+}
+
+static ism_status upload_coarse(ism_ctx *ctx, const EigenHost &E)
+{
     auto up = [&](double *d64, float *d32, const std::vector<double> &h) -> ism_status {
         std::vector<float> f(h.size());
         for (size_t i = 0; i < h.size(); ++i) f[i] = (float)h[i];
@@ -230,11 +301,11 @@ static ism_status upload_coarse(ism_ctx *ctx, const EigenHost &E)
     };
     ism_status s;
     if ((s = up(ctx->Qx64, ctx->Qx32, E.Qx)) != ISM_OK) return s;
-    if ((s = up(ctx->QxT64, ctx->QxT32, QxT)) != ISM_OK) return s;
+    if ((s = up(ctx->QxT64, ctx->QxT32, E.QxT)) != ISM_OK) return s;
     if ((s = up(ctx->Qy64, ctx->Qy32, E.Qy)) != ISM_OK) return s;
-    if ((s = up(ctx->QyT64, ctx->QyT32, QyT)) != ISM_OK) return s;
-    if ((s = up(ctx->Minv64, ctx->Minv32, Minv)) != ISM_OK) return s;
-    return ism_coarse_tc_upload(ctx, E.Qx, E.Qy, Minv);
+    if ((s = up(ctx->QyT64, ctx->QyT32, E.QyT)) != ISM_OK) return s;
+    if ((s = up(ctx->Minv64, ctx->Minv32, E.Minv)) != ISM_OK) return s;
+    return ism_coarse_tc_upload(ctx, E.Qx, E.QxT, E.Qy, E.QyT, E.Minv);
 }
 
 static void free_graphs(ism_ctx *ctx)
@@ -282,27 +353,26 @@ extern "C" void ism_destroy(ism_ctx *ctx)
 
 static ism_status make_plans(ism_ctx *ctx);
 
-static EigenHost build_eigen(const ism_ctx *ctx)
-{
-    EigenHost E;
-    s_eigen(ctx->ncx, ctx->bc[0], ctx->bc[1], E.Qx, E.lx);
-    s_eigen(ctx->ncy, ctx->bc[2], ctx->bc[3], E.Qy, E.ly);
-    return E;
-}
 
 ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarsen, ism_precision prec,
                            void *stream, ism_ctx **out)
 {
     if (!out || !bc) return ISM_ERR_ARG;
     if (coarsen != 8 && coarsen != 16 && coarsen != 32) return ISM_ERR_ARG;
-    if (nx <= 0 || ny <= 0 || nx % coarsen || ny % coarsen) return ISM_ERR_ARG;
+    if (nx < coarsen || ny < coarsen) return ISM_ERR_ARG;
     if ((long long)nx * ny > (1LL << 31) || nx > (1 << 20) || ny > (1 << 20)) return ISM_ERR_ARG;
-    if (nx / coarsen > 1024 || ny / coarsen > 1024) return ISM_ERR_ARG;
+    const int ncx = (nx + coarsen - 1) / coarsen, ncy = (ny + coarsen - 1) / coarsen;
+    if (ncx > 1024 || ncy > 1024) return ISM_ERR_ARG;
+    const bool ragged = nx % coarsen || ny % coarsen;
+    // a narrower last coarse cell needs a full one before it; the single-precision
+    // pass moves aligned groups of 4 cells along x
+    if ((nx % coarsen && ncx < 2) || (ny % coarsen && ncy < 2)) return ISM_ERR_ARG;
+    if (prec == ISM_MIXED && nx % 4) return ISM_ERR_ARG;
     if (!(h > 0.0) || !isfinite(h)) return ISM_ERR_ARG;
     const int mask = ism_bc_mask(bc);
     if (mask < 0) return ISM_ERR_ARG;
-    if ((mask & ISM_PER_X) && nx / coarsen < 4) return ISM_ERR_ARG;
-    if ((mask & ISM_PER_Y) && ny / coarsen < 4) return ISM_ERR_ARG;
+    if ((mask & ISM_PER_X) && (nx % coarsen || ncx < 4)) return ISM_ERR_ARG;
+    if ((mask & ISM_PER_Y) && (ny % coarsen || ncy < 4)) return ISM_ERR_ARG;
     if (prec != ISM_FP64 && prec != ISM_MIXED) return ISM_ERR_ARG;
 
     ism_ctx *ctx = (ism_ctx *)calloc(1, sizeof(ism_ctx));
@@ -310,8 +380,9 @@ ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarse
     ctx->nx = nx;
     ctx->ny = ny;
     ctx->m = coarsen;
-    ctx->ncx = nx / coarsen;
-    ctx->ncy = ny / coarsen;
+    ctx->ncx = ncx;
+    ctx->ncy = ncy;
+    ctx->ragged = ragged;
     ctx->n = (long long)nx * ny;
     ctx->h = h;
     ctx->bcmask = mask;
@@ -383,7 +454,9 @@ ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarse
         ism_destroy(ctx);
         return ISM_ERR_CUDA;
     }
-    ism_status s = upload_coarse(ctx, build_eigen(ctx));
+    EigenHost E;
+    ism_status s = build_eigen(ctx, ctx->opt.kind, E);
+    if (s == ISM_OK) s = upload_coarse(ctx, E);
     if (s != ISM_OK) {
         ism_destroy(ctx);
         return s;
@@ -435,7 +508,12 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
         return ISM_ERR_ARG;
     if (!(o->accom_tol_c > 0.0) || o->accom_max_coarse < 1) return ISM_ERR_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
+    // a narrower last coarse cell: the ISM and ACM operators, correction-scheme cycle
+    if (ctx->ragged && (o->kind == ISM_COARSE_GMG || o->kind == ISM_COARSE_ACMV || o->cycle == 1))
+        return ISM_ERR_ARG;
     const int kind_changed = o->kind != ctx->opt.kind;
+    EigenHost E;
+    if (kind_changed && build_eigen(ctx, o->kind, E) != ISM_OK) return ISM_ERR_ARG;
     cudaStreamSynchronize(ctx->ws);
     if (o->kind == ISM_COARSE_ACMV && !ctx->lvl_r[1]) {
         // levels 1 .. L-1 of the V-cycle (level l: (nx >> l) x (ny >> l))
@@ -450,7 +528,7 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     }
     ctx->opt = *o;
     free_graphs(ctx);
-    if (kind_changed) return upload_coarse(ctx, build_eigen(ctx));
+    if (kind_changed) return upload_coarse(ctx, E);
     return ISM_OK;
 }
 

@@ -49,6 +49,7 @@ struct ism_ctx {
     int bc[4];
     int bcmask;                // ism_bc_mask(bc)
     int singular;              // no Dirichlet-0 face (A_f 1 = 0)
+    int ragged;                // m does not divide nx or ny: the last coarse cell is narrower
     int prec;
     ism_options opt;
     cudaStream_t user_stream;  // ordering stream given by the caller
@@ -143,6 +144,17 @@ inline int ism_bc_mask(const int bc[4])
     return mask;
 }
 
+// 1-D factor of the coarse operator along one axis (ism_pencil.cu):
+// T V = W V diag(lam), L = (W V)^-1, V and L row-major n x n, lam ascending.
+struct IsmAxisFactor {
+    std::vector<double> V, L, lam;
+};
+// The factor of an axis of n fine cells (the last coarse cell narrower when
+// m does not divide n), computed numerically; lo, hi: ism_bc of its ends
+// (not periodic); kind: ism_coarse_kind (ISM or ACM).  false when a
+// numerical check fails.
+bool ism_axis_factor(int n, int m, int lo, int hi, int kind, IsmAxisFactor &F);
+
 ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarsen, ism_precision prec,
                            void *stream, ism_ctx **out);
 
@@ -167,8 +179,10 @@ ism_status ism_proj_buffers(ism_ctx *ctx);
 // cell; rcpart (or NULL) is cleared afterwards.
 bool ism_coarse_tc_supported(const ism_ctx *ctx);
 void ism_coarse_tc_prepare();   // kernel attributes (called by ism_setup, outside any capture)
-// Lay out the constant operands (eigenbases, 1/mu) as TF32 tiles on the device.
-ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, const std::vector<double> &Qy,
+// Lay out the constant operands of E = Qy [(QyT R Qx) . Minv] QxT as TF32
+// tiles on the device.
+ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, const std::vector<double> &QxT,
+                                const std::vector<double> &Qy, const std::vector<double> &QyT,
                                 const std::vector<double> &Minv);
 ism_status ism_launch_coarse_tc(ism_ctx *ctx, const float *rc, bool from_parts, float *ec, float *rcpart,
                                 const int *skip);

@@ -274,17 +274,42 @@ __device__ __forceinline__ T coarse_ghost(const T *__restrict__ q, int I, int J,
     return neg ? -v : v;
 }
 
+// Interpolation coordinate of fine cell x along an axis of n fine cells with
+// coarse cells of m = 2^lm, nc of them, the last one w = n - (nc-1) m wide
+// (w = m when m divides n): I0 is the coarse centre at or before the fine
+// centre x + 1/2 (-1: the ghost before the first one), t the weight of
+// I0 + 1.  Centre I sits at (I + 1/2) m except the last, at (nc-1) m + w/2;
+// the ghost beyond it is mirrored across the wall (distance w).  Along a
+// periodic axis (w = m) x may lie outside [0, n) and I0 runs over the
+// periodic extension.
 template <typename T>
-__device__ __forceinline__ T prolong_value(const T *__restrict__ q, int x, int y, int m,
+__device__ __forceinline__ void interp_coord(int x, int n, int m, int lm, int nc, int &I0, T &t)
+{
+    const int hm = m >> 1;
+    const int K = (nc - 1) << lm;          // first fine cell of the last coarse cell
+    const int w = n - K;
+    I0 = ((x - hm + m) >> lm) - 1;         // floor((x + 1/2)/m - 1/2)
+    if (w == m || x < K - hm) {
+        t = ((T)(x - I0 * m - hm) + (T)0.5) * ((T)1 / (T)m);   // m is a power of two: exact
+    } else if (2 * x + 1 < 2 * K + w) {    // between centres nc-2 and nc-1, (m + w)/2 apart
+        I0 = nc - 2;
+        t = (T)(2 * (x - K + hm) + 1) / (T)(m + w);
+    } else {                               // between the last centre and its ghost, w apart
+        I0 = nc - 1;
+        t = (T)(2 * (x - K) + 1 - w) / (T)(2 * w);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T prolong_value(const T *__restrict__ q, int x, int y, int nx, int ny, int m,
                                            int ncx, int ncy, int bcmask, int kind)
 {
     if (kind == ISM_COARSE_ACM) return q[(size_t)(y / m) * ncx + (x / m)];
-    const int hm = m >> 1;
-    const int I0 = (x - hm + m) / m - 1;   // floor((x + 1/2)/m - 1/2), x >= 0
-    const int J0 = (y - hm + m) / m - 1;
-    const T invm = (T)1 / (T)m;            // m is a power of two: exact
-    const T tx = ((T)(x - I0 * m - hm) + (T)0.5) * invm;
-    const T ty = ((T)(y - J0 * m - hm) + (T)0.5) * invm;
+    const int lm = __ffs(m) - 1;
+    int I0, J0;
+    T tx, ty;
+    interp_coord<T>(x, nx, m, lm, ncx, I0, tx);
+    interp_coord<T>(y, ny, m, lm, ncy, J0, ty);
     const T q11 = coarse_ghost(q, I0, J0, ncx, ncy, bcmask);
     const T q21 = coarse_ghost(q, I0 + 1, J0, ncx, ncy, bcmask);
     const T q12 = coarse_ghost(q, I0, J0 + 1, ncx, ncy, bcmask);
@@ -378,6 +403,7 @@ __global__ void k_resid(const T *__restrict__ p, const T *__restrict__ b, T *__r
     T acc = 0, r2 = 0, ps = 0, p2 = 0;
     for (int k = threadIdx.x; k < mm; k += blockDim.x) {
         const int i = I * m + (k % m), j = J * m + (k / m);
+        if (i >= nx || j >= ny) continue;      // narrower last coarse cell
         const size_t idx = (size_t)j * nx + i;
         const T pc = p[idx];
         const T s = nb_sum<T>([&](long long q) -> T { return p[q]; }, (long long)idx, i, j, nx, ny, bcmask);
@@ -416,7 +442,7 @@ __global__ void k_prolong(T *__restrict__ p, const T *__restrict__ ec, int nx, i
     const size_t idx = (size_t)j * nx + i;
     T v = p[idx];
     if (use_mean) v -= (T)st->mean;
-    p[idx] = v + prolong_value<T>(ec, i, j, m, ncx, ncy, bcmask, kind);
+    p[idx] = v + prolong_value<T>(ec, i, j, nx, ny, m, ncx, ncy, bcmask, kind);
 }
 
 // ----------------------------------------------------------------- coarse solve

@@ -65,8 +65,8 @@ extern "C" ism_status ism_residual_restrict_noalloc(int nx, int ny, int coarsen,
 {
     if (!bc || !p || !b || !rc || !norms) return ISM_ERR_ARG;
     if (coarsen != 8 && coarsen != 16 && coarsen != 32) return ISM_ERR_ARG;
-    if (nx <= 0 || ny <= 0 || nx % coarsen || ny % coarsen) return ISM_ERR_ARG;
-    const int ncx = nx / coarsen, ncy = ny / coarsen;
+    if (nx <= 0 || ny <= 0) return ISM_ERR_ARG;
+    const int ncx = (nx + coarsen - 1) / coarsen, ncy = (ny + coarsen - 1) / coarsen;   // last cell may be narrower
     if ((long long)ncx * ncy > ISM_NOALLOC_MAX_COARSE) return ISM_ERR_ARG;
     const int bcmask = ism_bc_mask(bc);
     if (bcmask < 0) return ISM_ERR_ARG;

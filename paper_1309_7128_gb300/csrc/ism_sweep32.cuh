@@ -32,8 +32,10 @@
 //
 // Options fused into the pass:
 //  PROLONG: add P e_c - mean while loading.  P e_c is evaluated in the
-//           separable form of Eq. 5: the CTA first interpolates the coarse
-//           rows it needs along x into shared memory,
+//           separable form of Eq. 5 (interpolation coordinates from
+//           interp_coord, which also covers a narrower last coarse cell):
+//           the CTA first interpolates the coarse rows it needs along x into
+//           shared memory,
 //           G[J][x] = (1 - t_x) e_c[J][I0] + t_x e_c[J][I0+1] (mirror ghosts
 //           at the ends), then p += (1 - t_y) G[J0][x] + t_y G[J0+1][x].
 //  RESID:   residual r = b - A_f p of the valid tile, its partial m x m block
@@ -231,7 +233,6 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
     //    and b, and the prolongation is added to the registers afterwards
     float P[SRR + 2][SNC];
     const int m = a.m, lm = a.lm, hm = m >> 1;
-    const float invm = 1.0f / (float)m;
     const bool acm = a.kind == ISM_COARSE_ACM;
     // rows of e_c used by region rows y0-1 .. y0+SRH (clamped to the coarse grid)
     int Jg0 = 0, nrow = 0, Ic0 = 0, ncol = 0;
@@ -293,8 +294,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
                     if (acm) {
                         g[q] = er[x >> lm];
                     } else {
-                        const int I0 = ((x - hm + m) >> lm) - 1;
-                        const float tx = ((float)(x - I0 * m - hm) + 0.5f) * invm;
+                        int I0;
+                        float tx;
+                        interp_coord<float>(x, nx, m, lm, ncx, I0, tx);
                         float qa, qb;
                         if (per_x) {
                             qa = er[I0];
@@ -324,8 +326,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
                     wa = 1.0f;
                     wb = 0.0f;
                 } else {
-                    const int J0 = ((y - hm + m) >> lm) - 1;
-                    const float ty = ((float)(y - J0 * m - hm) + 0.5f) * invm;
+                    int J0;
+                    float ty;
+                    interp_coord<float>(y, ny, m, lm, a.ncy, J0, ty);
                     int Ja = J0, Jb = J0 + 1;
                     float sa = 1.f, sb = 1.f;
                     if (!per_y && Ja < 0) { Ja = 0; if (a.bcmask & 4) sa = -1.f; }

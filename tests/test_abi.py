@@ -30,7 +30,8 @@ def test_status_strings(L):
 
 
 @pytest.mark.parametrize("args", [
-    (100, 64, 1.0, (0, 0, 0, 0), 16),    # nx not a multiple of m
+    (12, 64, 1.0, (0, 0, 0, 0), 16),     # nx smaller than m
+    (70, 64, 1.0, (2, 2, 0, 0), 16),     # periodic axis not a multiple of m
     (64, 64, 1.0, (0, 0, 0, 0), 12),     # m not in {8, 16, 32}
     (64, 64, 0.0, (0, 0, 0, 0), 16),     # h <= 0
     (64, 64, 1.0, (0, 3, 0, 0), 16),     # bad face type
@@ -49,6 +50,13 @@ def test_setup_rejects_bad_arguments(L, args):
     out = C.c_void_p(0)
     bca = (C.c_int * 4)(*bc)
     assert L.ism_setup(nx, ny, h, bca, m, 0, None, C.byref(out)) == ism.ISM_ERR_ARG
+    assert out.value is None
+
+
+def test_mixed_setup_needs_rows_of_whole_float4_groups(L):
+    out = C.c_void_p(0)
+    bca = (C.c_int * 4)(0, 0, 0, 0)
+    assert L.ism_setup(102, 64, 1.0, bca, 16, 1, None, C.byref(out)) == ism.ISM_ERR_ARG
     assert out.value is None
 
 
