@@ -120,11 +120,18 @@ const char *ism_status_str(ism_status s);
 /* ism_setup -- validate the problem and build the coarse level.
  * Sec. 3.3-3.4 and Sec. 4 (problem statement: grid, boundary conditions,
  * tile/coarsening size).
- *   nx, ny   fine cells; both multiples of `coarsen`, nx*ny <= 2^31.
+ *   nx, ny   fine cells, each >= `coarsen`, nx*ny <= 2^31.  When coarsen
+ *            does not divide nx (ny), the last coarse column (row) is
+ *            narrower (Sec. 3.3: padding, interpolation rectangles of
+ *            different sizes; the coarse centre sits at the middle of its
+ *            cell); such grids take the ISM and ACM coarse operators and the
+ *            correction-scheme cycle (ism_set_options rejects GMG, the deep
+ *            ACM V-cycle and cycle 1 there) and ISM_MIXED needs nx % 4 == 0.
  *   h        cell size (used by proj_step only; > 0).
  *   bc       host, 4 ints (ism_bc) for the west, east, south, north faces;
  *            ISM_BC_PERIODIC on both faces of an axis or on neither, and
- *            then at least 4 coarse cells along that axis.  A_f is singular
+ *            then that axis a multiple of coarsen with at least 4 coarse
+ *            cells.  A_f is singular
  *            (constants) when no face is Dirichlet-0: the solve then works
  *            on the mean-free subspace.
  *   coarsen  m in {8, 16, 32}: coarse cells are m x m blocks of fine cells;
@@ -136,8 +143,10 @@ const char *ism_status_str(ism_status s);
  *   stream   cudaStream_t to order all work on (NULL = legacy default stream).
  *   out      host; receives the new context.
  * Builds the coarse operator A_c = R A_f P in FP64 on the host (closed form
- * of the face-flux sums of Eq. 6-7), its separable eigenbases, and allocates
- * all workspaces.  Returns ISM_ERR_ARG, ISM_ERR_NOMEM or ISM_ERR_CUDA on
+ * of the face-flux sums of Eq. 6-7), its separable eigenbases (with a
+ * narrower last coarse cell: A_c = W_y x T_x + T_y x W_x and the 1-D pencils
+ * T V = W V diag(lam), computed and checked numerically; ISM_ERR_ARG if a
+ * check fails), and allocates all workspaces.  Returns ISM_ERR_ARG, ISM_ERR_NOMEM or ISM_ERR_CUDA on
  * failure (*out untouched). */
 ism_status ism_setup(int nx, int ny, double h, const int bc[4], int coarsen,
                      ism_precision prec, void *stream, ism_ctx **out);
@@ -198,7 +207,7 @@ ism_status ism_last_counts(const ism_ctx *ctx, int *outer, int *cycles, long lon
 ism_status ism_smooth(ism_ctx *ctx, void *p, const void *b, int sweeps);
 
 /* r_c = R (b - A_f p) (block sums over m x m, Sec. 3.2-3.3); rc: device,
- * (ny/m)*(nx/m) values of T.  norms: host, 2 doubles or NULL:
+ * ceil(ny/m)*ceil(nx/m) values of T.  norms: host, 2 doubles or NULL:
  * ||b - A_f p||_2 and sum(p). */
 ism_status ism_residual_restrict(ism_ctx *ctx, const void *p, const void *b,
                                  void *rc, double *norms);
@@ -213,10 +222,10 @@ ism_status ism_residual_restrict(ism_ctx *ctx, const void *p, const void *b,
  * compiled into the library (held by every GPU that loads it until the
  * process exits).
  *   nx, ny, coarsen, bc  as for ism_setup (bc: host, 4 ints);
- *                        (nx/coarsen)*(ny/coarsen) must be <= 32768, else
+ *                        ceil(nx/coarsen)*ceil(ny/coarsen) must be <= 32768, else
  *                        ISM_ERR_ARG (nothing launched).
  *   p, b                 device, nx*ny doubles (read only).
- *   rc                   device, (ny/m)*(nx/m) doubles: block sums of b - A_f p.
+ *   rc                   device, ceil(ny/m)*ceil(nx/m) doubles: block sums of b - A_f p.
  *   norms                device, 2 doubles: ||b - A_f p||_2 and sum(p).
  *   stream               cudaStream_t (NULL = legacy default stream); the
  *                        call is asynchronous on it.
@@ -230,8 +239,8 @@ ism_status ism_residual_restrict_noalloc(int nx, int ny, int coarsen, const int 
                                          const double *p, const double *b, double *rc,
                                          double *norms, void *stream);
 
-/* e_c = A_c^+ r_c (exact coarse solve on the mean-free subspace when all
- * faces are Neumann); rc, ec: device, (ny/m)*(nx/m) values of T. */
+/* e_c = A_c^+ r_c (exact coarse solve on the mean-free subspace when no
+ * face is Dirichlet-0); rc, ec: device, ceil(ny/m)*ceil(nx/m) values of T. */
 ism_status ism_coarse_solve(ism_ctx *ctx, const void *rc, void *ec);
 
 /* p += P e_c (bilinear, Eq. 5, mirror ghost centres beyond a wall, the
