@@ -110,6 +110,11 @@ typedef struct {
                              number of coarse cells. */
     double accom_tol_c;   /* cycle 1: coarse criterion (absolute maximum norm, default 1e-5) */
     int accom_max_coarse; /* cycle 1: cap on coarse Gauss-Seidel iterations (default 100000) */
+    int stream;           /* single precision: 1 runs the passes that carry neither the correction
+                             nor the residual (the middle passes of a cycle, ism_smooth) through the
+                             streaming pass (one warp per 128-column strip marching down the rows,
+                             the sweeps pipelined as a wavefront) when sweeps_per_pass is 1, 2 or 4;
+                             0 (default): register-tiled passes only.  For grids larger than L2. */
 } ism_options;
 
 typedef struct ism_ctx ism_ctx;

@@ -16,6 +16,7 @@
 
 #include "ism_kernels.cuh"
 #include "ism_sweep32.cuh"
+#include "ism_stream32.cuh"
 
 // ================================================================ control
 
@@ -138,6 +139,7 @@ static void default_options(ism_options *o, int prec)
     o->cycle = 0;
     o->accom_tol_c = 1e-5;
     o->accom_max_coarse = 100000;
+    o->stream = 0;
 }
 
 static const double kPi = 3.14159265358979323846;
@@ -507,6 +509,7 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     if (o->cycle == 1 && (((ctx->bcmask & ISM_PER_X) && (ctx->ncx & 1)) || ((ctx->bcmask & ISM_PER_Y) && (ctx->ncy & 1))))
         return ISM_ERR_ARG;
     if (!(o->accom_tol_c > 0.0) || o->accom_max_coarse < 1) return ISM_ERR_ARG;
+    if (o->stream < 0 || o->stream > 1) return ISM_ERR_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
     // a narrower last coarse cell: the ISM and ACM operators, correction-scheme cycle
     if (ctx->ragged && (o->kind == ISM_COARSE_GMG || o->kind == ISM_COARSE_ACMV || o->cycle == 1))
@@ -676,8 +679,41 @@ static ism_status launch_sweep_pair(ism_ctx *ctx, const SweepArgs &a, const Swee
     return ISM_OK;
 }
 
+// Streaming pass (ism_stream32.cuh): strips of 128 columns, chunks of rows
+// sized so that the tasks fill the resident warps of the GPU once (every
+// warp then runs the same number of steps).
+template <int K>
+static ism_status launch_stream(ism_ctx *ctx, const SweepArgs &a)
+{
+    using S = StreamShape<K>;
+    static int slots = 0;                        // resident warps on the device
+    if (!slots) {
+        int dev = 0, sms = 152, per_sm = 4;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream32<K>, 32 * ST_NW, S::smem) != cudaSuccess ||
+            per_sm < 1)
+            per_sm = 1;
+        cudaGetLastError();
+        slots = sms * per_sm * ST_NW;
+    }
+    const int nstrip = (ctx->nx + S::VW - 1) / S::VW;
+    const int nchunk = std::max(1, slots / nstrip);
+    int chunk_h = std::max(16 * K, (ctx->ny + nchunk - 1) / nchunk);
+    chunk_h += chunk_h & 1;                      // even: every chunk starts on an even row
+    const int ntask = nstrip * ((ctx->ny + chunk_h - 1) / chunk_h);
+    k_stream32<K><<<(ntask + ST_NW - 1) / ST_NW, 32 * ST_NW, S::smem, ctx->ws>>>(a, nstrip, chunk_h, ntask);
+    ctx->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? ISM_OK : ISM_ERR_CUDA;
+}
+
 static ism_status launch_sweep32(ism_ctx *ctx, SweepArgs a, bool prolong, bool resid)
 {
+    if (ctx->opt.stream && !prolong && !resid) {
+        if (a.K == 1) return launch_stream<1>(ctx, a);
+        if (a.K == 2) return launch_stream<2>(ctx, a);
+        if (a.K == 4) return launch_stream<4>(ctx, a);
+    }
     const SweepPlan &P = sweep_plan(ctx, a.K, resid);
     a.H = sweep_halo(a.K, resid);
     a.Hc = sweep_halo_cols(a.K, resid);
