@@ -17,6 +17,7 @@
 #include "ism_kernels.cuh"
 #include "ism_sweep32.cuh"
 #include "ism_stream32.cuh"
+#include "ism_restrict_stream.cuh"
 
 // ================================================================ control
 
@@ -466,6 +467,10 @@ ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarse
     // the fused sweep pass uses 80 KB of dynamic shared memory
     const int smb = (int)sweep_smem_bytes();
     ism_coarse_tc_prepare();
+    cudaFuncSetAttribute(k_restrict_stream<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RestrictShape<float>::smem);
+    cudaFuncSetAttribute(k_restrict_stream<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RestrictShape<double>::smem);
     cudaFuncSetAttribute(k_sweep32<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
     cudaFuncSetAttribute(k_sweep32<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
     cudaFuncSetAttribute(k_sweep32<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
@@ -579,15 +584,51 @@ static ism_status launch_coarse(ism_ctx *ctx, const T *rc, T *ec, T *Tm, const i
     return ISM_OK;
 }
 
+// Residual, restriction and norm partials.  Rows of whole 16-byte groups
+// (nx % 4 == 0): the streaming pass (ism_restrict_stream.cuh), strips of 128
+// columns and chunks of rows (multiples of m) sized to fill the resident
+// warps once; otherwise one CTA per coarse cell.  *nblk: the number of CTAs,
+// i.e. of norm partials.
 template <typename T>
 static ism_status launch_resid(ism_ctx *ctx, const T *p, const T *b, T *rc, const int *skip,
-                               int ctl_mode = -1, unsigned long long cond = 0)
+                               int ctl_mode = -1, unsigned long long cond = 0, int *nblk = nullptr)
 {
+    if (ctx->nx % 4 == 0) {
+        using S = RestrictShape<T>;
+        static int slots = 0;                    // resident warps on the device
+        if (!slots) {
+            int dev = 0, sms = 152, per_sm = 1;
+            if (cudaGetDevice(&dev) == cudaSuccess)
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_restrict_stream<T>, 32 * RR_NW, S::smem) !=
+                    cudaSuccess || per_sm < 1)
+                per_sm = 1;
+            cudaGetLastError();
+            slots = sms * per_sm * RR_NW;
+        }
+        const int m = ctx->m, nstrip = (ctx->nx + SRW - 1) / SRW;
+        const int nchunk = std::max(1, slots / nstrip);
+        int chunk_h = (ctx->ny + nchunk - 1) / nchunk;
+        chunk_h = ((chunk_h + m - 1) / m) * m;   // whole coarse rows
+        const int ntask = nstrip * ((ctx->ny + chunk_h - 1) / chunk_h);
+        const int grid = (ntask + RR_NW - 1) / RR_NW;
+        if (grid <= ctx->max_blocks) {
+            int lm = 0;
+            while ((1 << lm) < m) ++lm;
+            k_restrict_stream<T><<<grid, 32 * RR_NW, S::smem, ctx->ws>>>(
+                p, b, rc, ctx->partials, ctx->nx, ctx->ny, m, lm, ctx->ncx, ctx->bcmask, nstrip, chunk_h, ntask, skip,
+                ctx->st, ctl_mode, cond);
+            ISM_LAUNCH_CHECK(ctx);
+            if (nblk) *nblk = grid;
+            return ISM_OK;
+        }
+    }
     const int th = std::min(256, ctx->m * ctx->m);
     k_resid<T><<<dim3(ctx->ncx, ctx->ncy), th, 0, ctx->ws>>>(p, b, rc, ctx->partials, ctx->nx,
                                                                 ctx->ny, ctx->m, ctx->bcmask, skip,
                                                                 ctx->st, ctl_mode, cond);
     ISM_LAUNCH_CHECK(ctx);
+    if (nblk) *nblk = ctx->ncx * ctx->ncy;
     return ISM_OK;
 }
 
@@ -1207,13 +1248,15 @@ extern "C" ism_status ism_residual_restrict(ism_ctx *ctx, const void *p, const v
 {
     if (!ctx || !p || !b || !rc) return ISM_ERR_ARG;
     TRY(ism_enter(ctx));
-    if (ctx->prec == ISM_FP64) TRY(launch_resid<double>(ctx, (const double *)p, (const double *)b, (double *)rc, nullptr));
-    else TRY(launch_resid<float>(ctx, (const float *)p, (const float *)b, (float *)rc, nullptr));
+    int nb = 0;
+    if (ctx->prec == ISM_FP64)
+        TRY(launch_resid<double>(ctx, (const double *)p, (const double *)b, (double *)rc, nullptr, -1, 0, &nb));
+    else
+        TRY(launch_resid<float>(ctx, (const float *)p, (const float *)b, (float *)rc, nullptr, -1, 0, &nb));
     if (norms) {
-        std::vector<double> part((size_t)3 * ctx->ncx * ctx->ncy);
+        std::vector<double> part((size_t)3 * nb);
         ISM_CUDA_TRY(cudaMemcpyAsync(part.data(), ctx->partials, part.size() * 8, cudaMemcpyDeviceToHost, ctx->ws));
         ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
-        const int nb = ctx->ncx * ctx->ncy;
         double r2 = 0, ps = 0;
         for (int k = 0; k < nb; ++k) { r2 += part[k]; ps += part[nb + k]; }
         norms[0] = sqrt(r2);
