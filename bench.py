@@ -150,6 +150,46 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ roofline bookkeeping
 
+def large_grid_passes(peak, peak_kind, dev):
+    """Pass rates on a grid whose single-precision fields (128 MB) exceed L2:
+    the streaming one-sweep pass, the streaming residual + restriction pass and
+    the fused 8-sweep tiled pass, each timed alone with CUDA events on the
+    library's stream."""
+    nx, ny, m = 8192, 4096, 32
+    n = nx * ny
+    s, c = ism.ism_setup(nx, ny, 1.0 / nx, (0, 0, 0, 0), m, ism.ISM_MIXED)
+    ism.check(s, "ism_setup (large grid)")
+    p = torch.zeros((ny, nx), dtype=torch.float32, device=dev)
+    b = torch.randn((ny, nx), dtype=torch.float32, device=dev) * 1e-6
+    rc = torch.zeros((ny // m, nx // m), dtype=torch.float32, device=dev)
+    o = ism.ism_get_options(c)
+    o.stream = 1
+    ism.check(ism.ism_set_options(c, o), "ism_set_options")
+    s, us_s = ism.ism_time_pass(c, p, b, 1, 20)
+    ism.check(s, "ism_time_pass")
+    s, us_r = ism.ism_time_restrict(c, p, b, rc, 20)
+    ism.check(s, "ism_time_restrict")
+    o.stream = 0
+    ism.check(ism.ism_set_options(c, o), "ism_set_options")
+    s, us_t = ism.ism_time_pass(c, p, b, 8, 10)
+    ism.check(s, "ism_time_pass")
+    del c
+
+    def entry(kernel, us, bytes_cell, sweeps=None):
+        a = bytes_cell * n / (us * 1e-6) / 1e9
+        d = {"kernel": kernel, "bound": "hbm", "us_per_launch": round(us, 2),
+             "algorithmic_bytes_per_launch": bytes_cell * n, "achieved": round(a, 1), "peak": peak,
+             "unit": "GB/s", "frac": round(a / peak, 4), "peak_source": peak_kind}
+        if sweeps:
+            d["us_per_sweep"] = round(us / sweeps, 2)
+        return d
+
+    return {"grid": f"{nx}x{ny}, 32h (fields of 128 MB, larger than L2)",
+            "stream_sweep": entry("k_stream32<1>: one red-black sweep, streaming", us_s, 12.0, 1),
+            "restriction": entry("k_restrict_stream<float>: residual + block sums + norm partials", us_r, 8.0),
+            "tiled_8_sweeps": entry("k_sweep32: fused 8-sweep tiled pass (the solver's default)", us_t, 12.0, 8)}
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -359,6 +399,11 @@ def run_ours(args):
                         "moves 12 B per cell whatever the number of fused sweeps, so the fraction is "
                         "of an L2-resident, latency-bound kernel (cell_sweeps_per_s is its rate)"}
 
+    # ---- grids larger than L2: the streaming passes at 8192 x 4096 (128 MB fields)
+    large = None
+    if rank == 0 and not args.no_large:
+        large = large_grid_passes(peak, peak_kind, dev)
+
     # ---- end to end through the public API with host buffers
     hu = torch.zeros((n, n + 1), dtype=torch.float32).pin_memory()
     hv = torch.zeros((n + 1, n), dtype=torch.float32).pin_memory()
@@ -399,6 +444,8 @@ def run_ours(args):
                      "final_relres_max": max(relres),
                      "mcell_cycles_per_s": round(world * N_GRID * N_GRID * sum(cycles) / (total_ms / 1000.0) / 1e6, 1)},
            "roofline": roofline, "clocks": clocks, "e2e": e2e, "gpu_launches": int(launches)}
+    if large is not None:
+        out["large_grid_passes"] = large
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         smp = run_cpu_sample_subprocess(args.cpu_cycles)
@@ -450,6 +497,7 @@ def main():
     ap.add_argument("--cpu-cycles", type=int, default=12)
     ap.add_argument("--ref-cycles", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the 8192x4096 pass measurements")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --nu / --sweeps-per-pass / --nu-fp64 instead of ism_autotune")
     ap.add_argument("--nu", type=int, default=32)

@@ -261,6 +261,14 @@ ism_status ism_prolong_add(ism_ctx *ctx, const void *ec, void *p);
 ism_status ism_time_pass(ism_ctx *ctx, void *p, const void *b, int sweeps, int reps,
                          double *us_per_pass);
 
+/* Measurement helper: run `reps` residual + restriction passes (those of
+ * ism_residual_restrict, Sec. 3.2-3.3, norms left on the device) on p, b
+ * into rc (device arrays as for ism_residual_restrict) and return in
+ * *us_per_pass the mean device time of one pass, taken with CUDA events on
+ * the library's work stream.  Synchronises. */
+ism_status ism_time_restrict(ism_ctx *ctx, const void *p, const void *b, void *rc, int reps,
+                             double *us_per_pass);
+
 /* ---------------- projection time step (Sec. 2.2-2.3, Eq. 3-4) ---------- */
 
 /* Velocity boundary setup for proj_step.

@@ -1291,6 +1291,34 @@ extern "C" ism_status ism_prolong_add(ism_ctx *ctx, const void *ec, void *p)
     return ism_leave(ctx);
 }
 
+extern "C" ism_status ism_time_restrict(ism_ctx *ctx, const void *p, const void *b, void *rc, int reps,
+                                        double *us_per_pass)
+{
+    if (!ctx || !p || !b || !rc || reps < 1 || !us_per_pass) return ISM_ERR_ARG;
+    cudaEvent_t e0, e1;
+    ISM_CUDA_TRY(cudaEventCreate(&e0));
+    ISM_CUDA_TRY(cudaEventCreate(&e1));
+    auto pass = [&]() -> ism_status {
+        if (ctx->prec == ISM_FP64) return launch_resid<double>(ctx, (const double *)p, (const double *)b, (double *)rc, nullptr);
+        return launch_resid<float>(ctx, (const float *)p, (const float *)b, (float *)rc, nullptr);
+    };
+    ism_status st = ism_enter(ctx);
+    if (st == ISM_OK) st = pass();                           // warm-up
+    if (st == ISM_OK) {
+        ISM_CUDA_TRY(cudaEventRecord(e0, ctx->ws));
+        for (int r = 0; r < reps && st == ISM_OK; ++r) st = pass();
+        ISM_CUDA_TRY(cudaEventRecord(e1, ctx->ws));
+        ISM_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        ISM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        *us_per_pass = 1000.0 * ms / reps;
+        ism_leave(ctx);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 extern "C" ism_status ism_time_pass(ism_ctx *ctx, void *p, const void *b, int sweeps, int reps,
                                     double *us_per_pass)
 {

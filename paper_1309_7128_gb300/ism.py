@@ -61,6 +61,7 @@ _SIGS = {
     "ism_proj_tol": (_I, [_VP, _D, _I, _I]),
     "ism_last_dp": (_VP, [_VP]),
     "ism_time_pass": (_I, [_VP, _VP, _VP, _I, _I, C.POINTER(C.c_double)]),
+    "ism_time_restrict": (_I, [_VP, _VP, _VP, _VP, _I, C.POINTER(C.c_double)]),
     "ism_autotune": (_I, [_VP, _VP, _D, _I, C.POINTER(IsmOptions)]),
     "ism_residual_restrict_noalloc": (_I, [_I, _I, _I, C.POINTER(C.c_int), _VP, _VP, _VP, _VP, _VP]),
     "ism_solve_batched": (_I, [_I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _D, _I,
@@ -201,6 +202,13 @@ def ism_residual_restrict_noalloc(nx, ny, coarsen, bc, p, b, rc, norms, stream=N
     bca = (C.c_int * 4)(*[int(x) for x in bc])
     return lib().ism_residual_restrict_noalloc(int(nx), int(ny), int(coarsen), bca, _ptr(p), _ptr(b),
                                                _ptr(rc), _ptr(norms), _stream(stream))
+
+
+def ism_time_restrict(ctx, p, b, rc, reps):
+    """Returns (status, mean device microseconds per residual + restriction pass)."""
+    us = C.c_double(0.0)
+    s = lib().ism_time_restrict(ctx.handle, _ptr(p), _ptr(b), _ptr(rc), int(reps), C.byref(us))
+    return s, us.value
 
 
 def ism_time_pass(ctx, p, b, sweeps, reps):
