@@ -155,6 +155,9 @@ def large_grid_passes(peak, peak_kind, dev):
     the streaming one-sweep pass, the streaming residual + restriction pass and
     the fused 8-sweep tiled pass, each timed alone with CUDA events on the
     library's stream."""
+    import torch
+
+    from paper_1309_7128_gb300 import ism
     nx, ny, m = 8192, 4096, 32
     n = nx * ny
     s, c = ism.ism_setup(nx, ny, 1.0 / nx, (0, 0, 0, 0), m, ism.ISM_MIXED)
