@@ -315,8 +315,9 @@ def run_ours(args):
         else:
             s, o = ism.ism_autotune(c, rhs_tune, TOL, 1_000_000)
             ism.check(s, "ism_autotune")
-        return c, {"nu_sweeps": o.nu, "sweeps_per_pass": o.sweeps_per_pass,
-                   "autotuned": not args.no_autotune}
+        o = ism.ism_get_options(c)
+        return c, {"nu_sweeps": o.nu, "sweeps_per_pass": o.sweeps_per_pass, "stream": o.stream,
+                   "inner_tol": o.inner_tol, "autotuned": not args.no_autotune}
 
     ctx, opt_mixed = tuned_ctx(ism.ISM_MIXED)
     u = torch.zeros((n, n + 1), dtype=torch.float32, device=dev)

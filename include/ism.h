@@ -179,11 +179,12 @@ ism_status ism_set_options(ism_ctx *ctx, const ism_options *opt);
 ism_status ism_solve(ism_ctx *ctx, const double *rhs, double *p, double tol,
                      int max_cycles, int *cycles_out, double *relres_out);
 
-/* ism_autotune -- choose the sweeps per cycle and per fused pass for this
- * context by timing complete solves of rhs (device, nx*ny doubles) from a
- * zero initial guess over a fixed candidate list; keeps the fastest
- * candidate in the context's options and copies it to *best (host, may be
- * NULL).  No counterpart in the paper (its tile size and coarse tolerance
+/* ism_autotune -- choose the sweeps per cycle and per fused pass (and, for
+ * ISM_MIXED, whether the middle passes stream and the refinement's inner
+ * stopping factor inner_tol) for this context by timing complete solves of
+ * rhs (device, nx*ny doubles) from a zero initial guess over a fixed
+ * candidate list; keeps the fastest candidate in the context's options and
+ * copies it to *best (host, may be NULL).  No counterpart in the paper (its tile size and coarse tolerance
  * were tuned by hand, Sec. 4.1, 4.3.1).  Allocates one nx*ny double buffer
  * for the duration of the call.  Synchronises. */
 ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, int max_cycles,

@@ -19,6 +19,16 @@
 #include "ism_stream32.cuh"
 #include "ism_restrict_stream.cuh"
 
+// Dynamic shared memory of the streaming restriction (m = 8, 16, 32).
+template <typename T>
+static void restrict_stream_attrs()
+{
+    const int sm = (int)RestrictShape<T>::smem;
+    cudaFuncSetAttribute(k_restrict_stream<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_restrict_stream<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaFuncSetAttribute(k_restrict_stream<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+}
+
 // ================================================================ control
 
 __global__ void __launch_bounds__(256) k_ctl(IsmState *st, const double *partials, int nblk,
@@ -59,38 +69,106 @@ __global__ void k_rhs_stats(const double *__restrict__ x, double *__restrict__ y
 // ================================================================ mixed-path outer kernels
 
 // FP64 refinement step on the ping-pong pair p0/p1 (st->c64 selects the
-// current iterate).  UPDATE: p_out = p_in + e (e = inner iterate selected by
-// st->cur); then r = b - A_f p_out in FP64, r32 = (float) r, partials
-// (||r||^2, sum p_out).  Grid (ceil(nx/256), ny).
-template <bool UPDATE>
-__global__ void k_refine(double *p0, double *p1,
-                         const float *e0, const float *e1, const double *__restrict__ b,
-                         float *__restrict__ r32, double *partials, int nx, int ny, int bcmask,
-                         const IsmState *st)
+// current iterate), in two kernels so that every FP64 operation is done once
+// per cell (the FP64 pipe of this GPU is 1/64 of the FP32 rate):
+//   k_refine_add:   p_out = p_in + e (e = inner iterate selected by st->cur);
+//   k_refine_resid: r = b - A_f p in FP64 on p_out (after an update) or p_in
+//                   (first residual), r32 = (float) r, partials
+//                   (||r||^2, sum p).
+// nx % 4 == 0 (the mixed path's fields are whole float4 groups per row).
+__global__ void k_refine_add(double *p0, double *p1, const float *e0, const float *e1, long long n4,
+                             const IsmState *st)
 {
-    const int j = blockIdx.y;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const float *__restrict__ e = (UPDATE && st->cur) ? e1 : e0;
-    const double *__restrict__ p_in = st->c64 ? p1 : p0;
-    double *__restrict__ p_out = st->c64 ? p0 : p1;
+    const float4 *__restrict__ e = reinterpret_cast<const float4 *>(st->cur ? e1 : e0);
+    const double2 *__restrict__ pi = reinterpret_cast<const double2 *>(st->c64 ? p1 : p0);
+    double2 *__restrict__ po = reinterpret_cast<double2 *>(st->c64 ? p0 : p1);
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n4;
+         k += (long long)gridDim.x * blockDim.x) {
+        const float4 ev = e[k];
+        const double2 a = pi[2 * k], c = pi[2 * k + 1];
+        po[2 * k] = make_double2(a.x + (double)ev.x, a.y + (double)ev.y);
+        po[2 * k + 1] = make_double2(c.x + (double)ev.z, c.y + (double)ev.w);
+    }
+}
+
+constexpr int RF_ROWS = 4;       // rows per thread of k_refine_resid
+constexpr int RF_THREADS = 128;  // 4 columns each
+
+// One thread: 4 adjacent columns of RF_ROWS rows.  The neighbour sum takes
+// the terms in the order west, east, south, north with 0 for a wall face
+// (x + 0 == x: the same value as the sum over in-domain neighbours).
+__global__ void __launch_bounds__(RF_THREADS) k_refine_resid(const double *p0, const double *p1,
+                                                             const double *__restrict__ b, float *__restrict__ r32,
+                                                             double *partials, int nx, int ny, int bcmask,
+                                                             const IsmState *st, int after_update)
+{
+    const double *__restrict__ p = (after_update ? !st->c64 : st->c64) ? p1 : p0;
+    const int i = 4 * (blockIdx.x * RF_THREADS + threadIdx.x);
+    const int j0 = blockIdx.y * RF_ROWS;
+    const bool per_x = (bcmask & ISM_PER_X) != 0, per_y = (bcmask & ISM_PER_Y) != 0;
     double r2 = 0.0, ps = 0.0;
     if (i < nx) {
-        const size_t idx = (size_t)j * nx + i;
-        auto P = [&](size_t k) -> double {
-            double v = p_in[k];
-            if (UPDATE) v += (double)e[k];
-            return v;
-        };
-        const double pc = P(idx);
-        const double s = nb_sum<double>(P, (long long)idx, i, j, nx, ny, bcmask);
-        const double r = b[idx] - (s - (double)diag_count(i, j, nx, ny, bcmask) * pc);
-        if (UPDATE) p_out[idx] = pc;
-        r32[idx] = (float)r;
-        r2 = r * r;
-        ps = pc;
+        // west / east neighbours of the 4-column group
+        const bool hasw = i > 0 || per_x, hase = i + 4 < nx || per_x;
+        const int iw = i > 0 ? i - 1 : nx - 1, ie = i + 4 < nx ? i + 4 : 0;
+        // diagonal count per column without the south / north faces
+        double dcol[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int d = 4;
+            if (!per_x && i + q == 0) d += (bcmask & 1) ? 1 : -1;
+            if (!per_x && i + q == nx - 1) d += (bcmask & 2) ? 1 : -1;
+            dcol[q] = (double)d;
+        }
+        for (int jj = 0; jj < RF_ROWS; ++jj) {
+            const int j = j0 + jj;
+            if (j >= ny) break;
+            const bool hass = j > 0 || per_y, hasn = j < ny - 1 || per_y;
+            const int js = j > 0 ? j - 1 : ny - 1, jn = j < ny - 1 ? j + 1 : 0;
+            const double *row = p + (size_t)j * nx;
+            const double2 c01 = *reinterpret_cast<const double2 *>(row + i);
+            const double2 c23 = *reinterpret_cast<const double2 *>(row + i + 2);
+            double2 s01 = make_double2(0.0, 0.0), s23 = s01, n01 = s01, n23 = s01;
+            if (hass) {
+                s01 = *reinterpret_cast<const double2 *>(p + (size_t)js * nx + i);
+                s23 = *reinterpret_cast<const double2 *>(p + (size_t)js * nx + i + 2);
+            }
+            if (hasn) {
+                n01 = *reinterpret_cast<const double2 *>(p + (size_t)jn * nx + i);
+                n23 = *reinterpret_cast<const double2 *>(p + (size_t)jn * nx + i + 2);
+            }
+            const double w = hasw ? row[iw] : 0.0, e = hase ? row[ie] : 0.0;
+            const double pc[4] = {c01.x, c01.y, c23.x, c23.y};
+            const double so[4] = {s01.x, s01.y, s23.x, s23.y};
+            const double no[4] = {n01.x, n01.y, n23.x, n23.y};
+            const double2 b01 = *reinterpret_cast<const double2 *>(b + (size_t)j * nx + i);
+            const double2 b23 = *reinterpret_cast<const double2 *>(b + (size_t)j * nx + i + 2);
+            const double bv[4] = {b01.x, b01.y, b23.x, b23.y};
+            // south / north wall faces of this row (uniform across the block)
+            int drow = 0;
+            if (!per_y && j == 0) drow += (bcmask & 4) ? 1 : -1;
+            if (!per_y && j == ny - 1) drow += (bcmask & 8) ? 1 : -1;
+            float rr[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const double lf = q == 0 ? w : pc[q - 1], rt = q == 3 ? e : pc[q + 1];
+                const double d = drow ? dcol[q] + (double)drow : dcol[q];
+                const double sum = ((lf + rt) + so[q]) + no[q];
+                const double r = bv[q] - (sum - d * pc[q]);
+                rr[q] = (float)r;
+                r2 = fma(r, r, r2);
+                ps += pc[q];
+            }
+            *reinterpret_cast<float4 *>(r32 + (size_t)j * nx + i) = make_float4(rr[0], rr[1], rr[2], rr[3]);
+        }
     }
     double v[2] = {r2, ps};
     block_partials<2>(v, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+static inline dim3 refine_grid(int nx, int ny)
+{
+    return dim3((nx / 4 + RF_THREADS - 1) / RF_THREADS, (ny + RF_ROWS - 1) / RF_ROWS);
 }
 
 // out = in - mean (mean of the final iterate when all faces are Neumann);
@@ -334,7 +412,7 @@ extern "C" void ism_destroy(ism_ctx *ctx)
                     ctx->p64[1], ctx->e32[0], ctx->e32[1], ctx->r32, ctx->rc64, ctx->ec64,
                     ctx->T64, ctx->rc32, ctx->ec32, ctx->T32, ctx->partials, ctx->st,
                     ctx->st_k, ctx->us, ctx->vs, ctx->dp, ctx->rcpart, ctx->roll, ctx->scal,
-                    ctx->tc_block};
+                    ctx->tc_block, ctx->G64};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int l = 0; l < 6; ++l) {
@@ -427,6 +505,7 @@ ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarse
     ALLOC(ctx->rc64, nc * 8); ALLOC(ctx->ec64, nc * 8); ALLOC(ctx->T64, nc * 8);
     ALLOC(ctx->rc32, nc * 4); ALLOC(ctx->ec32, nc * 4); ALLOC(ctx->T32, nc * 4);
     ALLOC(ctx->rcpart, nc * 4 * 4);
+    if (prec == ISM_FP64) ALLOC(ctx->G64, (size_t)ctx->ncy * nx * 8);
     if (prec == ISM_MIXED) {
         ALLOC(ctx->p64[1], N * 8);
         ALLOC(ctx->e32[0], N * 4);
@@ -467,10 +546,8 @@ ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarse
     // the fused sweep pass uses 80 KB of dynamic shared memory
     const int smb = (int)sweep_smem_bytes();
     ism_coarse_tc_prepare();
-    cudaFuncSetAttribute(k_restrict_stream<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)RestrictShape<float>::smem);
-    cudaFuncSetAttribute(k_restrict_stream<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)RestrictShape<double>::smem);
+    restrict_stream_attrs<float>();
+    restrict_stream_attrs<double>();
     cudaFuncSetAttribute(k_sweep32<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
     cudaFuncSetAttribute(k_sweep32<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
     cudaFuncSetAttribute(k_sweep32<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
@@ -584,40 +661,51 @@ static ism_status launch_coarse(ism_ctx *ctx, const T *rc, T *ec, T *Tm, const i
     return ISM_OK;
 }
 
+// Streaming restriction for one m: strips of 128 columns and chunks of rows
+// (multiples of m) sized to fill the resident warps once.  Returns the number
+// of CTAs, or 0 when that exceeds the norm-partial slots.
+template <typename T, int M>
+static int launch_restrict_stream(ism_ctx *ctx, const T *p, const T *b, T *rc, const int *skip, int ctl_mode,
+                                  unsigned long long cond)
+{
+    using S = RestrictShape<T>;
+    static int slots = 0;                        // resident warps on the device
+    if (!slots) {
+        int dev = 0, sms = 152, per_sm = 1;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_restrict_stream<T, M>, 32 * RR_NW, S::smem) !=
+                cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        cudaGetLastError();
+        slots = sms * per_sm * RR_NW;
+    }
+    const int nstrip = (ctx->nx + SRW - 1) / SRW;
+    const int nchunk = std::max(1, slots / nstrip);
+    int chunk_h = (ctx->ny + nchunk - 1) / nchunk;
+    chunk_h = ((chunk_h + M - 1) / M) * M;       // whole coarse rows
+    const int ntask = nstrip * ((ctx->ny + chunk_h - 1) / chunk_h);
+    const int grid = (ntask + RR_NW - 1) / RR_NW;
+    if (grid > ctx->max_blocks) return 0;
+    k_restrict_stream<T, M><<<grid, 32 * RR_NW, S::smem, ctx->ws>>>(
+        p, b, rc, ctx->partials, ctx->nx, ctx->ny, ctx->ncx, ctx->bcmask, nstrip, chunk_h, ntask, skip, ctx->st,
+        ctl_mode, cond);
+    return grid;
+}
+
 // Residual, restriction and norm partials.  Rows of whole 16-byte groups
-// (nx % 4 == 0): the streaming pass (ism_restrict_stream.cuh), strips of 128
-// columns and chunks of rows (multiples of m) sized to fill the resident
-// warps once; otherwise one CTA per coarse cell.  *nblk: the number of CTAs,
-// i.e. of norm partials.
+// (nx % 4 == 0): the streaming pass (ism_restrict_stream.cuh); otherwise one
+// CTA per coarse cell.  *nblk: the number of CTAs, i.e. of norm partials.
 template <typename T>
 static ism_status launch_resid(ism_ctx *ctx, const T *p, const T *b, T *rc, const int *skip,
                                int ctl_mode = -1, unsigned long long cond = 0, int *nblk = nullptr)
 {
     if (ctx->nx % 4 == 0) {
-        using S = RestrictShape<T>;
-        static int slots = 0;                    // resident warps on the device
-        if (!slots) {
-            int dev = 0, sms = 152, per_sm = 1;
-            if (cudaGetDevice(&dev) == cudaSuccess)
-                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_restrict_stream<T>, 32 * RR_NW, S::smem) !=
-                    cudaSuccess || per_sm < 1)
-                per_sm = 1;
-            cudaGetLastError();
-            slots = sms * per_sm * RR_NW;
-        }
-        const int m = ctx->m, nstrip = (ctx->nx + SRW - 1) / SRW;
-        const int nchunk = std::max(1, slots / nstrip);
-        int chunk_h = (ctx->ny + nchunk - 1) / nchunk;
-        chunk_h = ((chunk_h + m - 1) / m) * m;   // whole coarse rows
-        const int ntask = nstrip * ((ctx->ny + chunk_h - 1) / chunk_h);
-        const int grid = (ntask + RR_NW - 1) / RR_NW;
-        if (grid <= ctx->max_blocks) {
-            int lm = 0;
-            while ((1 << lm) < m) ++lm;
-            k_restrict_stream<T><<<grid, 32 * RR_NW, S::smem, ctx->ws>>>(
-                p, b, rc, ctx->partials, ctx->nx, ctx->ny, m, lm, ctx->ncx, ctx->bcmask, nstrip, chunk_h, ntask, skip,
-                ctx->st, ctl_mode, cond);
+        int grid = 0;
+        if (ctx->m == 8) grid = launch_restrict_stream<T, 8>(ctx, p, b, rc, skip, ctl_mode, cond);
+        else if (ctx->m == 16) grid = launch_restrict_stream<T, 16>(ctx, p, b, rc, skip, ctl_mode, cond);
+        else if (ctx->m == 32) grid = launch_restrict_stream<T, 32>(ctx, p, b, rc, skip, ctl_mode, cond);
+        if (grid > 0) {
             ISM_LAUNCH_CHECK(ctx);
             if (nblk) *nblk = grid;
             return ISM_OK;
@@ -836,10 +924,20 @@ static ism_status fp64_cycle(ism_ctx *ctx, unsigned long long cond = 0)
     if (ctx->opt.kind == ISM_COARSE_ACMV) return acmv_cycle(ctx, cond);
     const int *skip = &ctx->st->done;
     TRY((launch_coarse<double, false>(ctx, ctx->rc64, ctx->ec64, ctx->T64, skip)));
-    k_prolong<double><<<row_grid(ctx->nx, ctx->ny, 128), 128, 0, ctx->ws>>>(
-        ctx->p64[0], ctx->ec64, ctx->nx, ctx->ny, ctx->m, ctx->ncx, ctx->ncy, ctx->bcmask,
-        ctx->opt.kind, ctx->st, ctx->singular, skip);
-    ISM_LAUNCH_CHECK(ctx);
+    if (ctx->opt.kind == ISM_COARSE_ACM) {
+        k_prolong<double><<<row_grid(ctx->nx, ctx->ny, 128), 128, 0, ctx->ws>>>(
+            ctx->p64[0], ctx->ec64, ctx->nx, ctx->ny, ctx->m, ctx->ncx, ctx->ncy, ctx->bcmask,
+            ctx->opt.kind, ctx->st, ctx->singular, skip);
+        ISM_LAUNCH_CHECK(ctx);
+    } else {
+        // bilinear (ISM, GMG): separable form, x first into G, then y per fine row
+        k_prolong_x<double><<<dim3((ctx->nx + 127) / 128, ctx->ncy), 128, 0, ctx->ws>>>(
+            ctx->ec64, ctx->G64, ctx->nx, ctx->m, ctx->ncx, ctx->ncy, ctx->bcmask, skip);
+        ISM_LAUNCH_CHECK(ctx);
+        k_prolong_y<double><<<dim3((ctx->nx + 1023) / 1024, ctx->ny), 256, 0, ctx->ws>>>(
+            ctx->p64[0], ctx->G64, ctx->nx, ctx->ny, ctx->m, ctx->ncy, ctx->bcmask, ctx->st, ctx->singular, skip);
+        ISM_LAUNCH_CHECK(ctx);
+    }
     TRY(launch_sweeps<double>(ctx, ctx->p64[0], ctx->b64, ctx->opt.nu, skip));
     return launch_resid<double>(ctx, ctx->p64[0], ctx->b64, ctx->rc64, skip, CTL_FP64_AFTER, cond);
 }
@@ -1025,10 +1123,12 @@ static ism_status inner_init(ism_ctx *ctx)
 
 static ism_status refine_update(ism_ctx *ctx, unsigned long long cond)
 {
-    const dim3 rg = row_grid(ctx->nx, ctx->ny, 256);
-    k_refine<true><<<rg, 256, 0, ctx->ws>>>(ctx->p64[0], ctx->p64[1], ctx->e32[0], ctx->e32[1],
-                                            ctx->b64, ctx->r32, ctx->partials, ctx->nx, ctx->ny,
-                                            ctx->bcmask, ctx->st);
+    k_refine_add<<<4 * 152, 256, 0, ctx->ws>>>(ctx->p64[0], ctx->p64[1], ctx->e32[0], ctx->e32[1], ctx->n / 4,
+                                               ctx->st);
+    ISM_LAUNCH_CHECK(ctx);
+    const dim3 rg = refine_grid(ctx->nx, ctx->ny);
+    k_refine_resid<<<rg, RF_THREADS, 0, ctx->ws>>>(ctx->p64[0], ctx->p64[1], ctx->b64, ctx->r32, ctx->partials,
+                                                   ctx->nx, ctx->ny, ctx->bcmask, ctx->st, 1);
     ISM_LAUNCH_CHECK(ctx);
     return launch_ctl(ctx, ctx->st, rg.x * rg.y, 2, CTL_OUTER_AFTER, cond);
 }
@@ -1110,11 +1210,10 @@ static ism_status solve_fp64(ism_ctx *ctx)
 
 static ism_status solve_mixed(ism_ctx *ctx)
 {
-    const dim3 rg = row_grid(ctx->nx, ctx->ny, 256);
+    const dim3 rg = refine_grid(ctx->nx, ctx->ny);
     const int nrb = rg.x * rg.y;
-    k_refine<false><<<rg, 256, 0, ctx->ws>>>(ctx->p64[0], ctx->p64[1], ctx->e32[0], ctx->e32[1],
-                                             ctx->b64, ctx->r32, ctx->partials, ctx->nx, ctx->ny,
-                                             ctx->bcmask, ctx->st);
+    k_refine_resid<<<rg, RF_THREADS, 0, ctx->ws>>>(ctx->p64[0], ctx->p64[1], ctx->b64, ctx->r32, ctx->partials,
+                                                   ctx->nx, ctx->ny, ctx->bcmask, ctx->st, 0);
     ISM_LAUNCH_CHECK(ctx);
     TRY(launch_ctl(ctx, ctx->st, nrb, 2, CTL_OUTER_INIT));
     TRY(read_state(ctx));
@@ -1364,12 +1463,18 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
     if (!ctx || !rhs || !(tol > 0.0) || max_cycles < 1) return ISM_ERR_ARG;
     // a cycle costs a fixed part (coarse solve, fused prolongation and residual,
     // control) plus one part per pass, and the total sweeps of a solve are
-    // nearly independent of nu: larger nu amortises the fixed part
-    static const int cand_mixed[][2] = {{8, 4},  {8, 8},  {16, 8}, {24, 8},  {32, 8},
-                                        {48, 8}, {64, 8}, {96, 8}, {128, 8}, {16, 4}};
-    static const int cand_fp64[][2] = {{8, 4}, {16, 4}, {32, 4}, {48, 4}, {64, 4}};
-    const int (*cand)[2] = ctx->prec == ISM_MIXED ? cand_mixed : cand_fp64;
-    const int ncand = ctx->prec == ISM_MIXED ? 10 : 5;
+    // nearly independent of nu: larger nu amortises the fixed part.  Mixed
+    // candidates {nu, sweeps per pass, stream}: the streaming middle passes
+    // (stream = 1, 4 sweeps per pass) win on grids larger than L2.
+    static const int cand_mixed[][3] = {{8, 4, 0},  {8, 8, 0},   {16, 8, 0}, {24, 8, 0}, {32, 8, 0},
+                                        {48, 8, 0}, {64, 8, 0},  {96, 8, 0}, {128, 8, 0}, {16, 4, 0},
+                                        {32, 4, 1}, {64, 4, 1}, {128, 4, 1}};
+    static const int cand_fp64[][3] = {{8, 4, 0}, {16, 4, 0}, {32, 4, 0}, {48, 4, 0}, {64, 4, 0}};
+    // then, for the mixed winner, the inner stopping factor of the refinement
+    static const double inner_tols[] = {1e-4, 1e-2};
+    const int (*cand)[3] = ctx->prec == ISM_MIXED ? cand_mixed : cand_fp64;
+    const int ncand = ctx->prec == ISM_MIXED ? 13 : 5;
+    const int ntol = ctx->prec == ISM_MIXED ? 2 : 0;
     const ism_options saved = ctx->opt;
     double *p = nullptr;
     if (cudaMalloc((void **)&p, (size_t)ctx->n * 8) != cudaSuccess) { cudaGetLastError(); return ISM_ERR_NOMEM; }
@@ -1379,9 +1484,15 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
     ism_options opt = saved, win = saved;
     float best_ms = 1e30f;
     ism_status st = ISM_OK;
-    for (int c = 0; c < ncand && st == ISM_OK; ++c) {
-        opt.nu = cand[c][0];
-        opt.sweeps_per_pass = cand[c][1];
+    for (int c = 0; c < ncand + ntol && st == ISM_OK; ++c) {
+        if (c < ncand) {
+            opt.nu = cand[c][0];
+            opt.sweeps_per_pass = cand[c][1];
+            opt.stream = cand[c][2];
+        } else {
+            opt = win;
+            opt.inner_tol = inner_tols[c - ncand];
+        }
         if ((st = ism_set_options(ctx, &opt)) != ISM_OK) break;
         float ms = 0.f;
         for (int rep = 0; rep < 2 && st == ISM_OK; ++rep) {     // first run builds the graph

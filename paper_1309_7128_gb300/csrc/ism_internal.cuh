@@ -67,6 +67,7 @@ struct ism_ctx {
     float *e32[2];             // mixed: single-precision inner iterate (ping-pong)
     float *r32;                // mixed: inner right-hand side
     double *rc64, *ec64, *T64; // coarse residual, correction, intermediate
+    double *G64;               // FP64: coarse rows interpolated along x (ncy x nx), separable prolongation
     float *rc32, *ec32, *T32;
     float *rcpart;             // 4 partial block sums per coarse cell (fused restriction)
     double *lvl_r[6], *lvl_e[6];   // deep V-cycle (ISM_COARSE_ACMV): residual / correction of levels 1..L-1

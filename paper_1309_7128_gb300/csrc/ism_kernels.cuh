@@ -445,6 +445,57 @@ __global__ void k_prolong(T *__restrict__ p, const T *__restrict__ ec, int nx, i
     p[idx] = v + prolong_value<T>(ec, i, j, nx, ny, m, ncx, ncy, bcmask, kind);
 }
 
+// Separable form of the bilinear prolongation (Eq. 5), used by the FP64
+// cycle, where every FP64 operation counts (the FP64 pipe of this GPU runs at
+// 1/64 of the FP32 rate).  First the coarse rows are interpolated along x:
+// G[J][x] = (1 - t_x) e_c[J][I0] + t_x e_c[J][I0 + 1], with the ghost centres
+// beyond a face along x as in coarse_ghost.  Grid (ceil(nx / 128), ncy).
+template <typename T>
+__global__ void k_prolong_x(const T *__restrict__ q, T *__restrict__ G, int nx, int m, int ncx, int ncy,
+                            int bcmask, const int *skip)
+{
+    if (skip && *skip) return;
+    const int J = blockIdx.y, x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    int I0;
+    T tx;
+    interp_coord<T>(x, nx, m, __ffs(m) - 1, ncx, I0, tx);
+    const T a = coarse_ghost(q, I0, J, ncx, ncy, bcmask), c = coarse_ghost(q, I0 + 1, J, ncx, ncy, bcmask);
+    G[(size_t)J * nx + x] = ((T)1 - tx) * a + tx * c;
+}
+
+// Then along y: p = p - mean + (1 - t_y) G[J0][x] + t_y G[J0 + 1][x], the
+// ghost rows beyond a south / north face folded into the two row weights
+// (the sign of an odd ghost) or wrapped (periodic).  Grid (ceil(nx / 1024),
+// ny), several cells per thread so that the row's weights are amortised.
+template <typename T>
+__global__ void k_prolong_y(T *__restrict__ p, const T *__restrict__ G, int nx, int ny, int m, int ncy,
+                            int bcmask, const IsmState *st, int use_mean, const int *skip)
+{
+    if (skip && *skip) return;
+    const int y = blockIdx.y;
+    int J0;
+    T ty;
+    interp_coord<T>(y, ny, m, __ffs(m) - 1, ncy, J0, ty);
+    T w0 = (T)1 - ty, w1 = ty;
+    int J1 = J0 + 1;
+    if (bcmask & ISM_PER_Y) {
+        J0 = wrap_mod(J0, ncy);
+        J1 = wrap_mod(J1, ncy);
+    } else {
+        if (J0 < 0) { J0 = 0; if (bcmask & 4) w0 = -w0; }
+        if (J1 >= ncy) { J1 = ncy - 1; if (bcmask & 8) w1 = -w1; }
+    }
+    const T *__restrict__ g0 = G + (size_t)J0 * nx, *__restrict__ g1 = G + (size_t)J1 * nx;
+    T *__restrict__ row = p + (size_t)y * nx;
+    const T mu = use_mean ? (T)st->mean : (T)0;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x) {
+        T v = row[x];
+        if (use_mean) v -= mu;
+        row[x] = v + (w0 * g0[x] + w1 * g1[x]);
+    }
+}
+
 // ----------------------------------------------------------------- coarse solve
 // A_c = (Qy x Qx) diag(mu) (Qy x Qx)^T, so A_c^+ r_c = Qy [(Qy^T R Qx) / mu] Qx^T
 // with 1/mu := 0 on the null mode.  R, E are ncy x ncx row-major.

@@ -1,7 +1,7 @@
 // ism_restrict_stream.cuh -- residual r = b - A_f p and its aggregating
 // restriction (Sec. 3.2-3.3: the block sums of r over the coarse cells), plus
-// the partial sums (||r||^2, sum p, sum p^2) for the convergence control, in
-// one streaming pass over p and b (FP32 or FP64).
+// the partial sums (||r||^2, sum p, and in FP32 sum p^2) for the convergence
+// control, in one streaming pass over p and b (FP32 or FP64).
 //
 // Each warp owns a strip of 128 columns starting at a multiple of 128 (so
 // every coarse cell of the strip is whole: m/4 adjacent lanes) and a chunk of
@@ -26,19 +26,24 @@ constexpr int RR_NW = 4;   // warps per CTA
 template <typename T>
 struct RestrictShape {
     static constexpr int PIECES = 4 * (int)sizeof(T) / 16;          // 16-byte pieces per lane and row
-    static constexpr int RS = sizeof(T) == 4 ? 10 : 8;               // ring rows
+    static constexpr int RS = 8;                                     // ring rows (divides m)
     static constexpr int SLOT = 2 * 32 * 4 + 8;                      // p, b of 32 lanes, 2 halo groups
     static constexpr size_t smem = (size_t)RR_NW * RS * SLOT * sizeof(T);
 };
 
-template <typename T>
+// M = m (8, 16 or 32): the loop over the m rows of a coarse row is unrolled,
+// and as the ring length divides m, every ring slot index is a constant.
+template <typename T, int M>
 __global__ void __launch_bounds__(32 * RR_NW)
 k_restrict_stream(const T *__restrict__ p, const T *__restrict__ b, T *__restrict__ rc, double *partials, int nx,
-                  int ny, int m, int lm, int ncx, int bcmask, int nstrip, int chunk_h, int ntask, const int *skip,
+                  int ny, int ncx, int bcmask, int nstrip, int chunk_h, int ntask, const int *skip,
                   IsmState *ctl_st, int ctl_mode, unsigned long long cond)
 {
     using S = RestrictShape<T>;
     constexpr int RS = S::RS, PIECES = S::PIECES, SLOT = S::SLOT, E16 = 16 / (int)sizeof(T);
+    constexpr int GL = M / 4;                                // lanes per coarse column
+    constexpr int LM = M == 8 ? 3 : M == 16 ? 4 : 5;
+    static_assert(M % RS == 0, "the ring length must divide m");
     if (skip && *skip) return;                               // the whole grid
     extern __shared__ __align__(16) unsigned char rr_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -59,33 +64,35 @@ k_restrict_stream(const T *__restrict__ p, const T *__restrict__ b, T *__restric
         const int cx = x0 + SNC * lane;
         const bool coldom = cx < nx;
         const bool colin = coldom || per_x;
-        const int cxl = per_x ? wrap_mod(cx, nx) : cx;
-        const int gl = m >> 2;                               // lanes per coarse column
-
-        // copies of row ya - 1 + k into ring slot k % RS (zeros outside the domain)
+        const T *pcol = p + (colin ? (per_x ? wrap_mod(cx, nx) : cx) : 0);
+        const T *bcol = b + (colin ? (per_x ? wrap_mod(cx, nx) : cx) : 0);
         // halo group of this lane: lane 0 the 4 columns left of the strip,
         // lane 31 the 4 right of it
+        const bool hlane = lane == 0 || lane == 31;
         const int hx = lane == 0 ? x0 - 4 : x0 + SRW;
-        const bool hin = (lane == 0 || lane == 31) && ((unsigned)hx < (unsigned)nx || per_x);
-        const int hxl = per_x ? wrap_mod(hx, nx) : hx;
-        auto fetch = [&](int k, int slot_k) {             // slot_k == k % RS
-            int y = ya - 1 + k;
+        const bool hin = hlane && ((unsigned)hx < (unsigned)nx || per_x);
+        const T *hcol = p + (hin ? (per_x ? wrap_mod(hx, nx) : hx) : 0);
+        T *hring = wring + 2 * 32 * 4 + (lane == 0 ? 0 : 4);
+
+        // copies of row y into ring slot `slot` (zeros outside the domain)
+        auto fetch = [&](int y, int slot) {
             bool rowin = (unsigned)y < (unsigned)ny;
-            if (per_y && !rowin) { y = wrap_mod(y, ny); rowin = true; }
-            const bool ok = rowin && colin;
-            const size_t off = ok ? (size_t)y * nx + cxl : 0;
-            T *slot = ring + (size_t)slot_k * SLOT;
+            if (per_y) {                                     // |overhang| < ny
+                y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+                rowin = true;
+            }
+            const size_t roff = rowin ? (size_t)y * nx : 0;
+            const int nb = rowin && colin ? 16 : 0;
+            T *sl = ring + slot * SLOT;
 #pragma unroll
             for (int c = 0; c < PIECES; ++c) {
-                cp_async16(slot + c * E16, p + off + c * E16, ok ? 16 : 0);
-                cp_async16(slot + 32 * 4 + c * E16, b + off + c * E16, ok ? 16 : 0);
+                cp_async16(sl + c * E16, pcol + roff + c * E16, nb);
+                cp_async16(sl + 32 * 4 + c * E16, bcol + roff + c * E16, nb);
             }
-            if (lane == 0 || lane == 31) {
-                const bool okh = rowin && hin;
-                const size_t offh = okh ? (size_t)y * nx + hxl : 0;
-                T *hs = wring + (size_t)slot_k * SLOT + 2 * 32 * 4 + (lane == 0 ? 0 : 4);
+            if (hlane) {
+                const int nh = rowin && hin ? 16 : 0;
 #pragma unroll
-                for (int c = 0; c < PIECES; ++c) cp_async16(hs + c * E16, p + offh + c * E16, okh ? 16 : 0);
+                for (int c = 0; c < PIECES; ++c) cp_async16(hring + slot * SLOT + c * E16, hcol + roff + c * E16, nh);
             }
             cp_async_commit();
         };
@@ -99,69 +106,79 @@ k_restrict_stream(const T *__restrict__ p, const T *__restrict__ b, T *__restric
             if (!per_x && x == nx - 1) d += (bcmask & 2) ? (T)1 : (T)-1;
             colD[q] = d;
         }
+        const T dS = (bcmask & 4) ? (T)1 : (T)-1, dN = (bcmask & 8) ? (T)1 : (T)-1;
 
+        // row ya - 1 + k goes to slot k % RS; rows ya - 1 .. ya + RS - 3 first
 #pragma unroll
-        for (int k = 0; k < RS - 1; ++k) fetch(k, k);
-        T Pm[4], P0[4], Pn[4], acc = (T)0;
-        // rows ya - 1 and ya (groups 0 and 1)
-        cp_async_wait<RS - 3>();
+        for (int k = 0; k < RS - 1; ++k) fetch(ya - 1 + k, k);
+        T Pm[4], P0[4], Pn[4];
+        cp_async_wait<RS - 3>();                             // rows ya - 1 and ya
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             Pm[q] = ring[q];
-            P0[q] = ring[(size_t)(1 % RS) * SLOT + q];
+            P0[q] = ring[SLOT + q];
         }
-        const int steps = yb - ya;
-        // ring slots of rows k = t + 1 (row y), t + 2 (row y + 1) and of the next copy (k = t + RS - 1)
-        int s1 = 1, s2 = 2 % RS, sf = RS - 1;
-        auto advance = [&](int &sl) { sl = (sl + 1 == RS) ? 0 : sl + 1; };
-        for (int t = 0; t < steps; ++t) {
-            const int y = ya + t;
-            // row y + 1 is group t + 2
-            cp_async_wait<RS - 4>();
-            const T *sn = ring + (size_t)s2 * SLOT;
-            const T *sb = ring + (size_t)s1 * SLOT + 32 * 4;
-            const T *sh = wring + (size_t)s1 * SLOT + 2 * 32 * 4;   // halo of row y
-            T bv[4];
+        // coarse rows of the chunk; row y = ya + t sits in slot (t + 1) % RS,
+        // and t = J M + j with RS | M, so the slot is (j + 1) % RS
+        for (int yJ = ya; yJ < yb; yJ += M) {
+            T acc = (T)0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { Pn[q] = sn[q]; bv[q] = sb[q]; }
-            // refill the slot of row y - 2 (consumed) with row ya - 1 + t + RS - 1
-            fetch(t + RS - 1, sf);
-            advance(s1);
-            advance(s2);
-            advance(sf);
-            // left / right neighbours across lanes, and beyond the strip
-            T left = __shfl_up_sync(FULLMASK, P0[3], 1), right = __shfl_down_sync(FULLMASK, P0[0], 1);
-            if (lane == 0) left = sh[3];
-            if (lane == 31) right = sh[4];
-            T rowD = (T)0;
-            if (!per_y && y == 0) rowD += (bcmask & 4) ? (T)1 : (T)-1;
-            if (!per_y && y == ny - 1) rowD += (bcmask & 8) ? (T)1 : (T)-1;
-            T rowsum = (T)0;
-            if (coldom) {                                      // all 4 columns: nx % 4 == 0
+            for (int j = 0; j < M; ++j) {
+                const int y = yJ + j;
+                if (y < yb) {                                // warp-uniform
+                    cp_async_wait<RS - 4>();                 // row y + 1 has landed
+                    const T *sn = ring + ((j + 2) % RS) * SLOT;
+                    const T *sb = ring + ((j + 1) % RS) * SLOT + 32 * 4;
+                    const T *sh = wring + ((j + 1) % RS) * SLOT + 2 * 32 * 4;   // halo of row y
+                    T bv[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const T lf = q == 0 ? left : P0[q - 1], rt = q == 3 ? right : P0[q + 1];
-                    // neighbour sum in the order of nb_sum (west, east, south, north);
-                    // a neighbour outside the domain was loaded as 0, so adding it is exact
-                    const T s = ((lf + rt) + Pm[q]) + Pn[q];
-                    const T r = bv[q] - (s - (colD[q] + rowD) * P0[q]);
-                    rowsum += r;
-                    r2 = fma(r, r, r2);
-                    ps += P0[q];
-                    p2 = fma(P0[q], P0[q], p2);
+                    for (int q = 0; q < 4; ++q) { Pn[q] = sn[q]; bv[q] = sb[q]; }
+                    // left / right neighbours across lanes, and beyond the strip
+                    T left = __shfl_up_sync(FULLMASK, P0[3], 1), right = __shfl_down_sync(FULLMASK, P0[0], 1);
+                    if (lane == 0) left = sh[3];
+                    if (lane == 31) right = sh[4];
+                    // refill the slot of row y - 2 (consumed) with row y + RS - 2
+                    fetch(y + RS - 2, (j + RS - 1) % RS);
+                    // diagonal: the south / north faces only change it on the
+                    // domain's first and last rows (uniform branch)
+                    T dg[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dg[q] = colD[q];
+                    if (!per_y && (y == 0 || y == ny - 1)) {
+                        T rowD = (T)0;
+                        if (y == 0) rowD += dS;
+                        if (y == ny - 1) rowD += dN;
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) dg[q] = colD[q] + rowD;
+                    }
+                    T rowsum = (T)0;
+                    if (coldom) {                            // all 4 columns: nx % 4 == 0
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const T lf = q == 0 ? left : P0[q - 1], rt = q == 3 ? right : P0[q + 1];
+                            // neighbour sum in the order of nb_sum (west, east, south, north);
+                            // a neighbour outside the domain was loaded as 0, so adding it is exact
+                            const T s = ((lf + rt) + Pm[q]) + Pn[q];
+                            const T r = bv[q] - (s - dg[q] * P0[q]);
+                            rowsum += r;
+                            r2 = fma(r, r, r2);
+                            ps += P0[q];
+                            // sum p^2 feeds only the single-precision inner control
+                            // (the FP64 controls read ||r|| and sum p)
+                            if (sizeof(T) == 4) p2 = fma(P0[q], P0[q], p2);
+                        }
+                    }
+                    acc += rowsum;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) { Pm[q] = P0[q]; P0[q] = Pn[q]; }
                 }
             }
-            acc += rowsum;
-            // end of a coarse row: combine the m/4 lanes of each coarse column
-            if (((y + 1) & (m - 1)) == 0 || y == ny - 1) {
-                T v = acc;
-                for (int o = 1; o < gl; o <<= 1) v += __shfl_xor_sync(FULLMASK, v, o);
-                const int I = cx >> lm;
-                if ((lane & (gl - 1)) == 0 && coldom && I < ncx) rc[(size_t)(y >> lm) * ncx + I] = v;
-                acc = (T)0;
-            }
+            // end of the coarse row: combine the m/4 lanes of each coarse column
+            T v = acc;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) { Pm[q] = P0[q]; P0[q] = Pn[q]; }
+            for (int o = 1; o < GL; o <<= 1) v += __shfl_xor_sync(FULLMASK, v, o);
+            const int I = cx >> LM;
+            if ((lane & (GL - 1)) == 0 && coldom && I < ncx) rc[(size_t)(yJ >> LM) * ncx + I] = v;
         }
         cp_async_wait<0>();
     }
