@@ -694,13 +694,14 @@ static int launch_restrict_stream(ism_ctx *ctx, const T *p, const T *b, T *rc, c
 }
 
 // Residual, restriction and norm partials.  Rows of whole 16-byte groups
-// (nx % 4 == 0): the streaming pass (ism_restrict_stream.cuh); otherwise one
-// CTA per coarse cell.  *nblk: the number of CTAs, i.e. of norm partials.
+// (nx % 4 == 0; along a periodic x axis whole 128-column strips): the
+// streaming pass (ism_restrict_stream.cuh); otherwise one CTA per coarse
+// cell.  *nblk: the number of CTAs, i.e. of norm partials.
 template <typename T>
 static ism_status launch_resid(ism_ctx *ctx, const T *p, const T *b, T *rc, const int *skip,
                                int ctl_mode = -1, unsigned long long cond = 0, int *nblk = nullptr)
 {
-    if (ctx->nx % 4 == 0) {
+    if (ctx->nx % 4 == 0 && (!(ctx->bcmask & ISM_PER_X) || ctx->nx % SRW == 0)) {
         int grid = 0;
         if (ctx->m == 8) grid = launch_restrict_stream<T, 8>(ctx, p, b, rc, skip, ctl_mode, cond);
         else if (ctx->m == 16) grid = launch_restrict_stream<T, 16>(ctx, p, b, rc, skip, ctl_mode, cond);

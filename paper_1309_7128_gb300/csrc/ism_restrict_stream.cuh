@@ -13,8 +13,9 @@
 // the coarse row the m/4 lanes of each coarse column combine their sums by a
 // fixed butterfly and one of them writes the block sum.  The left and right
 // neighbours of the strip's outer columns come through the ring as well
-// (lanes 0 and 31 copy one more 16-byte group of p each).
-// Cells outside the domain are 0 and not counted; along a periodic axis the
+// (lanes 0 and 31 copy one more 16-byte group of p each; the other lanes
+// copy zeros into a sink, so that no row takes a divergent branch).
+// Cells outside the domain are 0 and add exactly 0; along a periodic axis the
 // loads wrap (index mod n).  The pass reads 8 (FP32) or 16 (FP64) bytes per
 // cell and writes one value per coarse cell.
 #pragma once
@@ -28,7 +29,8 @@ struct RestrictShape {
     static constexpr int PIECES = 4 * (int)sizeof(T) / 16;          // 16-byte pieces per lane and row
     static constexpr int RS = 8;                                     // ring rows (divides m)
     static constexpr int SLOT = 2 * 32 * 4 + 8;                      // p, b of 32 lanes, 2 halo groups
-    static constexpr size_t smem = (size_t)RR_NW * RS * SLOT * sizeof(T);
+    static constexpr int WARP = RS * SLOT + 32 * 4;                  // + a sink for the halo copies of lanes 1..30
+    static constexpr size_t smem = (size_t)RR_NW * WARP * sizeof(T);
 };
 
 // M = m (8, 16 or 32): the loop over the m rows of a coarse row is unrolled,
@@ -47,8 +49,8 @@ k_restrict_stream(const T *__restrict__ p, const T *__restrict__ b, T *__restric
     if (skip && *skip) return;                               // the whole grid
     extern __shared__ __align__(16) unsigned char rr_raw[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    // ring of this warp: [RS] slots of p [32 lanes][4], b [32][4], halo [2][4]
-    T *wring = reinterpret_cast<T *>(rr_raw) + (size_t)w * RS * SLOT;
+    // ring of this warp: [RS] slots of p [32 lanes][4], b [32][4], halo [2][4]; then the sink
+    T *wring = reinterpret_cast<T *>(rr_raw) + (size_t)w * S::WARP;
     T *ring = wring + lane * 4;
     const int task = blockIdx.x * RR_NW + w;
     const bool active = task < ntask;                        // warp-uniform
@@ -72,7 +74,11 @@ k_restrict_stream(const T *__restrict__ p, const T *__restrict__ b, T *__restric
         const int hx = lane == 0 ? x0 - 4 : x0 + SRW;
         const bool hin = hlane && ((unsigned)hx < (unsigned)nx || per_x);
         const T *hcol = p + (hin ? (per_x ? wrap_mod(hx, nx) : hx) : 0);
-        T *hring = wring + 2 * 32 * 4 + (lane == 0 ? 0 : 4);
+        // every lane issues the halo copy (no divergent branch per row): lanes 0
+        // and 31 into the slot's halo groups, the others 16 zero bytes into
+        // their own place in the sink, which nothing reads
+        T *hring = hlane ? wring + 2 * 32 * 4 + (lane == 0 ? 0 : 4) : wring + RS * SLOT + lane * 4;
+        const int hstride = hlane ? SLOT : 0;
 
         // copies of row y into ring slot `slot` (zeros outside the domain)
         auto fetch = [&](int y, int slot) {
@@ -89,11 +95,9 @@ k_restrict_stream(const T *__restrict__ p, const T *__restrict__ b, T *__restric
                 cp_async16(sl + c * E16, pcol + roff + c * E16, nb);
                 cp_async16(sl + 32 * 4 + c * E16, bcol + roff + c * E16, nb);
             }
-            if (hlane) {
-                const int nh = rowin && hin ? 16 : 0;
+            const int nh = rowin && hin ? 16 : 0;
 #pragma unroll
-                for (int c = 0; c < PIECES; ++c) cp_async16(hring + slot * SLOT + c * E16, hcol + roff + c * E16, nh);
-            }
+            for (int c = 0; c < PIECES; ++c) cp_async16(hring + slot * hstride + c * E16, hcol + roff + c * E16, nh);
             cp_async_commit();
         };
         // per-column divisor part (W / E faces) for diag = 4 + column part + row part
@@ -137,6 +141,11 @@ k_restrict_stream(const T *__restrict__ p, const T *__restrict__ b, T *__restric
                     T left = __shfl_up_sync(FULLMASK, P0[3], 1), right = __shfl_down_sync(FULLMASK, P0[0], 1);
                     if (lane == 0) left = sh[3];
                     if (lane == 31) right = sh[4];
+                    // a lane beyond the east wall holds zeros; with a zero west
+                    // neighbour as well its residuals are exactly 0, so every lane
+                    // accumulates without a branch (a periodic x axis takes this
+                    // pass only when its strips are whole, nx % 128 == 0)
+                    if (!coldom) left = (T)0;
                     // refill the slot of row y - 2 (consumed) with row y + RS - 2
                     fetch(y + RS - 2, (j + RS - 1) % RS);
                     // diagonal: the south / north faces only change it on the
@@ -152,21 +161,19 @@ k_restrict_stream(const T *__restrict__ p, const T *__restrict__ b, T *__restric
                         for (int q = 0; q < 4; ++q) dg[q] = colD[q] + rowD;
                     }
                     T rowsum = (T)0;
-                    if (coldom) {                            // all 4 columns: nx % 4 == 0
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const T lf = q == 0 ? left : P0[q - 1], rt = q == 3 ? right : P0[q + 1];
-                            // neighbour sum in the order of nb_sum (west, east, south, north);
-                            // a neighbour outside the domain was loaded as 0, so adding it is exact
-                            const T s = ((lf + rt) + Pm[q]) + Pn[q];
-                            const T r = bv[q] - (s - dg[q] * P0[q]);
-                            rowsum += r;
-                            r2 = fma(r, r, r2);
-                            ps += P0[q];
-                            // sum p^2 feeds only the single-precision inner control
-                            // (the FP64 controls read ||r|| and sum p)
-                            if (sizeof(T) == 4) p2 = fma(P0[q], P0[q], p2);
-                        }
+                    for (int q = 0; q < 4; ++q) {
+                        const T lf = q == 0 ? left : P0[q - 1], rt = q == 3 ? right : P0[q + 1];
+                        // neighbour sum in the order of nb_sum (west, east, south, north);
+                        // a neighbour outside the domain was loaded as 0, so adding it is exact
+                        const T s = ((lf + rt) + Pm[q]) + Pn[q];
+                        const T r = bv[q] - (s - dg[q] * P0[q]);
+                        rowsum += r;
+                        r2 = fma(r, r, r2);
+                        ps += P0[q];
+                        // sum p^2 feeds only the single-precision inner control
+                        // (the FP64 controls read ||r|| and sum p)
+                        if (sizeof(T) == 4) p2 = fma(P0[q], P0[q], p2);
                     }
                     acc += rowsum;
 #pragma unroll

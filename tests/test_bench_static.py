@@ -1,11 +1,13 @@
-"""Static check of bench.py on CPU: every name a function of the benchmark
-reads is bound somewhere it can see (module level, its arguments, its own
-assignments and imports, or builtins).  The GPU legs of the benchmark only
-run on a GPU, so a missing import there would otherwise surface only when
-the benchmark is timed."""
+"""Static check of the measurement scripts on CPU (bench.py and the timing
+helpers of the package): every name a function reads is bound somewhere it
+can see (module level, its arguments, its own assignments and imports, or
+builtins).  Their GPU legs only run on a GPU, so a missing import there would
+otherwise surface only when they are timed."""
 import ast
 import builtins
 import os
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -48,8 +50,10 @@ def _check(fn, outer, missing):
             _check(f, local, missing)
 
 
-def test_bench_functions_read_only_bound_names():
-    tree = ast.parse(open(os.path.join(ROOT, "bench.py")).read())
+@pytest.mark.parametrize("path", ["bench.py", "paper_1309_7128_gb300/timepass.py",
+                                  "paper_1309_7128_gb300/workloads.py"])
+def test_functions_read_only_bound_names(path):
+    tree = ast.parse(open(os.path.join(ROOT, path)).read())
     module = set(dir(builtins)) | {"__file__", "__name__"}
     for node in tree.body:
         if not isinstance(node, (ast.FunctionDef, ast.ClassDef)):
