@@ -635,8 +635,6 @@ ism_status ism_leave(ism_ctx *ctx)
 
 static inline dim3 row_grid(int nx, int ny, int threads) { return dim3((nx + threads - 1) / threads, ny); }
 
-static inline int coarse_threads(int ncx) { return std::min(256, ((ncx + 31) / 32) * 32); }
-
 // e_c = A_c^+ r_c.  FUSED (single precision inside the cycle): r_c is read as
 // the sum of the 4 partial block sums and the x-interpolated rows G are made.
 template <typename T, bool FUSED>
@@ -779,12 +777,6 @@ static ism_status make_plans(ism_ctx *ctx)
             ISM_CUDA_TRY(cudaMemcpy(P.edge, e.data(), e.size() * sizeof(int2), cudaMemcpyHostToDevice));
         }
     return ISM_OK;
-}
-
-static inline int sweep_nblk(ism_ctx *ctx, int K, bool resid)
-{
-    const SweepPlan &P = sweep_plan(ctx, K, resid);
-    return P.gx * P.gy;
 }
 
 // Interior and edge launches of one pass run concurrently: the edge launch
@@ -1467,14 +1459,16 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
     // nearly independent of nu: larger nu amortises the fixed part.  Mixed
     // candidates {nu, sweeps per pass, stream}: the streaming middle passes
     // (stream = 1, 4 sweeps per pass) win on grids larger than L2.
-    static const int cand_mixed[][3] = {{8, 4, 0},  {8, 8, 0},   {16, 8, 0}, {24, 8, 0}, {32, 8, 0},
-                                        {48, 8, 0}, {64, 8, 0},  {96, 8, 0}, {128, 8, 0}, {16, 4, 0},
-                                        {32, 4, 1}, {64, 4, 1}, {128, 4, 1}};
-    static const int cand_fp64[][3] = {{8, 4, 0}, {16, 4, 0}, {32, 4, 0}, {48, 4, 0}, {64, 4, 0}};
+    static const int cand_mixed[][3] = {{8, 4, 0},   {8, 8, 0},   {16, 8, 0},  {24, 8, 0}, {32, 8, 0},
+                                        {48, 8, 0},  {64, 8, 0},  {96, 8, 0},  {128, 8, 0}, {192, 8, 0},
+                                        {256, 8, 0}, {16, 4, 0},  {32, 4, 1},  {64, 4, 1}, {128, 4, 1}};
+    static const int cand_fp64[][3] = {{8, 4, 0}, {16, 4, 0}, {32, 4, 0}, {48, 4, 0}, {64, 4, 0}, {96, 4, 0},
+                                       {128, 4, 0}};
     // then, for the mixed winner, the inner stopping factor of the refinement
     static const double inner_tols[] = {1e-4, 1e-2};
     const int (*cand)[3] = ctx->prec == ISM_MIXED ? cand_mixed : cand_fp64;
-    const int ncand = ctx->prec == ISM_MIXED ? 13 : 5;
+    const int ncand = ctx->prec == ISM_MIXED ? (int)(sizeof(cand_mixed) / sizeof(cand_mixed[0]))
+                                             : (int)(sizeof(cand_fp64) / sizeof(cand_fp64[0]));
     const int ntol = ctx->prec == ISM_MIXED ? 2 : 0;
     const ism_options saved = ctx->opt;
     double *p = nullptr;
