@@ -337,8 +337,7 @@ def run_ours(args):
     # ---- timed region: K projection steps, L2 flushed before each
     gpu_id = getattr(torch.cuda.get_device_properties(dev), "uuid", None)
     sampler = ClockSampler(f"GPU-{gpu_id}" if gpu_id else str(local))
-    _, cyc0, launches0 = ism.ism_last_counts(ctx)
-    launches0 = ism.ism_last_counts(ctx)[2]
+    launches0 = ism.ism_last_counts(ctx)[2]          # cumulative launch counter of the context
     per_step, cycles, outers, relres = [], [], [], []
     sampler.start()
     barrier(world)

@@ -245,6 +245,17 @@ ism_status ism_residual_restrict_noalloc(int nx, int ny, int coarsen, const int 
                                          const double *p, const double *b, double *rc,
                                          double *norms, void *stream);
 
+/* ism_residual_norms -- norms of the residual r = rhs - A_f p of an FP64
+ * iterate, in FP64: *l2 = ||r||_2 (the solver's stopping quantity, relative
+ * to ||rhs||_2 there) and *maxabs = max |r| (the paper's own criterion, an
+ * absolute maximum norm, Sec. 4.3.1; a non-finite residual gives +inf).
+ * Any context precision.  rhs, p: device, nx*ny doubles, row-major, read
+ * only, used as given (an all-Neumann solve removes the mean of its
+ * right-hand side first: pass the mean-free rhs to measure the equations it
+ * solved).  l2, maxabs: host, either may be NULL, not both (ISM_ERR_ARG).
+ * Ordered on the context's stream like ism_solve; synchronises. */
+ism_status ism_residual_norms(ism_ctx *ctx, const double *rhs, const double *p, double *l2, double *maxabs);
+
 /* e_c = A_c^+ r_c (exact coarse solve on the mean-free subspace when no
  * face is Dirichlet-0); rc, ec: device, ceil(ny/m)*ceil(nx/m) values of T. */
 ism_status ism_coarse_solve(ism_ctx *ctx, const void *rc, void *ec);

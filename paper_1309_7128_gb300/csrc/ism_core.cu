@@ -171,6 +171,37 @@ static inline dim3 refine_grid(int nx, int ny)
     return dim3((nx / 4 + RF_THREADS - 1) / RF_THREADS, (ny + RF_ROWS - 1) / RF_ROWS);
 }
 
+// Norms of the residual r = rhs - A_f p (FP64) of a given iterate: per block
+// the sum of r^2 (fixed order) and max |r| (a non-finite residual counts as
+// +inf), written to partials[blk] and partials[nblk + blk].  Grid
+// (ceil(nx/256), ny).
+__global__ void __launch_bounds__(256) k_resnorms(const double *__restrict__ p, const double *__restrict__ b,
+                                                  double *partials, int nx, int ny, int bcmask)
+{
+    const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+    double r2 = 0.0, rm = 0.0;
+    if (i < nx) {
+        const size_t idx = (size_t)j * nx + i;
+        const double s = nb_sum<double>([&](long long k) -> double { return p[k]; }, (long long)idx, i, j, nx, ny,
+                                        bcmask);
+        const double r = b[idx] - (s - (double)diag_count(i, j, nx, ny, bcmask) * p[idx]);
+        r2 = r * r;
+        rm = isfinite(r) ? fabs(r) : INFINITY;
+    }
+    __shared__ double mx[8];
+    double m = rm;
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(FULLMASK, m, o));
+    if ((threadIdx.x & 31) == 0) mx[threadIdx.x >> 5] = m;
+    const int nblk = gridDim.x * gridDim.y, bid = blockIdx.y * gridDim.x + blockIdx.x;
+    double v[1] = {r2};
+    block_partials<1>(v, partials, nblk, bid);      // its barriers also publish mx[]
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t = fmax(t, mx[k]);
+        partials[(size_t)nblk + bid] = t;
+    }
+}
+
 // out = in - mean (mean of the final iterate when all faces are Neumann);
 // zeros when the right-hand side vanished.  in_alt replaces in when st->c64.
 __global__ void k_finalize(const double *in, const double *in_alt, double *out, long long n,
@@ -1354,6 +1385,28 @@ extern "C" ism_status ism_residual_restrict(ism_ctx *ctx, const void *p, const v
         norms[0] = sqrt(r2);
         norms[1] = ps;
     }
+    return ism_leave(ctx);
+}
+
+extern "C" ism_status ism_residual_norms(ism_ctx *ctx, const double *rhs, const double *p, double *l2,
+                                         double *maxabs)
+{
+    if (!ctx || !rhs || !p || (!l2 && !maxabs)) return ISM_ERR_ARG;
+    TRY(ism_enter(ctx));
+    const dim3 g = row_grid(ctx->nx, ctx->ny, 256);
+    k_resnorms<<<g, 256, 0, ctx->ws>>>(p, rhs, ctx->partials, ctx->nx, ctx->ny, ctx->bcmask);
+    ISM_LAUNCH_CHECK(ctx);
+    const int nb = (int)(g.x * g.y);
+    std::vector<double> part((size_t)2 * nb);
+    ISM_CUDA_TRY(cudaMemcpyAsync(part.data(), ctx->partials, part.size() * 8, cudaMemcpyDeviceToHost, ctx->ws));
+    ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+    double r2 = 0.0, rm = 0.0;
+    for (int k = 0; k < nb; ++k) {
+        r2 += part[k];
+        rm = std::max(rm, part[(size_t)nb + k]);
+    }
+    if (l2) *l2 = sqrt(r2);
+    if (maxabs) *maxabs = rm;
     return ism_leave(ctx);
 }
 

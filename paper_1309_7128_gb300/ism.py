@@ -54,6 +54,7 @@ _SIGS = {
     "ism_last_counts": (_I, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "ism_smooth": (_I, [_VP, _VP, _VP, _I]),
     "ism_residual_restrict": (_I, [_VP, _VP, _VP, _VP, C.POINTER(C.c_double)]),
+    "ism_residual_norms": (_I, [_VP, _VP, _VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "ism_coarse_solve": (_I, [_VP, _VP, _VP]),
     "ism_prolong_add": (_I, [_VP, _VP, _VP]),
     "ism_set_flow": (_I, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_double), _VP, _D]),
@@ -216,6 +217,14 @@ def ism_time_pass(ctx, p, b, sweeps, reps):
     us = C.c_double(0.0)
     s = lib().ism_time_pass(ctx.handle, _ptr(p), _ptr(b), int(sweeps), int(reps), C.byref(us))
     return s, us.value
+
+
+def ism_residual_norms(ctx, rhs, p):
+    """Returns (status, ||rhs - A_f p||_2, max |rhs - A_f p|) for FP64 device tensors."""
+    l2 = C.c_double(0.0)
+    mx = C.c_double(0.0)
+    s = lib().ism_residual_norms(ctx.handle, _ptr(rhs), _ptr(p), C.byref(l2), C.byref(mx))
+    return s, l2.value, mx.value
 
 
 def ism_coarse_solve(ctx, rc, ec):

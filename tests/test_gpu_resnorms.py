@@ -1,0 +1,67 @@
+"""ism_residual_norms (the L2 norm and the maximum norm of b - A_f p) against
+the oracle's residual, on grids with ragged edges, every face mix and
+periodic axes; after a solve it reproduces the solver's own stopping
+quantity; non-finite residuals are reported as such."""
+import numpy as np
+import pytest
+
+import oracle as O
+from synth.inputs import random_field, smooth_rhs
+from tests.conftest import ALL_BCS, PERIODIC_BCS
+from tests.gpu_util import dev64, ensure_built, ism, setup
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    ensure_built()
+
+
+@pytest.mark.parametrize("nx,ny,m", [(160, 96, 32), (200, 136, 16), (256, 192, 32)])
+@pytest.mark.parametrize("bc", ALL_BCS + PERIODIC_BCS)
+@pytest.mark.parametrize("prec", [ism.ISM_FP64, ism.ISM_MIXED])
+def test_residual_norms_match_oracle(nx, ny, m, bc, prec):
+    if (bc[0] == 2 and (nx % m or nx // m < 4)) or (bc[2] == 2 and (ny % m or ny // m < 4)):
+        pytest.skip("periodic axes are multiples of m with at least 4 coarse cells")
+    if prec == ism.ISM_MIXED and nx % 4:
+        pytest.skip("the mixed path needs nx % 4 == 0")
+    p = random_field(nx, ny, 21)
+    b = random_field(nx, ny, 22)
+    ctx = setup(nx, ny, m, bc, prec=prec)
+    s, l2, mx = ism.ism_residual_norms(ctx, dev64(b), dev64(p))
+    assert s == ism.ISM_OK
+    r = O.residual(p, b, bc)
+    assert abs(l2 - np.linalg.norm(r)) <= 1e-12 * np.linalg.norm(r)
+    assert abs(mx - np.abs(r).max()) <= 1e-13 * np.abs(r).max()
+
+
+@pytest.mark.parametrize("bc", [(0, 0, 0, 0), (0, 1, 0, 0), (2, 2, 0, 0)])
+def test_residual_norms_reproduce_the_solver_stopping_quantity(bc):
+    nx, ny, m = 256, 192, 32
+    b = smooth_rhs(nx, ny, 7) + (0.0 if O.is_singular(bc) else 1e-6)
+    if O.is_singular(bc):
+        b = b - b.mean()                                  # the equations the solver solves
+    ctx = setup(nx, ny, m, bc)
+    bd, pd = dev64(b), dev64(np.zeros((ny, nx)))
+    s, cyc, rel = ism.ism_solve(ctx, bd, pd, 1e-8, 100000)
+    assert s == ism.ISM_OK and rel <= 1e-8
+    s, l2, mx = ism.ism_residual_norms(ctx, bd, pd)
+    assert s == ism.ISM_OK
+    assert abs(l2 / np.linalg.norm(b) - rel) <= 1e-6 * rel
+    assert 0.0 < mx <= l2
+
+
+def test_residual_norms_report_non_finite_and_take_one_output():
+    nx, ny = 128, 64
+    ctx = setup(nx, ny, 16, (0, 0, 0, 0))
+    p = random_field(nx, ny, 3)
+    p[10, 20] = np.nan
+    s, l2, mx = ism.ism_residual_norms(ctx, dev64(random_field(nx, ny, 4)), dev64(p))
+    assert s == ism.ISM_OK and np.isnan(l2) and mx == np.inf
+    import ctypes as C
+    d = C.c_double(-1.0)
+    q = dev64(np.zeros((ny, nx)))
+    assert ism.lib().ism_residual_norms(ctx.handle, q.data_ptr(), q.data_ptr(), None, C.byref(d)) == ism.ISM_OK
+    assert d.value == 0.0
+    assert ism.lib().ism_residual_norms(ctx.handle, q.data_ptr(), q.data_ptr(), None, None) == ism.ISM_ERR_ARG
