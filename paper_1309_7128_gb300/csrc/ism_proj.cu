@@ -91,17 +91,18 @@ __global__ void k_predict_v(const float *__restrict__ u, const float *__restrict
     vs[(size_t)j * nx + i] = out;
 }
 
-// b = h (u_e - u_w + v_n - v_s) / dt in double; partial sums of b.
+// b = h (u_e - u_w + v_n - v_s) / dt in double; partial sums of b.  h_dt =
+// h / dt is formed once on the host: a double division per cell costs about
+// ten operations of this GPU's slow FP64 pipe.
 __global__ void k_divergence(const float *__restrict__ u, const float *__restrict__ v,
-                             double *__restrict__ b, int nx, int ny, double h, double dt,
-                             double *partials)
+                             double *__restrict__ b, int nx, int ny, double h_dt, double *partials)
 {
     const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
     double s = 0.0;
     if (i < nx) {
         const double du = (double)UA(i + 1, j) - (double)UA(i, j);
         const double dv = (double)VA(i, j + 1) - (double)VA(i, j);
-        const double val = h * (du + dv) / dt;
+        const double val = h_dt * (du + dv);
         b[(size_t)j * nx + i] = val;
         s = val;
     }
@@ -233,7 +234,7 @@ extern "C" ism_status proj_step(ism_ctx *ctx, float *u, float *v, float *p, doub
     h0.inv_n = 1.0 / (double)ctx->n;
     ISM_CUDA_TRY(cudaMemcpyAsync(ctx->st, &h0, offsetof(IsmState, hist), cudaMemcpyHostToDevice, ctx->ws));
     const dim3 dg((nx + 255) / 256, ny);
-    k_divergence<<<dg, 256, 0, ctx->ws>>>(ctx->us, ctx->vs, ctx->b64, nx, ny, ctx->h, dt, ctx->partials);
+    k_divergence<<<dg, 256, 0, ctx->ws>>>(ctx->us, ctx->vs, ctx->b64, nx, ny, ctx->h / dt, ctx->partials);
     ISM_LAUNCH_CHECK(ctx);
     k_ctl<<<1, 256, 0, ctx->ws>>>(ctx->st, ctx->partials, dg.x * dg.y, 1, 0 /*CTL_RHS_MEAN*/, 0);
     ISM_LAUNCH_CHECK(ctx);
