@@ -184,9 +184,10 @@ ism_status ism_solve(ism_ctx *ctx, const double *rhs, double *p, double tol,
  * stopping factor inner_tol) for this context by timing complete solves of
  * rhs (device, nx*ny doubles) from a zero initial guess over a fixed
  * candidate list; keeps the fastest candidate in the context's options and
- * copies it to *best (host, may be NULL).  No counterpart in the paper (its tile size and coarse tolerance
- * were tuned by hand, Sec. 4.1, 4.3.1).  Allocates one nx*ny double buffer
- * for the duration of the call.  Synchronises. */
+ * copies it to *best (host, may be NULL).  No counterpart in the paper (its
+ * tile size and coarse tolerance were tuned by hand, Sec. 4.1, 4.3.1).
+ * Allocates one nx*ny double buffer for the duration of the call.
+ * Synchronises. */
 ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, int max_cycles,
                         ism_options *best);
 
@@ -197,6 +198,16 @@ int ism_coarsening(const ism_ctx *ctx);
  * or per refinement iteration (mixed), starting with the initial guess.
  * hist: host array of cap doubles; returns the number of entries written. */
 int ism_last_history(const ism_ctx *ctx, double *hist, int cap);
+
+/* Right-hand side of the last ism_solve or proj_step.  With every face
+ * Neumann (or periodic) A_f is singular and A_f p = b is solvable only when
+ * sum(b) = 0; the solve removes the mean of b first (the paper is silent on
+ * this; its Neumann benchmarks have compatible data).  *mean_removed (host,
+ * may be NULL): that mean, 0 when a face is Dirichlet-0.  *incompatible
+ * (host, may be NULL): 1 when |sum(b)| > 1e-12 sum|b|, i.e. the removal
+ * changed the problem beyond rounding, else 0.  Not set by the batched
+ * solve. */
+ism_status ism_last_rhs(const ism_ctx *ctx, double *mean_removed, int *incompatible);
 
 /* Counters of the last solve (host, any may be NULL): refinement iterations
  * (mixed; 0 for FP64; coarse Gauss-Seidel iterations with cycle 1),

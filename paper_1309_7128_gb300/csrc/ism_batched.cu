@@ -167,7 +167,7 @@ __global__ void k_b_rhs(BDom *dom, const int2 *chunks, int mode, BState *bs)
     b_last_block(st, D.partials, D.nchunk, 1, mode == 0 ? CTL_RHS_MEAN : CTL_RHS_NORM, bs);
 }
 
-// FP64 refinement per problem (same arithmetic as k_refine, cells in chunks):
+// FP64 refinement per problem (the arithmetic of the single-problem refinement, cells in chunks):
 // UPDATE: only problems whose inner solve finished and which are not done.
 template <bool UPDATE>
 __global__ void k_b_refine(BDom *dom, const int2 *chunks, BState *bs)

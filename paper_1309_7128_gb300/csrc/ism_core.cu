@@ -46,24 +46,27 @@ __global__ void __launch_bounds__(256) k_ctl(IsmState *st, const double *partial
 
 // ================================================================ rhs preparation
 
-// partial sums of x (mode 0: sum x) or of (x - mean)^2 with y = x - mean (mode 1)
+// partial sums of x and |x| (mode 0) or of (x - mean)^2 with y = x - mean
+// (mode 1, second column 0)
 __global__ void k_rhs_stats(const double *__restrict__ x, double *__restrict__ y, long long n,
                             const IsmState *st, int mode, int sub_mean, double *partials)
 {
-    double s = 0.0;
+    double s = 0.0, sa = 0.0;
     const double mu = (mode == 1 && sub_mean) ? st->mean : 0.0;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         double v = x[i];
-        if (mode == 0) s += v;
-        else {
+        if (mode == 0) {
+            s += v;
+            sa += fabs(v);
+        } else {
             v -= mu;
             y[i] = v;
             s += v * v;
         }
     }
-    double v1[1] = {s};
-    block_partials<1>(v1, partials, gridDim.x, blockIdx.x);
+    double v2[2] = {s, sa};
+    block_partials<2>(v2, partials, gridDim.x, blockIdx.x);
 }
 
 // ================================================================ mixed-path outer kernels
@@ -1059,7 +1062,7 @@ ism_status ism_prepare_rhs(ism_ctx *ctx, const double *rhs)
     const int G = 4 * 152;
     k_rhs_stats<<<G, 256, 0, ctx->ws>>>(rhs, nullptr, ctx->n, ctx->st, 0, 0, ctx->partials);
     ISM_LAUNCH_CHECK(ctx);
-    TRY(launch_ctl(ctx, ctx->st, G, 1, CTL_RHS_MEAN));
+    TRY(launch_ctl(ctx, ctx->st, G, 2, CTL_RHS_MEAN));
     k_rhs_stats<<<G, 256, 0, ctx->ws>>>(rhs, ctx->b64, ctx->n, ctx->st, 1, ctx->singular, ctx->partials);
     ISM_LAUNCH_CHECK(ctx);
     return launch_ctl(ctx, ctx->st, G, 1, CTL_RHS_NORM);
@@ -1268,6 +1271,8 @@ ism_status ism_solve_internal(ism_ctx *ctx, double tol, int max_cycles)
     TRY(read_state(ctx));
     IsmState h = *ctx->st_host;
     const double bn = h.bnorm;
+    ctx->last_rhs_sum = h.rhs_sum;
+    ctx->last_rhs_l1 = h.rhs_l1;
     const int zr = h.zero_rhs, stt = h.status, dn = h.done;
     init_state(ctx, &h, tol, max_cycles);
     h.bnorm = bn;
@@ -1328,6 +1333,15 @@ extern "C" int ism_last_history(const ism_ctx *ctx, double *hist, int cap)
     if (cudaMemcpy(hist, ctx->st->hist, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
         return 0;
     return n;
+}
+
+extern "C" ism_status ism_last_rhs(const ism_ctx *ctx, double *mean_removed, int *incompatible)
+{
+    if (!ctx) return ISM_ERR_ARG;
+    const double sum = ctx->singular ? ctx->last_rhs_sum : 0.0;
+    if (mean_removed) *mean_removed = sum / (double)ctx->n;
+    if (incompatible) *incompatible = ctx->singular && fabs(sum) > 1e-12 * ctx->last_rhs_l1;
+    return ISM_OK;
 }
 
 extern "C" ism_status ism_last_counts(const ism_ctx *ctx, int *outer, int *cycles, long long *launches)

@@ -35,6 +35,8 @@ struct IsmState {
     double mean_e;     // mixed: mean of the inner iterate
     double r32norm;    // mixed: ||r|| of the current inner right-hand side
     double rin, enorm; // mixed: latest inner residual and iterate norms
+    double rhs_sum;    // sum of the right-hand side as given (before the mean is removed)
+    double rhs_l1;     // its L1 norm (0 where the preparation does not form it: batched)
     int c64;           // mixed: which FP64 buffer holds the outer iterate
     int skip_init;     // batched: 0 while a new inner solve still needs its first restriction
     int tc_fail;       // a tensor-core coarse solve gave up waiting for its MMAs
@@ -89,6 +91,7 @@ struct ism_ctx {
 
     // last solve
     int last_cycles, last_outer, last_status, last_nhist;
+    double last_rhs_sum, last_rhs_l1;   // right-hand side of the last ism_solve / proj_step
     double last_relres;
     long long launches;
     unsigned long long uid;    // unique per context (batched plan cache key)

@@ -106,7 +106,7 @@ __device__ __forceinline__ void block_partials(double (&v)[NQ], double *partials
 // ----------------------------------------------------------------- convergence control
 
 enum CtlMode {
-    CTL_RHS_MEAN = 0,   // S0 = sum b                  -> st->mean
+    CTL_RHS_MEAN = 0,   // S0 = sum b, S1 = sum |b|    -> st->mean, rhs_sum, rhs_l1
     CTL_RHS_NORM = 1,   // S0 = ||b - mean||^2          -> bnorm, zero_rhs, status
     CTL_FP64_INIT = 2,  // S0 = ||r||^2, S1 = sum p    -> hist[0], done?
     CTL_FP64_AFTER = 3, // same after one cycle         -> cycles++, hist, done?
@@ -134,6 +134,9 @@ __device__ __forceinline__ void ctl_reduce(const double *partials, int nblk, int
         }
         __syncthreads();
     }
+    if (t == 0)
+        for (int q = nq; q < ISM_NQ; ++q) S[q] = 0.0;   // columns this control point does not form
+    __syncthreads();
 }
 
 // Convergence bookkeeping of one control point (one thread).
@@ -142,6 +145,8 @@ __device__ __forceinline__ void ctl_decide(IsmState *st, const double *S, int mo
     switch (mode) {
     case CTL_RHS_MEAN:
         st->mean = S[0] * st->inv_n;
+        st->rhs_sum = S[0];
+        st->rhs_l1 = S[1];
         break;
     case CTL_RHS_NORM: {
         const double bn = sqrt(S[0]);

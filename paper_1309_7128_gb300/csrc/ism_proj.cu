@@ -91,23 +91,24 @@ __global__ void k_predict_v(const float *__restrict__ u, const float *__restrict
     vs[(size_t)j * nx + i] = out;
 }
 
-// b = h (u_e - u_w + v_n - v_s) / dt in double; partial sums of b.  h_dt =
+// b = h (u_e - u_w + v_n - v_s) / dt in double; partial sums of b and |b|.  h_dt =
 // h / dt is formed once on the host: a double division per cell costs about
 // ten operations of this GPU's slow FP64 pipe.
 __global__ void k_divergence(const float *__restrict__ u, const float *__restrict__ v,
                              double *__restrict__ b, int nx, int ny, double h_dt, double *partials)
 {
     const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
-    double s = 0.0;
+    double s = 0.0, sa = 0.0;
     if (i < nx) {
         const double du = (double)UA(i + 1, j) - (double)UA(i, j);
         const double dv = (double)VA(i, j + 1) - (double)VA(i, j);
         const double val = h_dt * (du + dv);
         b[(size_t)j * nx + i] = val;
         s = val;
+        sa = fabs(val);
     }
-    double v1[1] = {s};
-    block_partials<1>(v1, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
+    double v2[2] = {s, sa};
+    block_partials<2>(v2, partials, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x);
 }
 
 // v = v* - (dt/h) grad dp on the faces whose normal velocity is free
@@ -236,7 +237,7 @@ extern "C" ism_status proj_step(ism_ctx *ctx, float *u, float *v, float *p, doub
     const dim3 dg((nx + 255) / 256, ny);
     k_divergence<<<dg, 256, 0, ctx->ws>>>(ctx->us, ctx->vs, ctx->b64, nx, ny, ctx->h / dt, ctx->partials);
     ISM_LAUNCH_CHECK(ctx);
-    k_ctl<<<1, 256, 0, ctx->ws>>>(ctx->st, ctx->partials, dg.x * dg.y, 1, 0 /*CTL_RHS_MEAN*/, 0);
+    k_ctl<<<1, 256, 0, ctx->ws>>>(ctx->st, ctx->partials, dg.x * dg.y, 2, 0 /*CTL_RHS_MEAN*/, 0);
     ISM_LAUNCH_CHECK(ctx);
     k_rhs_stats<<<4 * 152, 256, 0, ctx->ws>>>(ctx->b64, ctx->b64, ctx->n, ctx->st, 1, ctx->singular, ctx->partials);
     ISM_LAUNCH_CHECK(ctx);

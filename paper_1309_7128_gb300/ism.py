@@ -55,6 +55,7 @@ _SIGS = {
     "ism_smooth": (_I, [_VP, _VP, _VP, _I]),
     "ism_residual_restrict": (_I, [_VP, _VP, _VP, _VP, C.POINTER(C.c_double)]),
     "ism_residual_norms": (_I, [_VP, _VP, _VP, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "ism_last_rhs": (_I, [_VP, C.POINTER(C.c_double), C.POINTER(C.c_int)]),
     "ism_coarse_solve": (_I, [_VP, _VP, _VP]),
     "ism_prolong_add": (_I, [_VP, _VP, _VP]),
     "ism_set_flow": (_I, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_double), _VP, _D]),
@@ -225,6 +226,14 @@ def ism_residual_norms(ctx, rhs, p):
     mx = C.c_double(0.0)
     s = lib().ism_residual_norms(ctx.handle, _ptr(rhs), _ptr(p), C.byref(l2), C.byref(mx))
     return s, l2.value, mx.value
+
+
+def ism_last_rhs(ctx):
+    """Returns (status, mean removed from the last right-hand side, incompatible flag)."""
+    mu = C.c_double(0.0)
+    flag = C.c_int(0)
+    s = lib().ism_last_rhs(ctx.handle, C.byref(mu), C.byref(flag))
+    return s, mu.value, bool(flag.value)
 
 
 def ism_coarse_solve(ctx, rc, ec):

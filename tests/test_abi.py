@@ -75,3 +75,4 @@ def test_null_context_is_rejected(L):
     assert L.ism_solve_batched(-1, None, None, None, 1e-8, 10, None, None) == ism.ISM_ERR_ARG
     d = C.c_double()
     assert L.ism_residual_norms(None, None, None, C.byref(d), C.byref(d)) == ism.ISM_ERR_ARG
+    assert L.ism_last_rhs(None, C.byref(d), None) == ism.ISM_ERR_ARG

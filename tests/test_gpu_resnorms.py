@@ -65,3 +65,41 @@ def test_residual_norms_report_non_finite_and_take_one_output():
     assert ism.lib().ism_residual_norms(ctx.handle, q.data_ptr(), q.data_ptr(), None, C.byref(d)) == ism.ISM_OK
     assert d.value == 0.0
     assert ism.lib().ism_residual_norms(ctx.handle, q.data_ptr(), q.data_ptr(), None, None) == ism.ISM_ERR_ARG
+
+
+@pytest.mark.parametrize("bc,shift", [((0, 0, 0, 0), 0.5), ((0, 0, 0, 0), 0.0), ((2, 2, 0, 0), 0.25),
+                                      ((0, 1, 0, 0), 0.5)])
+@pytest.mark.parametrize("prec", [ism.ISM_FP64, ism.ISM_MIXED])
+def test_last_rhs_reports_the_removed_mean_and_compatibility(bc, shift, prec):
+    nx, ny, m = 256, 192, 32
+    b = smooth_rhs(nx, ny, 9)
+    b = b - b.mean() + shift
+    ctx = setup(nx, ny, m, bc, prec=prec)
+    s, cyc, rel = ism.ism_solve(ctx, dev64(b), dev64(np.zeros((ny, nx))), 1e-8, 100000)
+    assert s == ism.ISM_OK and rel <= 1e-8
+    s, mean, flag = ism.ism_last_rhs(ctx)
+    assert s == ism.ISM_OK
+    if O.is_singular(bc):
+        assert abs(mean - b.mean()) <= 1e-12 * max(abs(b).mean(), 1e-300)
+        assert flag == (abs(b.sum()) > 1e-12 * abs(b).sum())
+        assert flag == (shift != 0.0)
+    else:
+        assert mean == 0.0 and not flag
+
+
+def test_last_rhs_after_a_projection_step():
+    """The divergence of a cavity predictor sums to zero up to rounding."""
+    from synth.inputs import smooth_velocity
+    nx = ny = 128
+    u, v = smooth_velocity(nx, ny, 4)
+    import torch
+    ud = torch.tensor(0.1 * u, dtype=torch.float32, device="cuda:0")
+    vd = torch.tensor(0.1 * v, dtype=torch.float32, device="cuda:0")
+    pd = torch.zeros((ny, nx), dtype=torch.float32, device="cuda:0")
+    ctx = setup(nx, ny, 16, (0, 0, 0, 0), prec=ism.ISM_MIXED)
+    cav = (ism.ISM_VEL_NOSLIP,) * 4
+    ism.check(ism.ism_set_flow(ctx, cav, (0, 0, 0, 1.0), None, 1.0))
+    ism.check(ism.ism_proj_tol(ctx, 1e-8, 100000, False))
+    ism.check(ism.proj_step(ctx, ud, vd, pd, 1e-4, 1e-2))
+    s, mean, flag = ism.ism_last_rhs(ctx)
+    assert s == ism.ISM_OK and not flag
