@@ -76,3 +76,13 @@ def test_null_context_is_rejected(L):
     d = C.c_double()
     assert L.ism_residual_norms(None, None, None, C.byref(d), C.byref(d)) == ism.ISM_ERR_ARG
     assert L.ism_last_rhs(None, C.byref(d), None) == ism.ISM_ERR_ARG
+
+
+def test_every_declared_function_has_a_binding():
+    """The ctypes table covers exactly the functions of include/ism.h, and each
+    has a Python function of the same name (ism_destroy runs from the context
+    wrapper's finaliser, ism_status_str behind status_str)."""
+    declared = set(ism.declared_functions())
+    assert declared == set(ism._SIGS)
+    wrapped = {n for n in dir(ism) if callable(getattr(ism, n))} | {"ism_destroy", "ism_status_str"}
+    assert declared <= wrapped, sorted(declared - wrapped)
