@@ -231,13 +231,13 @@ ism_status ism_residual_restrict(ism_ctx *ctx, const void *p, const void *b,
 
 /* ism_residual_restrict_noalloc -- the FP64 residual and restriction of
  * ism_residual_restrict for callers that must not allocate device memory
- * (a stream capture in progress, real-time loops that cannot take the
- * synchronisation of cudaMalloc/cudaFree, hosts whose device memory belongs
- * to their own arena).  The paper has no counterpart; this is a library
- * convenience.  It needs no context and allocates nothing, on the device or
- * the host: the per-block partial sums live in a fixed 768 KiB array
- * compiled into the library (held by every GPU that loads it until the
- * process exits).
+ * when they need it: real-time loops that cannot take the implicit device
+ * synchronisation of cudaMalloc/cudaFree, and hosts whose device memory is
+ * handed out by their own arena and may not be allocated behind its back.
+ * The paper has no counterpart; this is a library convenience.  It needs no
+ * context and allocates nothing, on the device or the host: the per-block
+ * partial sums live in a fixed 768 KiB array compiled into the library
+ * (held by every GPU that loads it until the process exits).
  *   nx, ny, coarsen, bc  as for ism_setup (bc: host, 4 ints);
  *                        ceil(nx/coarsen)*ceil(ny/coarsen) must be <= 32768, else
  *                        ISM_ERR_ARG (nothing launched).
@@ -246,12 +246,14 @@ ism_status ism_residual_restrict(ism_ctx *ctx, const void *p, const void *b,
  *   norms                device, 2 doubles: ||b - A_f p||_2 and sum(p).
  *   stream               cudaStream_t (NULL = legacy default stream); the
  *                        call is asynchronous on it.
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call uses the same array, so calls whose kernels overlap on the GPU
- * (different streams without ordering) race and give wrong results; calls
- * on one stream, or otherwise ordered, are safe.  Each call overwrites all
- * the entries it reads, so nothing needs clearing between calls. */
+ * The first call on each device (and the first after that device's context
+ * was re-created, e.g. by cudaDeviceReset) looks up the array's device
+ * address with cudaGetSymbolAddress; make that first call before any stream
+ * capture.  Every call uses the same array, so calls whose kernels overlap
+ * on the GPU (different streams without ordering) race and give wrong
+ * results; calls on one stream, or otherwise ordered, are safe.  Each call
+ * overwrites all the entries it reads, so nothing needs clearing between
+ * calls. */
 ism_status ism_residual_restrict_noalloc(int nx, int ny, int coarsen, const int bc[4],
                                          const double *p, const double *b, double *rc,
                                          double *norms, void *stream);

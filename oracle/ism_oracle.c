@@ -14,6 +14,14 @@
  * loops.  Build with -ffp-contract=off so that no multiply-add is fused on
  * any host.
  *
+ * Threads (OpenMP, when built with it): the row loops of the cell-wise
+ * operations may be split over threads.  Every cell's value is computed by
+ * one thread with the same arithmetic in the same order, and a row only
+ * writes its own cells: a Gauss-Seidel colour reads only cells of the other
+ * colour (fixed during that colour), every sum of the restriction belongs to
+ * one coarse cell.  Results are therefore bit-identical for any number of
+ * threads; or_set_threads(1) gives the sequential program.
+ *
  * Conventions (Sec. 2.3, Sec. 3.3):
  *   cell-centred field p[j*nx + i], cell (i, j), i along x, j along y;
  *   face order bc[0..3] = west, east, south, north;
@@ -39,6 +47,34 @@
 #include <stddef.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Number of threads for the row loops (n <= 0: all host cores); returns the
+   count in use (1 without OpenMP). */
+int or_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+int or_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* row loop split over threads (each iteration writes its own row) */
+#define ROWS_PARALLEL _Pragma("omp parallel for schedule(static)")
 
 #define F_W 0
 #define F_E 1
@@ -77,6 +113,7 @@ static double cell_flux_sum(int nx, int ny, const int *bc, const double *p,
 /* out = A_f p */
 void or_apply_af(int nx, int ny, const int *bc, const double *p, double *out)
 {
+    ROWS_PARALLEL
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
             AT(out, i, j) = cell_flux_sum(nx, ny, bc, p, i, j);
@@ -86,6 +123,7 @@ void or_apply_af(int nx, int ny, const int *bc, const double *p, double *out)
 void or_residual(int nx, int ny, const int *bc, const double *p,
                  const double *b, double *r)
 {
+    ROWS_PARALLEL
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
             AT(r, i, j) = AT(b, i, j) - cell_flux_sum(nx, ny, bc, p, i, j);
@@ -104,6 +142,7 @@ void or_residual(int nx, int ny, const int *bc, const double *p,
 static void gs_colour(int nx, int ny, const int *bc, double *p, const double *b,
                       int colour)
 {
+    ROWS_PARALLEL
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             if (((i + j) & 1) != colour) continue;
@@ -143,6 +182,7 @@ static int block_end(int I, int n, int m) { return (I + 1) * m < n ? (I + 1) * m
 void or_restrict(int nx, int ny, int m, const double *r, double *rc)
 {
     int ncx = ncoarse(nx, m), ncy = ncoarse(ny, m);
+    ROWS_PARALLEL
     for (int J = 0; J < ncy; ++J)
         for (int I = 0; I < ncx; ++I) {
             double s = 0.0;
@@ -220,6 +260,7 @@ static double bilinear_at(int nx, int ny, int m, const int *bc, const double *q,
 /* p += P q (bilinear prolongation with the same rule, Sec. 3.3) */
 void or_prolong_add(int nx, int ny, int m, const int *bc, const double *q, double *p)
 {
+    ROWS_PARALLEL
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
             AT(p, i, j) += bilinear_at(nx, ny, m, bc, q, i, j);
@@ -229,6 +270,7 @@ void or_prolong_add(int nx, int ny, int m, const int *bc, const double *q, doubl
 void or_prolong_const_add(int nx, int ny, int m, const double *q, double *p)
 {
     int ncx = ncoarse(nx, m);
+    ROWS_PARALLEL
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
             AT(p, i, j) += q[(size_t)(j / m) * ncx + (i / m)];
@@ -397,6 +439,7 @@ static float cell_flux_sum_f(int nx, int ny, const int *bc, const float *p,
 void or_residual_f32(int nx, int ny, const int *bc, const float *p,
                      const float *b, float *r)
 {
+    ROWS_PARALLEL
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
             AT(r, i, j) = AT(b, i, j) - cell_flux_sum_f(nx, ny, bc, p, i, j);
@@ -405,6 +448,7 @@ void or_residual_f32(int nx, int ny, const int *bc, const float *p,
 static void gs_colour_f(int nx, int ny, const int *bc, float *p, const float *b,
                         int colour)
 {
+    ROWS_PARALLEL
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             if (((i + j) & 1) != colour) continue;
@@ -436,6 +480,7 @@ void or_rbgs_sweep_f32(int nx, int ny, const int *bc, float *p, const float *b)
 void or_restrict_f32(int nx, int ny, int m, const float *r, double *rc)
 {
     int ncx = ncoarse(nx, m), ncy = ncoarse(ny, m);
+    ROWS_PARALLEL
     for (int J = 0; J < ncy; ++J)
         for (int I = 0; I < ncx; ++I) {
             double s = 0.0;
@@ -448,6 +493,7 @@ void or_restrict_f32(int nx, int ny, int m, const float *r, double *rc)
 
 void or_prolong_add_f32(int nx, int ny, int m, const int *bc, const double *q, float *p)
 {
+    ROWS_PARALLEL
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
             AT(p, i, j) = AT(p, i, j) + (float)bilinear_at(nx, ny, m, bc, q, i, j);

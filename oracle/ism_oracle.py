@@ -47,7 +47,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle's C part in place (gcc, no fused multiply-add)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math",
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                                "-fPIC", "-shared", "-std=c99", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
@@ -75,16 +75,32 @@ def lib():
                 "or_predictor": [i, i, d, d, d, _ip, _dp, _dp, d, _dp, _dp, _dp, _dp, _dp],
                 "or_divergence": [i, i, d, d, _dp, _dp, _dp],
                 "or_correct": [i, i, d, d, _ip, _dp, _dp, _dp, _dp],
+                "or_set_threads": [i],
+                "or_get_threads": [],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
                 f.argtypes = args
-                f.restype = C.c_int if name in ("or_coarse_operator", "or_coarse_gs4") else None
+                f.restype = C.c_int if name in ("or_coarse_operator", "or_coarse_gs4", "or_set_threads",
+                                                "or_get_threads") else None
+            # sequential unless a caller asks for threads (set_threads): the
+            # test grids are small, where thread start-up costs more than it saves
+            L.or_set_threads(1)
             _lib = L
     return _lib
 
 
 BC_NEUMANN, BC_DIRICHLET0, BC_PERIODIC = 0, 1, 2
+
+
+def set_threads(n: int) -> int:
+    """Threads of the C part's row loops (n <= 0: all host cores); returns the
+    count in use.  Results are bit-identical for any count."""
+    return int(lib().or_set_threads(int(n)))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
 
 
 def _faces(k):

@@ -317,7 +317,7 @@ extern "C" ism_status proj_step_adjoint(ism_ctx *ctx, const float *u, const floa
     ISM_CUDA_TRY(cudaMemcpyAsync(ctx->st, &h0, offsetof(IsmState, hist), cudaMemcpyHostToDevice, ctx->ws));
     TRY(ism_prepare_rhs(ctx, ctx->b64));
     ISM_CUDA_TRY(cudaMemsetAsync(ctx->p64[0], 0, (size_t)ctx->n * 8, ctx->ws));
-    ism_status st = ism_solve_internal(ctx, ctx->proj_tol, ctx->proj_max_cycles);
+    ism_status st = ism_solve_internal(ctx, ctx->proj_tol, ctx->proj_max_cycles, false);
     if (st != ISM_OK && st != ISM_ERR_NOT_CONVERGED) {
         ism_leave(ctx);
         return st;

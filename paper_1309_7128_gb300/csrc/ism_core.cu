@@ -1265,14 +1265,16 @@ static ism_status solve_mixed(ism_ctx *ctx)
     return read_state(ctx);
 }
 
-ism_status ism_solve_internal(ism_ctx *ctx, double tol, int max_cycles)
+ism_status ism_solve_internal(ism_ctx *ctx, double tol, int max_cycles, bool record_rhs)
 {
     // keep rhs-preparation results (bnorm, zero_rhs, status) and reset the rest
     TRY(read_state(ctx));
     IsmState h = *ctx->st_host;
     const double bn = h.bnorm;
-    ctx->last_rhs_sum = h.rhs_sum;
-    ctx->last_rhs_l1 = h.rhs_l1;
+    if (record_rhs) {
+        ctx->last_rhs_sum = h.rhs_sum;
+        ctx->last_rhs_l1 = h.rhs_l1;
+    }
     const int zr = h.zero_rhs, stt = h.status, dn = h.done;
     init_state(ctx, &h, tol, max_cycles);
     h.bnorm = bn;

@@ -168,7 +168,9 @@ ism_status ism_leave(ism_ctx *ctx);
 
 // Solve on internal buffers: b64 holds the right-hand side (mean removed),
 // p64[0] the initial guess; on return p64[0] holds the solution.
-ism_status ism_solve_internal(ism_ctx *ctx, double tol, int max_cycles);
+// record_rhs: keep the right-hand side's sums for ism_last_rhs (the caller's
+// own solves, ism_solve and proj_step; not the adjoint's internal solve).
+ism_status ism_solve_internal(ism_ctx *ctx, double tol, int max_cycles, bool record_rhs = true);
 // The accommodative strategy (cycle = 1, ism_accom.cu) on the same buffers.
 ism_status ism_solve_accommodative(ism_ctx *ctx, double tol, int max_sweeps);
 // Copy user rhs into b64 (removing the mean when singular) and compute ||b||.

@@ -103,3 +103,30 @@ def test_last_rhs_after_a_projection_step():
     ism.check(ism.proj_step(ctx, ud, vd, pd, 1e-4, 1e-2))
     s, mean, flag = ism.ism_last_rhs(ctx)
     assert s == ism.ISM_OK and not flag
+
+
+def test_last_rhs_is_not_replaced_by_the_adjoint_solve():
+    """ism_last_rhs describes the caller's last ism_solve / proj_step: the
+    adjoint's own pressure solve (proj_step_adjoint) leaves it unchanged."""
+    from synth.inputs import random_field, smooth_velocity
+    nx = ny = 128
+    u, v = smooth_velocity(nx, ny, 4)
+    import torch
+    ud = torch.tensor(0.1 * u, dtype=torch.float32, device="cuda:0")
+    vd = torch.tensor(0.1 * v, dtype=torch.float32, device="cuda:0")
+    pd = torch.zeros((ny, nx), dtype=torch.float32, device="cuda:0")
+    u0, v0 = ud.clone(), vd.clone()
+    ctx = setup(nx, ny, 16, (0, 0, 0, 0), prec=ism.ISM_MIXED)
+    ism.check(ism.ism_set_flow(ctx, (ism.ISM_VEL_NOSLIP,) * 4, (0, 0, 0, 1.0), None, 1.0))
+    ism.check(ism.ism_proj_tol(ctx, 1e-8, 100000, False))
+    ism.check(ism.proj_step(ctx, ud, vd, pd, 1e-4, 1e-2))
+    s, mean_fwd, flag_fwd = ism.ism_last_rhs(ctx)
+    assert s == ism.ISM_OK
+    # adjoint seeds with a large nonzero mean in the divergence of the adjoint solve
+    gu = torch.tensor(random_field(nx + 1, ny, 5) + 3.0, dtype=torch.float32, device="cuda:0")
+    gv = torch.tensor(random_field(nx, ny + 1, 6) - 2.0, dtype=torch.float32, device="cuda:0")
+    gp = torch.tensor(random_field(nx, ny, 7), dtype=torch.float32, device="cuda:0")
+    ism.check(ism.proj_step_adjoint(ctx, u0, v0, 1e-4, 1e-2, gu, gv, gp))
+    s, mean_after, flag_after = ism.ism_last_rhs(ctx)
+    assert s == ism.ISM_OK
+    assert mean_after == mean_fwd and flag_after == flag_fwd

@@ -1,8 +1,9 @@
 """The allocation-free residual + restriction entry point, for callers that
-cannot allocate device memory (during a stream capture, in real-time loops,
-or when their device memory belongs to their own arena), against the
-context-based ism_residual_restrict, on two calls in a row through the C
-ABI.  Named to be collected last."""
+cannot allocate device memory when they need a residual (real-time loops
+that cannot take cudaMalloc's implicit synchronisation, hosts whose device
+memory belongs to their own arena), against the context-based
+ism_residual_restrict, on two calls in a row through the C ABI.  Named to be
+collected last."""
 import numpy as np
 import pytest
 
