@@ -115,6 +115,12 @@ typedef struct {
                              streaming pass (one warp per 128-column strip marching down the rows,
                              the sweeps pipelined as a wavefront) when sweeps_per_pass is 1, 2 or 4;
                              0 (default): register-tiled passes only.  For grids larger than L2. */
+    int fault_test;       /* failure-detection test only; 0 (default) in normal use.  1: every
+                             tensor-core coarse solve (coarse_tc) first waits for an mbarrier phase
+                             that nothing completes, under the same time limit as its real waits
+                             (about 0.2 s); the wait runs out, the kernel records the failure, lets
+                             its bulk copies finish, frees its tensor memory and returns, and the
+                             solve stops with ISM_ERR_CUDA.  The CUDA context stays usable. */
 } ism_options;
 
 typedef struct ism_ctx ism_ctx;
@@ -382,7 +388,7 @@ ism_status proj_rollout_grad(ism_ctx *ctx, const float *u0, const float *v0, con
  * tensor cores (one CTA per problem) when every context has coarse_tc set and
  * a coarse grid of at most 64 x 64, else on the CUDA cores.  The graph is
  * built on the first call with a given list of contexts and reused while the
- * list (and nu, sweeps_per_pass, coarse_tc) is unchanged.
+ * list is unchanged and no member's options were set since.
  *   ctxs   host, n distinct contexts.  rhs, p: host arrays of n device pointers
  *          (as for ism_solve: p holds the initial guess and receives the result).
  *   max_cycles  cap on single-precision cycles per problem (>= 1).

@@ -49,7 +49,7 @@ struct BState {
 };
 
 struct Plan {
-    std::vector<unsigned long long> uids;
+    std::vector<unsigned long long> uids, gens;   // member contexts and their option generations
     int n = 0, nu = 0, K = 0;
     BDom *dom = nullptr;         // device, n
     BState *bst = nullptr;       // device
@@ -359,6 +359,7 @@ static ism_status build_plan(Plan *P, const std::vector<ism_ctx *> &cs)
         for (int l = 0; l < c->ncy; ++l) crows.push_back(make_int2(d, l));
         P->maxncx = std::max(P->maxncx, c->ncx);
         P->uids.push_back(c->uid);
+        P->gens.push_back(c->opt_gen);
     }
     P->nchunks = (int)chunks.size();
     P->ncrows = (int)crows.size();
@@ -527,7 +528,7 @@ static bool plan_matches(const Plan *P, const std::vector<ism_ctx *> &cs)
     if (!P || (int)cs.size() != P->n || cs[0]->opt.nu != P->nu || cs[0]->opt.sweeps_per_pass != P->K) return false;
     if ((P->ctc != nullptr) != batch_uses_tc(cs)) return false;
     for (size_t d = 0; d < cs.size(); ++d)
-        if (cs[d]->uid != P->uids[d]) return false;
+        if (cs[d]->uid != P->uids[d] || cs[d]->opt_gen != P->gens[d]) return false;
     return true;
 }
 

@@ -35,7 +35,7 @@ namespace {
 
 constexpr int CT_THREADS = 256;
 constexpr int CT_MAXC = 64;                   // max ncx, ncy
-constexpr uint32_t CT_WAIT = 1u << 22;        // mbarrier polls before giving up
+constexpr uint64_t CT_WAIT_NS = 200000000ull; // time limit of every mbarrier wait (0.2 s)
 constexpr uint32_t CT_CHUNK = 32768;          // bytes per bulk copy
 constexpr int CT_RITEMS = (CT_MAXC * CT_MAXC / 4 + CT_THREADS - 1) / CT_THREADS;   // R^T items per thread
 
@@ -95,6 +95,7 @@ struct CoarseTcArgs {
     const int *skip;
     IsmState *st;             // tc_fail is set when a wait runs out
     int *consumed;            // set to 1 once R has been used (batched: first restriction), or NULL
+    int fault_test;           // 1: wait first for a phase that nothing completes (failure-detection test)
 };
 
 __device__ __forceinline__ void put4(unsigned char *tile, int row, int k, int K, float a, float b, float c,
@@ -105,9 +106,10 @@ __device__ __forceinline__ void put4(unsigned char *tile, int row, int k, int K,
 }
 
 // Issue D = A B over K (one thread), commit, and wait for completion (all
-// threads; CTA-uniform result).
+// threads; CTA-uniform result).  On failure the MMAs may still be in flight:
+// *pending receives the parity of their phase (else -1).
 __device__ bool run_gemm(const unsigned char *sA, const unsigned char *sB, int K, uint32_t tmem, uint32_t idesc,
-                         uint64_t *bar, uint32_t parity)
+                         uint64_t *bar, uint32_t parity, int *pending)
 {
     tc::fence_smem_async();
     tc::fence_before_sync();
@@ -120,9 +122,11 @@ __device__ bool run_gemm(const unsigned char *sA, const unsigned char *sB, int K
                          idesc, s > 0);
         tc::mma_commit(bar);
     }
-    const bool ok = tc::mbar_wait(bar, parity, CT_WAIT);
+    const bool ok = tc::mbar_wait(bar, parity, CT_WAIT_NS);
     tc::fence_after_sync();
-    return __syncthreads_and(ok) != 0;
+    const bool all = __syncthreads_and(ok) != 0;
+    *pending = all ? -1 : (int)parity;
+    return all;
 }
 
 // Accumulator row `row` (the TMEM lane of this warp's quarter), 16-column
@@ -143,7 +147,7 @@ template <bool FROM_PARTS>
 __device__ __forceinline__ void coarse_tc_body(const CoarseTcArgs &a)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t bar_mma, bar_ld;
+    __shared__ uint64_t bar_mma, bar_ld, bar_never;
     __shared__ uint32_t tslot;
     const TcLayout &L = a.L;
     const int t = threadIdx.x, ncx = L.ncx, ncy = L.ncy, Np = L.Np, Kx = L.Kx, Ky = L.Ky;
@@ -156,6 +160,7 @@ __device__ __forceinline__ void coarse_tc_body(const CoarseTcArgs &a)
     if (t == 0) {
         tc::mbar_init(&bar_mma, 1);
         tc::mbar_init(&bar_ld, 1);
+        tc::mbar_init(&bar_never, 1);         // no thread ever arrives on it
         tc::mbar_expect_tx(&bar_ld, L.cbytes);
         for (uint32_t o = 0; o < L.cbytes; o += CT_CHUNK)
             tc::bulk_g2s(smem + o, a.cst + o, (L.cbytes - o) < CT_CHUNK ? (L.cbytes - o) : CT_CHUNK, &bar_ld);
@@ -193,9 +198,15 @@ __device__ __forceinline__ void coarse_tc_body(const CoarseTcArgs &a)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tslot;
-    const bool got = tc::mbar_wait(&bar_ld, 0, CT_WAIT);
+    // the constants; under fault_test a phase that nothing completes first
+    // (the wait runs out and the failure path below is taken)
+    bool ld_done = false;
+    if (!a.fault_test) ld_done = tc::mbar_wait(&bar_ld, 0, CT_WAIT_NS);
+    ld_done = __syncthreads_and(ld_done) != 0;
+    const bool got = a.fault_test ? tc::mbar_wait(&bar_never, 0, CT_WAIT_NS) : ld_done;
     bool ok = __syncthreads_and(got) != 0;
-    if (ok) ok = run_gemm(cA1, dB, Ky, tmem, idesc, &bar_mma, 0);
+    int pending = -1;                         // parity of MMAs still in flight after a failed wait
+    if (ok) ok = run_gemm(cA1, dB, Ky, tmem, idesc, &bar_mma, 0, &pending);
 
     // product 2: A = T1 (rows l, K = Kx), B = Qx as (n, k) -> Qx[k][n]
     if (ok) {
@@ -204,7 +215,7 @@ __device__ __forceinline__ void coarse_tc_body(const CoarseTcArgs &a)
             for (int q = 0; q < 16; q += 4)
                 if (c + q < Kx) put4(dA, l, c + q, Kx, v[q], v[q + 1], v[q + 2], v[q + 3]);
         });
-        ok = run_gemm(dA, cB2, Kx, tmem, idesc, &bar_mma, 1);
+        ok = run_gemm(dA, cB2, Kx, tmem, idesc, &bar_mma, 1, &pending);
     }
 
     // product 3: A = Qy, B[n][k] = (T2 .* Minv)[k][n]: the rows k < Ky of T2
@@ -232,7 +243,7 @@ __device__ __forceinline__ void coarse_tc_body(const CoarseTcArgs &a)
             }
             put4(dB, n, k0, Ky, s[0], s[1], s[2], s[3]);
         }
-        ok = run_gemm(cA3, dB, Ky, tmem, idesc, &bar_mma, 0);
+        ok = run_gemm(cA3, dB, Ky, tmem, idesc, &bar_mma, 0, &pending);
     }
 
     // product 4: A = T3 (rows l, K = Kx), B = Qx^T as (n, k) -> Qx[n][k]
@@ -242,7 +253,7 @@ __device__ __forceinline__ void coarse_tc_body(const CoarseTcArgs &a)
             for (int q = 0; q < 16; q += 4)
                 if (c + q < Kx) put4(dA, l, c + q, Kx, v[q], v[q + 1], v[q + 2], v[q + 3]);
         });
-        ok = run_gemm(dA, cB4, Kx, tmem, idesc, &bar_mma, 1);
+        ok = run_gemm(dA, cB4, Kx, tmem, idesc, &bar_mma, 1, &pending);
     }
 
     if (ok) {
@@ -262,12 +273,12 @@ __device__ __forceinline__ void coarse_tc_body(const CoarseTcArgs &a)
             }
         });
     } else {
-        // a wait ran out: report it, give the copies and MMAs in flight a
-        // bounded time to finish, and leave E untouched
+        // a wait ran out: report it, give the bulk copies and the MMAs still
+        // in flight a bounded time to finish (their memory is freed below),
+        // and leave E untouched
         if (t == 0) atomicExch(&a.st->tc_fail, 1);
-        tc::mbar_wait(&bar_ld, 0, CT_WAIT);
-        tc::mbar_wait(&bar_mma, 0, CT_WAIT);
-        tc::mbar_wait(&bar_mma, 1, CT_WAIT);
+        if (!ld_done) tc::mbar_wait(&bar_ld, 0, CT_WAIT_NS);
+        if (pending >= 0) tc::mbar_wait(&bar_mma, (uint32_t)pending, CT_WAIT_NS);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -322,6 +333,7 @@ static CoarseTcArgs coarse_tc_args(ism_ctx *ctx, const float *rc, float *ec, flo
     a.skip = skip;
     a.st = ctx->st;
     a.consumed = nullptr;
+    a.fault_test = ctx->opt.fault_test;
     return a;
 }
 

@@ -253,6 +253,7 @@ static void default_options(ism_options *o, int prec)
     o->accom_tol_c = 1e-5;
     o->accom_max_coarse = 100000;
     o->stream = 0;
+    o->fault_test = 0;
 }
 
 static const double kPi = 3.14159265358979323846;
@@ -626,6 +627,7 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
         return ISM_ERR_ARG;
     if (!(o->accom_tol_c > 0.0) || o->accom_max_coarse < 1) return ISM_ERR_ARG;
     if (o->stream < 0 || o->stream > 1) return ISM_ERR_ARG;
+    if (o->fault_test < 0 || o->fault_test > 1) return ISM_ERR_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
     // a narrower last coarse cell: the ISM and ACM operators, correction-scheme cycle
     if (ctx->ragged && (o->kind == ISM_COARSE_GMG || o->kind == ISM_COARSE_ACMV || o->cycle == 1))
@@ -646,6 +648,7 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
         }
     }
     ctx->opt = *o;
+    ctx->opt_gen++;
     free_graphs(ctx);
     if (kind_changed) return upload_coarse(ctx, E);
     return ISM_OK;

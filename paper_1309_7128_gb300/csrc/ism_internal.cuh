@@ -54,6 +54,7 @@ struct ism_ctx {
     int ragged;                // m does not divide nx or ny: the last coarse cell is narrower
     int prec;
     ism_options opt;
+    unsigned long long opt_gen;  // incremented by every ism_set_options (batched plans are keyed on it)
     cudaStream_t user_stream;  // ordering stream given by the caller
     cudaStream_t ws;           // private work stream (graph capture needs a non-legacy stream)
     cudaStream_t ws2;          // forked stream for concurrent launches within a step

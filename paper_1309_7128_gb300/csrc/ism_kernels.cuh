@@ -171,7 +171,8 @@ __device__ __forceinline__ void ctl_decide(IsmState *st, const double *S, int mo
         st->relres = rel;
         st->mean = S[1] * st->inv_n;
         if (k < ISM_HMAX) st->hist[k] = rel;
-        if (!isfinite(rel)) { st->status = ISM_ERR_NONFINITE; st->done = 1; }
+        if (st->tc_fail) { st->status = ISM_ERR_CUDA; st->done = 1; }   // a coarse solve gave up waiting
+        else if (!isfinite(rel)) { st->status = ISM_ERR_NONFINITE; st->done = 1; }
         else if (rel <= st->tol || st->zero_rhs) { st->status = ISM_OK; st->done = 1; }
         else if (fp64 ? (st->cycles >= st->max_cycles)
                       : (st->outer >= st->max_outer || st->cycles >= st->max_cycles)) {
@@ -198,7 +199,7 @@ __device__ __forceinline__ void ctl_decide(IsmState *st, const double *S, int mo
         st->enorm = en;
         st->mean_e = S[1] * st->inv_n;
         const double lim = fmax(st->inner_tol * st->r32norm, st->floor_mult * 0x1p-23 * en);
-        if (!isfinite(rin)) st->inner_done = 1;
+        if (!isfinite(rin) || st->tc_fail) st->inner_done = 1;
         else if (rin <= lim || st->inner_cycles >= st->inner_max || st->cycles >= st->max_cycles)
             st->inner_done = 1;
         break;

@@ -10,10 +10,10 @@
 //       (row / 8) * SBO + (k / 4) * 128 + (row % 8) * 16 + (k % 4) * 4,
 //     SBO = 32 K (the K/4 core matrices of an 8-row group are contiguous,
 //     LBO = 128 bytes between neighbours along K);
-//   * completion through tcgen05.commit on an mbarrier, waited for with an
-//     iteration limit (a wait that runs out reports failure instead of
-//     spinning on); operand tiles may arrive by bulk asynchronous copies
-//     (cp.async.bulk) completing on an mbarrier.
+//   * completion through tcgen05.commit on an mbarrier, waited for with a
+//     time limit on the global timer (a wait that runs out reports failure
+//     instead of spinning on); operand tiles may arrive by bulk asynchronous
+//     copies (cp.async.bulk) completing on an mbarrier.
 #pragma once
 
 #include <stdint.h>
@@ -107,12 +107,20 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
 
-// Wait for the phase with the given parity to complete; false after
-// `limit` unsuccessful polls.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase with the given parity to complete; false once
+// `limit_ns` nanoseconds (global timer) have passed without it.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns)
 {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < limit; ++it) {
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -120,8 +128,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done) : "r"(a), "r"(parity) : "memory");
         if (done) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 // D (+)= A B for one K = 8 step; accumulate selects D += A B.

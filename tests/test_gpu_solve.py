@@ -97,7 +97,7 @@ def test_accommodative_strategy_matches_oracle(nx, ny, m, bc):
     """The paper's accommodative strategy (cycle = 1, FP64): the same number
     of coarse Gauss-Seidel iterations as the oracle (the coarse arithmetic is
     rounded step by step in the oracle's order), the same number of fine
-    sweeps up to one, the criterion met, the field to 1e-10."""
+    sweeps, the criterion met, the field to 1e-10."""
     b = smooth_rhs(nx, ny, 12) + (1e-6 if any(bc) else 0.0)
     tol_f, tol_c = 1e-7, 1e-6
     p_ref, nc_ref, nf_ref, mx_ref = O.OracleAccommodative(nx, ny, m, bc).solve(b, tol_f=tol_f, tol_c=tol_c)
@@ -107,7 +107,7 @@ def test_accommodative_strategy_matches_oracle(nx, ny, m, bc):
     outer, cycles, _ = ism.ism_last_counts(ctx)
     print(f"{nx}x{ny}/{m}: coarse {outer} vs {nc_ref}, fine {cycles} vs {nf_ref}")
     assert s == ism.ISM_OK and mx <= tol_f
-    assert outer == nc_ref and abs(cycles - nf_ref) <= 1
+    assert outer == nc_ref and cycles == nf_ref
     assert rel(host(p), p_ref) <= 1e-10
     # options: FP64 with the ISM coarse operator only
     for prec, kind in ((ism.ISM_MIXED, 0), (ism.ISM_FP64, ism.ISM_COARSE_ACM)):
