@@ -285,18 +285,23 @@ ism_status ism_coarse_solve(ism_ctx *ctx, const void *rc, void *ec);
 ism_status ism_prolong_add(ism_ctx *ctx, const void *ec, void *p);
 
 /* Measurement helper: run `reps` smoothing passes of `sweeps` sweeps each
- * (as ism_smooth, one fused pass per call for ISM_MIXED) on p, b and return
- * in *us_per_pass the mean device time of one pass, taken with CUDA events
- * on the library's work stream.  Synchronises.  No counterpart in the paper
- * (Table 1 reports per-kernel wall times, Sec. 4.1). */
+ * (as ism_smooth, one fused pass per call for ISM_MIXED; an odd reps is
+ * rounded up to even there, so that the result ends in p) on p, b and return
+ * in *us_per_pass the mean device time of one pass.  The passes are captured
+ * into one CUDA graph on the library's work stream and replayed (once to
+ * warm up, once timed between CUDA events on that stream), so consecutive
+ * kernels run without host launch gaps, as inside a solve.  Synchronises.
+ * No counterpart in the paper (Table 1 reports per-kernel wall times,
+ * Sec. 4.1). */
 ism_status ism_time_pass(ism_ctx *ctx, void *p, const void *b, int sweeps, int reps,
                          double *us_per_pass);
 
 /* Measurement helper: run `reps` residual + restriction passes (those of
  * ism_residual_restrict, Sec. 3.2-3.3, norms left on the device) on p, b
  * into rc (device arrays as for ism_residual_restrict) and return in
- * *us_per_pass the mean device time of one pass, taken with CUDA events on
- * the library's work stream.  Synchronises. */
+ * *us_per_pass the mean device time of one pass, timed like ism_time_pass
+ * (one captured graph of the passes, replayed between CUDA events on the
+ * work stream).  Synchronises. */
 ism_status ism_time_restrict(ism_ctx *ctx, const void *p, const void *b, void *rc, int reps,
                              double *us_per_pass);
 
@@ -332,6 +337,21 @@ ism_status ism_proj_tol(ism_ctx *ctx, double tol, int max_cycles, int warm_start
 /* Last pressure increment dp of proj_step: device, nx*ny doubles owned by
  * the context (valid until the next call on it). */
 const double *ism_last_dp(const ism_ctx *ctx);
+
+/* Right-hand side of the context's last pressure solve as it was solved
+ * (ism_solve, proj_step or an adjoint step: Eq. 4's h div(v*)/dt in flux
+ * units for a projection step, its mean removed when every face is Neumann
+ * or periodic): device, nx*ny doubles owned by the context, valid until the
+ * next call on it.  With ism_last_dp it lets a caller check the equations a
+ * step solved (e.g. the residual b - A_f dp). */
+const double *ism_last_b(const ism_ctx *ctx);
+
+/* Set the pressure increment that the next proj_step starts its solve from
+ * when warm start is on (ism_proj_tol), as if it were the last increment:
+ * dp0 device, nx*ny doubles, copied (asynchronously, on the context's
+ * stream).  Restarts a run from a saved state (u, v, p and the last dp) with
+ * the same solves as the uninterrupted run.  No counterpart in the paper. */
+ism_status ism_set_warm_start(ism_ctx *ctx, const double *dp0);
 
 /* ---------------- adjoint of the projection step ------------------------
  * No counterpart in the paper, which runs the step forwards only.  The

@@ -353,6 +353,101 @@ int or_coarse_operator(int nx, int ny, int m, const int *bc, int kind, double *A
     return 0;
 }
 
+/* The same assembly for large coarse grids, returned as (row, column,     */
+/* value) triples instead of a dense matrix: the interpolant of e_J is       */
+/* evaluated on a window of the coarse cells J-1..J+1 with a border of one   */
+/* zero cell (the interpolant vanishes beyond them), and the face sums of    */
+/* every coarse cell K of the window are taken there with the same rules and */
+/* the same order of operations as face_sums.  Walls only (no periodic       */
+/* face: its wrapped neighbours lie outside the window).  rows, cols, vals   */
+/* hold 9 nc entries; returns the number written, or -1 (allocation failed,  */
+/* or a periodic face).  The columns are independent, so they may be split   */
+/* over threads; each triple is computed by one thread as in the dense form. */
+/* ------------------------------------------------------------------------ */
+
+#define WIN(a, i, j) (a)[(size_t)((j) - wy0 + 1) * (size_t)(wx + 2) + (size_t)((i) - wx0 + 1)]
+
+static double face_sums_window(int nx, int ny, int m, const int *bc, const double *w,
+                               int wx0, int wy0, int wx, int KI, int KJ)
+{
+    int x0 = KI * m, x1 = block_end(KI, nx, m), y0 = KJ * m, y1 = block_end(KJ, ny, m);
+    double s = 0.0;
+    for (int j = y0; j < y1; ++j) {                     /* west face */
+        if (x0 > 0) s += WIN(w, x0 - 1, j) - WIN(w, x0, j);
+        else if (bc[F_W] == BC_DIR) s += -WIN(w, x0, j) - WIN(w, x0, j);
+    }
+    for (int j = y0; j < y1; ++j) {                     /* east face */
+        if (x1 < nx) s += WIN(w, x1, j) - WIN(w, x1 - 1, j);
+        else if (bc[F_E] == BC_DIR) s += -WIN(w, x1 - 1, j) - WIN(w, x1 - 1, j);
+    }
+    for (int i = x0; i < x1; ++i) {                     /* south face */
+        if (y0 > 0) s += WIN(w, i, y0 - 1) - WIN(w, i, y0);
+        else if (bc[F_S] == BC_DIR) s += -WIN(w, i, y0) - WIN(w, i, y0);
+    }
+    for (int i = x0; i < x1; ++i) {                     /* north face */
+        if (y1 < ny) s += WIN(w, i, y1) - WIN(w, i, y1 - 1);
+        else if (bc[F_N] == BC_DIR) s += -WIN(w, i, y1 - 1) - WIN(w, i, y1 - 1);
+    }
+    return s;
+}
+
+long or_coarse_operator_coo(int nx, int ny, int m, const int *bc, int kind,
+                            int *rows, int *cols, double *vals)
+{
+    int ncx = ncoarse(nx, m), ncy = ncoarse(ny, m);
+    long nc = (long)ncx * ncy;
+    for (int f = 0; f < 4; ++f)
+        if (bc[f] == BC_PER) return -1;
+    long count = 0;
+    int fail = 0;
+    /* each column writes its own 9 slots: column c owns entries 9c .. 9c+8 */
+    _Pragma("omp parallel")
+    {
+        const size_t wmax = (size_t)(3 * m + 2) * (size_t)(3 * m + 2);
+        double *w = (double *)calloc(wmax, sizeof(double));
+        double *q = (double *)calloc((size_t)nc, sizeof(double));
+        if (!w || !q) {
+            _Pragma("omp atomic write")
+            fail = 1;
+        } else {
+            _Pragma("omp for schedule(static)")
+            for (long col = 0; col < nc; ++col) {
+                int JI = (int)(col % ncx), JJ = (int)(col / ncx);
+                int bi0 = JI - 1 < 0 ? 0 : JI - 1, bi1 = JI + 1 >= ncx ? ncx - 1 : JI + 1;
+                int bj0 = JJ - 1 < 0 ? 0 : JJ - 1, bj1 = JJ + 1 >= ncy ? ncy - 1 : JJ + 1;
+                int wx0 = bi0 * m, wy0 = bj0 * m;
+                int wx = block_end(bi1, nx, m) - wx0, wy = block_end(bj1, ny, m) - wy0;
+                memset(w, 0, (size_t)(wx + 2) * (size_t)(wy + 2) * sizeof(double));
+                q[col] = 1.0;
+                for (int j = wy0; j < wy0 + wy; ++j)
+                    for (int i = wx0; i < wx0 + wx; ++i)
+                        WIN(w, i, j) = (kind == 0) ? bilinear_at(nx, ny, m, bc, q, i, j)
+                                                   : q[(size_t)(j / m) * ncx + (i / m)];
+                q[col] = 0.0;
+                int k = 0;
+                for (int KJ = bj0; KJ <= bj1; ++KJ)
+                    for (int KI = bi0; KI <= bi1; ++KI, ++k) {
+                        rows[9 * col + k] = KJ * ncx + KI;
+                        cols[9 * col + k] = (int)col;
+                        vals[9 * col + k] = face_sums_window(nx, ny, m, bc, w, wx0, wy0, wx, KI, KJ);
+                    }
+                for (; k < 9; ++k) {             /* unused slots (edge columns) */
+                    rows[9 * col + k] = -1;
+                    cols[9 * col + k] = -1;
+                    vals[9 * col + k] = 0.0;
+                }
+            }
+        }
+        free(w);
+        free(q);
+    }
+    if (fail) return -1;
+    count = 9 * nc;
+    return count;
+}
+
+#undef WIN
+
 /* ------------------------------------------------------------------------ */
 /* Gauss-Seidel on the coarse equations A_c e = r (the paper's iterative      */
 /* coarse solve, Sec. 4.3.1), four-colour ordering of the nine-point stencil: */
@@ -538,6 +633,7 @@ void or_predictor(int nx, int ny, double h, double dt, double nu,
 {
     double ih = 1.0 / h, ih2 = 1.0 / (h * h);
     /* x-faces */
+    ROWS_PARALLEL
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i <= nx; ++i) {
             double uc = UU(i, j);
@@ -566,6 +662,7 @@ void or_predictor(int nx, int ny, double h, double dt, double nu,
         }
     }
     /* y-faces: south and north are walls (zero normal velocity) */
+    ROWS_PARALLEL
     for (int j = 0; j <= ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             double vc = VV(i, j);
@@ -586,6 +683,7 @@ void or_predictor(int nx, int ny, double h, double dt, double nu,
 void or_divergence(int nx, int ny, double h, double dt, const double *u,
                    const double *v, double *b)
 {
+    ROWS_PARALLEL
     for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
             b[(size_t)j * nx + i] = h * ((UU(i + 1, j) - UU(i, j))
@@ -598,6 +696,7 @@ void or_correct(int nx, int ny, double h, double dt, const int *vel_bc,
                 const double *dp, double *u, double *v, double *p)
 {
     double s = dt / h;
+    ROWS_PARALLEL
     for (int j = 0; j < ny; ++j) {
         for (int i = 1; i < nx; ++i)
             UU(i, j) -= s * (dp[(size_t)j * nx + i] - dp[(size_t)j * nx + i - 1]);
@@ -606,6 +705,7 @@ void or_correct(int nx, int ny, double h, double dt, const int *vel_bc,
             UU(nx, j) -= s * (-pin - pin);
         }
     }
+    ROWS_PARALLEL
     for (int j = 1; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
             VV(i, j) -= s * (dp[(size_t)j * nx + i] - dp[(size_t)(j - 1) * nx + i]);

@@ -68,6 +68,7 @@ def lib():
                 "or_prolong_const_add": [i, i, i, _dp, _dp],
                 "or_coarse_operator": [i, i, i, _ip, i, _dp],
                 "or_coarse_gs4": [i, i, _dp, _dp, _dp, C.c_double, i, i],
+                "or_coarse_operator_coo": [i, i, i, _ip, i, _ip, _ip, _dp],
                 "or_residual_f32": [i, i, _ip, _fp, _fp, _fp],
                 "or_rbgs_sweep_f32": [i, i, _ip, _fp, _fp],
                 "or_restrict_f32": [i, i, i, _fp, _dp],
@@ -83,6 +84,7 @@ def lib():
                 f.argtypes = args
                 f.restype = C.c_int if name in ("or_coarse_operator", "or_coarse_gs4", "or_set_threads",
                                                 "or_get_threads") else None
+            L.or_coarse_operator_coo.restype = C.c_long
             # sequential unless a caller asks for threads (set_threads): the
             # test grids are small, where thread start-up costs more than it saves
             L.or_set_threads(1)
@@ -93,9 +95,39 @@ def lib():
 BC_NEUMANN, BC_DIRICHLET0, BC_PERIODIC = 0, 1, 2
 
 
+def _blas_one_thread():
+    """Run the OpenBLAS libraries that numpy and scipy load on one thread.
+    The oracle's BLAS calls (norms, the coarse LU solve) are small; OpenBLAS
+    worker threads that keep spinning between them take the cores the
+    threaded row loops need (a 256^2 solve on 16 threads was 15x slower than
+    on one).  Searches the loaded libraries (/proc/self/maps) for the
+    OpenBLAS thread setter under the names these builds export."""
+    try:
+        with open("/proc/self/maps") as f:
+            libs = sorted({ln.split()[-1] for ln in f if "openblas" in ln.lower() and "/" in ln})
+    except OSError:
+        return
+    for path in libs:
+        try:
+            L = C.CDLL(path)
+        except OSError:
+            continue
+        for name in ("openblas_set_num_threads", "openblas_set_num_threads64_",
+                     "scipy_openblas_set_num_threads", "scipy_openblas_set_num_threads64_"):
+            fn = getattr(L, name, None)
+            if fn is not None:
+                fn.argtypes = [C.c_int]
+                fn.restype = None
+                fn(1)
+
+
 def set_threads(n: int) -> int:
     """Threads of the C part's row loops (n <= 0: all host cores); returns the
-    count in use.  Results are bit-identical for any count."""
+    count in use.  Results are bit-identical for any count.  BLAS stays on
+    one thread (see _blas_one_thread)."""
+    if int(n) != 1:
+        import scipy.linalg  # noqa: F401  (load scipy's OpenBLAS before limiting it)
+        _blas_one_thread()
     return int(lib().or_set_threads(int(n)))
 
 
@@ -206,6 +238,25 @@ def coarse_operator(nx, ny, m, bc, kind="ism"):
     return Ac
 
 
+def coarse_operator_sparse(nx, ny, m, bc, kind="ism"):
+    """The coarse operator of kind 'ism' or 'acm' as a scipy CSR matrix,
+    assembled column by column with the same face-flux sums as
+    coarse_operator (walls only: no periodic face).  For coarse grids too
+    large for a dense matrix."""
+    import scipy.sparse
+    if kind not in ("ism", "acm"):
+        raise ValueError("sparse assembly: kinds 'ism' and 'acm'")
+    nc = ncoarse(nx, m) * ncoarse(ny, m)
+    rows = np.empty(9 * nc, dtype=np.int32)
+    cols = np.empty(9 * nc, dtype=np.int32)
+    vals = np.empty(9 * nc, dtype=np.float64)
+    got = lib().or_coarse_operator_coo(nx, ny, m, _bc(bc), 0 if kind == "ism" else 1, rows, cols, vals)
+    if got < 0:
+        raise ValueError("sparse assembly failed (periodic face or allocation)")
+    keep = rows >= 0
+    return scipy.sparse.csr_matrix((vals[keep], (rows[keep], cols[keep])), shape=(nc, nc))
+
+
 # --------------------------------------------------------------------------
 # the two-level solver
 # --------------------------------------------------------------------------
@@ -220,7 +271,10 @@ class OracleISM:
     piecewise-constant correction (ACM), red-black Gauss-Seidel smoothing.
     """
 
-    def __init__(self, nx, ny, m, bc=(0, 0, 0, 0), kind="ism", nu=8):
+    # coarse grids above this many cells are factorised as sparse matrices
+    SPARSE_ABOVE = 4096
+
+    def __init__(self, nx, ny, m, bc=(0, 0, 0, 0), kind="ism", nu=8, coarse="auto"):
         if kind == "gmg" and (nx % m or ny % m):
             raise ValueError("the GMG comparator needs a grid that is a multiple of the coarsening factor")
         bca = _bc(bc)
@@ -231,8 +285,15 @@ class OracleISM:
         self.kind = kind
         self.nu = nu
         self.singular = is_singular(self.bc)
+        nc = ncoarse(nx, m) * ncoarse(ny, m)
+        if coarse == "auto":
+            coarse = "sparse" if (nc > self.SPARSE_ABOVE and kind in ("ism", "acm")
+                                  and not np.any(bca == BC_PERIODIC)) else "dense"
+        self.coarse = coarse
+        if coarse == "sparse":
+            self._setup_sparse(nc)
+            return
         self.Ac = coarse_operator(nx, ny, m, self.bc, kind)
-        nc = self.Ac.shape[0]
         M = -self.Ac
         if self.singular:
             # all-Neumann: A_c 1 = 0.  (-A_c + 1 1^T / nc) is nonsingular and,
@@ -241,8 +302,29 @@ class OracleISM:
             M = M + np.full((nc, nc), 1.0 / nc)
         self._lu = scipy.linalg.lu_factor(M, check_finite=False)
 
+    def _setup_sparse(self, nc):
+        """Sparse LU (SuperLU, a library routine) of -A_c; with all faces
+        Neumann of the bordered matrix [[-A_c, 1], [1^T, 0]], whose solution
+        for a zero-sum right-hand side is minus the mean-free solution of
+        A_c e = r_c (the Lagrange multiplier is then 0)."""
+        import scipy.sparse
+        import scipy.sparse.linalg
+        self.Ac = coarse_operator_sparse(self.nx, self.ny, self.m, self.bc, self.kind)
+        M = -self.Ac
+        if self.singular:
+            one = scipy.sparse.csr_matrix(np.ones((nc, 1)))
+            M = scipy.sparse.bmat([[M, one], [one.T, None]], format="csr")
+        self._splu = scipy.sparse.linalg.splu(M.tocsc())
+        self._nc = nc
+
     # e_c = A_c^+ r_c (exact coarse solve)
     def coarse_solve(self, rc):
+        if self.coarse == "sparse":
+            rhs = rc.reshape(-1)
+            if self.singular:
+                rhs = np.concatenate([rhs, [0.0]])
+            x = self._splu.solve(rhs)[: self._nc]
+            return (-x).reshape(rc.shape)
         x = scipy.linalg.lu_solve(self._lu, rc.reshape(-1), check_finite=False)
         return (-x).reshape(rc.shape)
 

@@ -1455,32 +1455,57 @@ extern "C" ism_status ism_prolong_add(ism_ctx *ctx, const void *ec, void *p)
     return ism_leave(ctx);
 }
 
+// Device time of `reps` launches of pass(r), r = 0 .. reps-1, as the solver
+// runs them: the launches are captured into one CUDA graph on the work
+// stream (no host launch gaps between kernels, as inside the solve graphs),
+// the graph is replayed once to warm up and once between two CUDA events on
+// the work stream.
+template <typename F>
+static ism_status time_graph(ism_ctx *ctx, int reps, F pass, double *us_per_pass)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t gx = nullptr;
+    ism_status st = ISM_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = ISM_ERR_CUDA;
+    if (st == ISM_OK && cudaStreamBeginCapture(ctx->ws, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        st = ISM_ERR_CUDA;
+    if (st == ISM_OK) {
+        for (int r = 0; r < reps && st == ISM_OK; ++r) st = pass(r);
+        // always end the capture, also after a failed launch
+        if (cudaStreamEndCapture(ctx->ws, &g) != cudaSuccess && st == ISM_OK) st = ISM_ERR_CUDA;
+    }
+    if (st == ISM_OK && cudaGraphInstantiate(&gx, g, 0) != cudaSuccess) st = ISM_ERR_CUDA;
+    if (st == ISM_OK && cudaGraphLaunch(gx, ctx->ws) != cudaSuccess) st = ISM_ERR_CUDA;      // warm-up
+    if (st == ISM_OK && (cudaEventRecord(e0, ctx->ws) != cudaSuccess || cudaGraphLaunch(gx, ctx->ws) != cudaSuccess ||
+                         cudaEventRecord(e1, ctx->ws) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess))
+        st = ISM_ERR_CUDA;
+    if (st == ISM_OK) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = ISM_ERR_CUDA;
+        else *us_per_pass = 1000.0 * ms / reps;
+    }
+    if (gx) cudaGraphExecDestroy(gx);
+    if (g) cudaGraphDestroy(g);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st != ISM_OK) cudaGetLastError();
+    return st;
+}
+
 extern "C" ism_status ism_time_restrict(ism_ctx *ctx, const void *p, const void *b, void *rc, int reps,
                                         double *us_per_pass)
 {
     if (!ctx || !p || !b || !rc || reps < 1 || !us_per_pass) return ISM_ERR_ARG;
-    cudaEvent_t e0, e1;
-    ISM_CUDA_TRY(cudaEventCreate(&e0));
-    ISM_CUDA_TRY(cudaEventCreate(&e1));
-    auto pass = [&]() -> ism_status {
+    auto pass = [&](int) -> ism_status {
         if (ctx->prec == ISM_FP64) return launch_resid<double>(ctx, (const double *)p, (const double *)b, (double *)rc, nullptr);
         return launch_resid<float>(ctx, (const float *)p, (const float *)b, (float *)rc, nullptr);
     };
-    ism_status st = ism_enter(ctx);
-    if (st == ISM_OK) st = pass();                           // warm-up
-    if (st == ISM_OK) {
-        ISM_CUDA_TRY(cudaEventRecord(e0, ctx->ws));
-        for (int r = 0; r < reps && st == ISM_OK; ++r) st = pass();
-        ISM_CUDA_TRY(cudaEventRecord(e1, ctx->ws));
-        ISM_CUDA_TRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        ISM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-        *us_per_pass = 1000.0 * ms / reps;
-        ism_leave(ctx);
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    return st;
+    TRY(ism_enter(ctx));
+    ism_status st = time_graph(ctx, reps, pass, us_per_pass);
+    ism_status s2 = ism_leave(ctx);
+    ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+    return st != ISM_OK ? st : s2;
 }
 
 extern "C" ism_status ism_time_pass(ism_ctx *ctx, void *p, const void *b, int sweeps, int reps,
@@ -1488,36 +1513,21 @@ extern "C" ism_status ism_time_pass(ism_ctx *ctx, void *p, const void *b, int sw
 {
     if (!ctx || !p || !b || sweeps < 1 || reps < 1 || !us_per_pass) return ISM_ERR_ARG;
     if (ctx->prec == ISM_MIXED && sweeps > SMAXK) return ISM_ERR_ARG;
-    cudaEvent_t e0, e1;
-    ISM_CUDA_TRY(cudaEventCreate(&e0));
-    ISM_CUDA_TRY(cudaEventCreate(&e1));
-    ism_status st = ism_smooth(ctx, p, b, sweeps);          // warm-up
-    if (st == ISM_OK) {
-        TRY(ism_enter(ctx));
-        ISM_CUDA_TRY(cudaEventRecord(e0, ctx->ws));
-        for (int r = 0; r < reps && st == ISM_OK; ++r) {
-            if (ctx->prec == ISM_FP64) {
-                st = launch_sweeps<double>(ctx, (double *)p, (const double *)b, sweeps, nullptr);
-            } else {
-                SweepArgs a = inner_args(ctx, ctx->st_k, (float *)p, ctx->e32[1], (const float *)b, nullptr, nullptr);
-                a.use_mean = 0;
-                a.K = sweeps;
-                a.q = r & 1;
-                st = launch_sweep32(ctx, a, false, false);
-            }
-        }
-        ISM_CUDA_TRY(cudaEventRecord(e1, ctx->ws));
-        ISM_CUDA_TRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        ISM_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-        *us_per_pass = 1000.0 * ms / reps;
-        if (ctx->prec == ISM_MIXED && (reps & 1))
-            ISM_CUDA_TRY(cudaMemcpyAsync(p, ctx->e32[1], (size_t)ctx->n * 4, cudaMemcpyDeviceToDevice, ctx->ws));
-        ism_leave(ctx);
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    return st;
+    // an even number of single-precision passes: the ping-pong ends in p
+    if (ctx->prec == ISM_MIXED) reps += reps & 1;
+    auto pass = [&](int r) -> ism_status {
+        if (ctx->prec == ISM_FP64) return launch_sweeps<double>(ctx, (double *)p, (const double *)b, sweeps, nullptr);
+        SweepArgs a = inner_args(ctx, ctx->st_k, (float *)p, ctx->e32[1], (const float *)b, nullptr, nullptr);
+        a.use_mean = 0;
+        a.K = sweeps;
+        a.q = r & 1;
+        return launch_sweep32(ctx, a, false, false);
+    };
+    TRY(ism_enter(ctx));
+    ism_status st = time_graph(ctx, reps, pass, us_per_pass);
+    ism_status s2 = ism_leave(ctx);
+    ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+    return st != ISM_OK ? st : s2;
 }
 
 // ================================================================ autotuner

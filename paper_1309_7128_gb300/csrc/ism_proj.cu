@@ -187,6 +187,19 @@ extern "C" ism_status ism_proj_tol(ism_ctx *ctx, double tol, int max_cycles, int
 
 extern "C" const double *ism_last_dp(const ism_ctx *ctx) { return ctx ? ctx->dp : nullptr; }
 
+extern "C" const double *ism_last_b(const ism_ctx *ctx) { return ctx ? ctx->b64 : nullptr; }
+
+ism_status ism_proj_buffers(ism_ctx *ctx);
+
+extern "C" ism_status ism_set_warm_start(ism_ctx *ctx, const double *dp0)
+{
+    if (!ctx || !dp0) return ISM_ERR_ARG;
+    TRY(ism_proj_buffers(ctx));
+    TRY(ism_enter(ctx));
+    ISM_CUDA_TRY(cudaMemcpyAsync(ctx->dp, dp0, (size_t)ctx->n * 8, cudaMemcpyDeviceToDevice, ctx->ws));
+    return ism_leave(ctx);
+}
+
 ism_status ism_proj_buffers(ism_ctx *ctx)
 {
     if (ctx->us) return ISM_OK;

@@ -62,6 +62,8 @@ _SIGS = {
     "proj_step": (_I, [_VP, _VP, _VP, _VP, _D, _D]),
     "ism_proj_tol": (_I, [_VP, _D, _I, _I]),
     "ism_last_dp": (_VP, [_VP]),
+    "ism_last_b": (_VP, [_VP]),
+    "ism_set_warm_start": (_I, [_VP, _VP]),
     "ism_time_pass": (_I, [_VP, _VP, _VP, _I, _I, C.POINTER(C.c_double)]),
     "ism_time_restrict": (_I, [_VP, _VP, _VP, _VP, _I, C.POINTER(C.c_double)]),
     "ism_autotune": (_I, [_VP, _VP, _D, _I, C.POINTER(IsmOptions)]),
@@ -261,6 +263,28 @@ def proj_step(ctx, u, v, p, dt, nu):
 def ism_last_dp(ctx):
     """Device address of the context's last pressure increment (nx*ny doubles)."""
     return lib().ism_last_dp(ctx.handle)
+
+
+def ism_set_warm_start(ctx, dp0):
+    """Next warm-started proj_step starts from dp0 (device, nx*ny doubles)."""
+    return lib().ism_set_warm_start(ctx.handle, _ptr(dp0))
+
+
+def device_view(ptr, shape, dtype="float64"):
+    """A torch tensor aliasing library-owned device memory (ism_last_dp,
+    ism_last_b): no copy; valid until the next call on the owning context."""
+    import torch
+
+    class _Arr:
+        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": {"float64": "<f8", "float32": "<f4"}[dtype],
+                                    "data": (int(ptr), False), "version": 3, "strides": None}
+    return torch.as_tensor(_Arr(), device="cuda")
+
+
+def ism_last_b(ctx):
+    """Device address of the right-hand side of the context's last pressure
+    solve (nx*ny doubles, mean removed when all faces are Neumann)."""
+    return lib().ism_last_b(ctx.handle)
 
 
 def ism_solve_batched(ctxs, rhs, p, tol=1e-8, max_cycles=100000):

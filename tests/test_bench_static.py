@@ -50,8 +50,7 @@ def _check(fn, outer, missing):
             _check(f, local, missing)
 
 
-@pytest.mark.parametrize("path", ["bench.py", "paper_1309_7128_gb300/timepass.py",
-                                  "paper_1309_7128_gb300/workloads.py"])
+@pytest.mark.parametrize("path", ["bench.py", "paper_1309_7128_gb300/timepass.py"])
 def test_functions_read_only_bound_names(path):
     tree = ast.parse(open(os.path.join(ROOT, path)).read())
     module = set(dir(builtins)) | {"__file__", "__name__"}

@@ -211,3 +211,30 @@ def test_threaded_loops_are_bit_identical_to_one_thread(bc):
         O.set_threads(prev)
     for x, y in zip(out[1], out[0]):
         assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_threaded_projection_step_is_bit_identical_to_one_thread():
+    """Predictor, divergence and correction (Eq. 3-4) on their threaded row
+    loops give the one-thread results bit for bit (jet boundaries)."""
+    from synth.inputs import jet_inflow
+    nx, ny = 96, 64
+    jet = (O.VEL_INFLOW, O.VEL_OUTFLOW, O.VEL_FREESLIP, O.VEL_FREESLIP)
+    u0 = random_field(nx + 1, ny, 30) * 0.1
+    v0 = random_field(nx, ny + 1, 31) * 0.1
+    p0 = random_field(nx, ny, 32)
+    dp = random_field(nx, ny, 33) * 1e-3
+    prof = jet_inflow(ny, width=16, seed=1)
+    out = {}
+    prev = O.get_threads()
+    try:
+        for t in (1, 0):
+            O.set_threads(t)
+            us, vs = O.predictor(u0, v0, p0, 1.0, 0.1, 0.01, jet, u_in=prof, conv_u=1.0)
+            b = O.divergence(us, vs, 1.0, 0.1)
+            u, v, p = us.copy(), vs.copy(), p0.copy()
+            O.correct(u, v, p, dp, 1.0, 0.1, jet)
+            out[t] = (us, vs, b, u, v, p)
+    finally:
+        O.set_threads(prev)
+    for x, y in zip(out[1], out[0]):
+        assert np.array_equal(x, y)
