@@ -816,6 +816,21 @@ static ism_status make_plans(ism_ctx *ctx)
     return ISM_OK;
 }
 
+// Streaming multiprocessors of the current device (read once).
+static int ism_sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0, n = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            sms = n;
+        else
+            sms = 152;
+        cudaGetLastError();
+    }
+    return sms;
+}
+
 // Interior and edge launches of one pass run concurrently: the edge launch
 // goes to a forked stream joined back before the next kernel.
 template <bool PR, bool RE>
@@ -879,6 +894,9 @@ static ism_status launch_sweep32(ism_ctx *ctx, SweepArgs a, bool prolong, bool r
     a.TW = sweep_tile_w(a.K, resid);
     a.TH = sweep_tile_h(a.K, resid);
     a.gx = P.gx; a.gy = P.gy; a.ix0 = P.ix0; a.iy0 = P.iy0; a.edge_tiles = P.edge;
+    a.pf_ahead = 2 * ism_sm_count();            // one wave of resident CTAs (2 per SM) ahead
+    a.pgx = P.ix1 - P.ix0;
+    a.pn = a.pgx * (P.iy1 - P.iy0);
     if (!resid) a.ctl_mode = -1;
     ism_status st;
     if (prolong && resid) st = launch_sweep_pair<true, true>(ctx, a, P);
@@ -981,7 +999,8 @@ static SweepArgs inner_args(ism_ctx *ctx, IsmState *st, float *e0, float *e1, co
     a.nx = ctx->nx; a.ny = ctx->ny; a.m = ctx->m; a.ncx = ctx->ncx; a.ncy = ctx->ncy;
     a.lm = ctx->m == 8 ? 3 : ctx->m == 16 ? 4 : 5;
     a.bcmask = ctx->bcmask; a.kind = ctx->opt.kind; a.K = ctx->opt.sweeps_per_pass;
-    a.q = 0; a.use_mean = ctx->singular; a.ctl_mode = -1;
+    a.q = 0; a.use_mean = ctx->singular; a.ctl_mode = -1; a.pf_ahead = 0;
+    a.pgx = a.pn = 0;
     a.H = a.Hc = a.TW = a.TH = 0;
     a.cond = 0;
     return a;

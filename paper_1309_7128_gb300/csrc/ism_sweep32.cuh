@@ -30,6 +30,12 @@
 // any other cell: they are copies, and the error front argument above holds
 // unchanged.
 //
+// Interior tiles (region strictly inside the domain) read their rows without
+// bounds checks, and while they sweep they start an L2 prefetch of the rows
+// of the interior tile one wave of resident CTAs ahead (cp.async.bulk
+// .prefetch.L2): that tile's CTA then loads from L2 what would otherwise come
+// from HBM.
+//
 // Options fused into the pass:
 //  PROLONG: add P e_c - mean while loading.  P e_c is evaluated in the
 //           separable form of Eq. 5 (interpolation coordinates from
@@ -47,7 +53,7 @@
 
 constexpr int SNC = 4;                  // columns per thread
 constexpr int SRR = 16;                 // rows per warp
-constexpr int SNW = 8;                  // warps per CTA
+constexpr int SNW = 8;                  // warps per CTA (a 16-warp, 256-row region was slower at 8192 x 4096)
 constexpr int SRW = 32 * SNC;           // region width 128
 constexpr int SRH = SNW * SRR;          // region height 128
 constexpr int STHREADS = 32 * SNW;      // 256
@@ -68,6 +74,8 @@ struct SweepArgs {
     int ix0, iy0;             // interior launch: tile = block + (ix0, iy0)
     const int2 *edge_tiles;   // edge launch: tile = edge_tiles[block]
     unsigned long long cond;  // graph while-node handle set by the control, or 0
+    int pf_ahead;             // interior tiles: prefetch into L2 the tile this many tiles ahead (0: off)
+    int pgx, pn;              // interior tile grid: columns and number of tiles (row-major from ix0, iy0)
 };
 
 // Row halo 2K (+1 for the residual); the column halo is rounded up to a
@@ -76,6 +84,33 @@ __host__ __device__ inline int sweep_halo(int K, bool resid) { return 2 * K + (r
 __host__ __device__ inline int sweep_halo_cols(int K, bool resid) { return (sweep_halo(K, resid) + 3) & ~3; }
 __host__ __device__ inline int sweep_tile_w(int K, bool resid) { return SRW - 2 * sweep_halo_cols(K, resid); }
 __host__ __device__ inline int sweep_tile_h(int K, bool resid) { return SRH - 2 * sweep_halo(K, resid); }
+
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(p), "r"(bytes) : "memory");
+}
+
+// Start bringing the rows of p and b that interior tile `id` (row-major
+// over the interior tiles) loads into L2 (one bulk prefetch per row of its
+// region, clipped to the domain), so that the CTA that runs it about one
+// wave later finds them there instead of in HBM.  Same tile geometry as
+// sweep_tile.
+__device__ __forceinline__ void prefetch_tile(const SweepArgs &a, const float *pin, int id)
+{
+    if (id >= a.pn) return;
+    const int bx = id % a.pgx + a.ix0, by = id / a.pgx + a.iy0;
+    const int x0 = bx * a.TW - a.Hc, y0 = by * a.TH - a.H;
+    const int xa = max(x0, 0), xb = min(x0 + SRW, a.nx);
+    if (xb <= xa) return;
+    const unsigned bytes = (unsigned)(xb - xa) * 4u;       // x0, nx multiples of 4: 16-byte pieces
+    for (int k = threadIdx.x; k < 2 * (SRH + 2); k += STHREADS) {
+        const bool isb = k >= SRH + 2;
+        const int y = y0 - 1 + (isb ? k - (SRH + 2) : k);
+        if ((unsigned)y >= (unsigned)a.ny || (isb && (y < y0 || y >= y0 + SRH))) continue;
+        prefetch_l2((isb ? a.b : pin) + (size_t)y * a.nx + xa, bytes);
+    }
+}
 
 // b in shared memory: per region row two planes of 32 float2, plane 0 holding
 // (b_q0, b_q2) and plane 1 (b_q1, b_q3) of each lane's columns 4l+q, so the
@@ -178,7 +213,7 @@ inline size_t sweep_smem_bytes()
 // (listed in edge_tiles); otherwise the launch over the interior tiles.
 // The pass on tile (bx, by) of the problem described by a; one CTA.
 template <bool PROLONG, bool RESID, bool EDGE>
-__device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, const int by)
+__device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, const int by, const int pf_id)
 {
     extern __shared__ __align__(16) float sm[];
     float *bsm = sm;                       // SRH x SRW (b per thread, colour-pair order)
@@ -257,26 +292,47 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
             esm[t] = a.E[(size_t)J * a.ncx + I];
         }
     }
+    if (!EDGE) {
+        // interior tile: every row and column of the region lies in the domain,
+        // so the rows are read without bounds checks (fewer instructions in
+        // the load phase: 8% of the pass at 8192 x 4096)
+        const float *src = pin + (size_t)(y0 + ry0 - 1) * nx + cx;
 #pragma unroll
-    for (int r = 0; r < SRR + 2; ++r) {
-        int y = y0 + ry0 + r - 1;
-        bool rowin = (unsigned)y < (unsigned)ny;
-        if (per_y && !rowin) { y = wrap_mod(y, ny); rowin = true; }   // periodic copy
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (rowin && colin) v = *reinterpret_cast<const float4 *>(pin + (size_t)y * nx + cxl);
-        P[r][0] = v.x; P[r][1] = v.y; P[r][2] = v.z; P[r][3] = v.w;
-    }
+        for (int r = 0; r < SRR + 2; ++r) {
+            const float4 v = *reinterpret_cast<const float4 *>(src + (size_t)r * nx);
+            P[r][0] = v.x; P[r][1] = v.y; P[r][2] = v.z; P[r][3] = v.w;
+        }
+        const float *bsrc = a.b + (size_t)(y0 + ry0) * nx + cx;
 #pragma unroll
-    for (int r = 0; r < SRR; ++r) {
-        int y = y0 + ry0 + r;
-        bool rowin = (unsigned)y < (unsigned)ny;
-        if (per_y && !rowin) { y = wrap_mod(y, ny); rowin = true; }
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (rowin && colin) v = *reinterpret_cast<const float4 *>(a.b + (size_t)y * nx + cxl);
-        if (!edge) { v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f; }
-        float2 *row = reinterpret_cast<float2 *>(bs + r * SRW);
-        row[lane] = make_float2(v.x, v.z);
-        row[32 + lane] = make_float2(v.y, v.w);
+        for (int r = 0; r < SRR; ++r) {
+            float4 v = *reinterpret_cast<const float4 *>(bsrc + (size_t)r * nx);
+            v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f;
+            float2 *row = reinterpret_cast<float2 *>(bs + r * SRW);
+            row[lane] = make_float2(v.x, v.z);
+            row[32 + lane] = make_float2(v.y, v.w);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < SRR + 2; ++r) {
+            int y = y0 + ry0 + r - 1;
+            bool rowin = (unsigned)y < (unsigned)ny;
+            if (per_y && !rowin) { y = wrap_mod(y, ny); rowin = true; }   // periodic copy
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rowin && colin) v = *reinterpret_cast<const float4 *>(pin + (size_t)y * nx + cxl);
+            P[r][0] = v.x; P[r][1] = v.y; P[r][2] = v.z; P[r][3] = v.w;
+        }
+#pragma unroll
+        for (int r = 0; r < SRR; ++r) {
+            int y = y0 + ry0 + r;
+            bool rowin = (unsigned)y < (unsigned)ny;
+            if (per_y && !rowin) { y = wrap_mod(y, ny); rowin = true; }
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rowin && colin) v = *reinterpret_cast<const float4 *>(a.b + (size_t)y * nx + cxl);
+            if (!edge) { v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f; }
+            float2 *row = reinterpret_cast<float2 *>(bs + r * SRW);
+            row[lane] = make_float2(v.x, v.z);
+            row[32 + lane] = make_float2(v.y, v.w);
+        }
     }
     if (PROLONG) {
         const float mean = a.use_mean ? (float)a.st->mean_e : 0.f;
@@ -346,6 +402,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         }
     }
 
+    if (!EDGE && pf_id >= 0) prefetch_tile(a, pin, pf_id);
+
     // 2. 2K half-sweeps, red ((x+y) even) first
     const int base = (x0 + y0 + ry0) & 1;      // colour parity of (column 0, row 0) of this warp
     for (int s = 0; s < 2 * a.K; ++s) {
@@ -356,7 +414,18 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
     }
 
     // 3. write back the valid tile (rows [H, H+TH), columns [Hc, Hc+TW) of the region)
-    if (colvalid) {
+    if (!EDGE) {
+        if (SNC * lane >= Hc && SNC * lane < Hc + TW) {
+            float *dst = pout + (size_t)(y0 + ry0) * nx + cx;
+#pragma unroll
+            for (int r = 0; r < SRR; ++r) {
+                const int rr = ry0 + r;
+                if (rr >= H && rr < H + TH)
+                    *reinterpret_cast<float4 *>(dst + (size_t)r * nx) =
+                        make_float4(P[r + 1][0], P[r + 1][1], P[r + 1][2], P[r + 1][3]);
+            }
+        }
+    } else if (colvalid) {
 #pragma unroll
         for (int r = 0; r < SRR; ++r) {
             const int rr = ry0 + r, y = y0 + rr;
@@ -446,9 +515,11 @@ __global__ void __launch_bounds__(STHREADS, 2) k_sweep32(SweepArgs a)
     if (a.skip && *a.skip) return;
     if (EDGE) {
         const int2 t = a.edge_tiles[blockIdx.x];
-        sweep_tile<PROLONG, RESID, EDGE>(a, t.x, t.y);
+        sweep_tile<PROLONG, RESID, EDGE>(a, t.x, t.y, -1);
     } else {
-        sweep_tile<PROLONG, RESID, EDGE>(a, blockIdx.x + a.ix0, blockIdx.y + a.iy0);
+        const int id = blockIdx.y * gridDim.x + blockIdx.x;
+        sweep_tile<PROLONG, RESID, EDGE>(a, blockIdx.x + a.ix0, blockIdx.y + a.iy0,
+                                         a.pf_ahead > 0 ? id + a.pf_ahead : -1);
     }
 }
 
@@ -461,7 +532,7 @@ __global__ void __launch_bounds__(STHREADS, 2) k_sweep32_batch(const SweepArgs *
     const int4 w = work[blockIdx.x];
     const SweepArgs &a = table[w.x];
     if (a.skip && *a.skip) return;
-    sweep_tile<PROLONG, RESID, EDGE>(a, w.y, w.z);
+    sweep_tile<PROLONG, RESID, EDGE>(a, w.y, w.z, -1);
 }
 
 // Sum of the 4 partial block sums (fixed order) -> R (ncy x ncx).
