@@ -785,6 +785,24 @@ def run_rollout(ism, dev):
             "rollout_forward_and_gradient_s": round(e0.elapsed_time(e1) / 1000.0, 3), "final_enstrophy": loss}
 
 
+def run_tolc(args):
+    """The paper's Benchmark I (500^2 cavity with counter-moving walls) with
+    its accommodative strategy: average synchronisation counts and Laplacians
+    per step over the first steps, for three coarse criteria and three
+    coarsenings (the full sweep: python -m paper_1309_7128_gb300.tolc_study)."""
+    from paper_1309_7128_gb300 import tolc_study
+    rows = [tolc_study.run(500, m, t, args.tolc_steps) for m in (8, 16, 32) for t in (1e-6, 1e-5, 1e-4)]
+    for r in rows:
+        r.pop("first_steps", None)
+        for k in ("I_c", "I_f", "NCC_f", "NCC_c", "NCC_t", "N_Lap"):
+            r[k] = round(r[k], 2)
+    return {"workload": f"Benchmark I: 500x500 cavity, counter-moving walls, nu=0.1, v0=0.1, h=dt=1, first "
+                        f"{args.tolc_steps} steps from rest; FP64 accommodative solve (coarse GS to tol_c, fine "
+                        f"sweeps to max|r| <= 1e-6), warm start",
+            "measures": "NCC_f = 2 I_f, NCC_c = I_c, NCC_t = NCC_f + NCC_c, N_Lap = I_f + I_c / m^2 (averages per step)",
+            "rows": rows}
+
+
 # ------------------------------------------------------------------ our implementation
 
 def run_ours(args):
@@ -889,6 +907,7 @@ def run_ours(args):
             out["config0"] = run_config0(ism, dev, args)
             out["batched256"] = run_batched(ism, dev, args)
             out["rollout512"] = run_rollout(ism, dev)
+            out["bench1_accommodative"] = run_tolc(args)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -977,6 +996,7 @@ def main():
     ap.add_argument("--extra-steps", type=int, default=10, help="timed steps of the cavity comparison")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample time on all cores")
     ap.add_argument("--ref-cycles", type=int, default=3)
+    ap.add_argument("--tolc-steps", type=int, default=20, help="Benchmark I steps per (m, tol_c) pair")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 8192x4096 Neumann pass measurements")
     ap.add_argument("--no-extras", action="store_true", help="skip the cavity, config-0, batched and rollout keys")

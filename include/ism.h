@@ -107,7 +107,9 @@ typedef struct {
                              accom_tol_c, bilinear correction, red-black sweeps on the fine grid until
                              max |r| <= tol (ism_solve's tol is then an absolute maximum norm and
                              max_cycles caps the fine sweeps).  A periodic axis then needs an even
-                             number of coarse cells. */
+                             number of coarse cells; a grid that is not a multiple of coarsen takes
+                             it with walls only (its coarse coefficients are those of
+                             A_c = W_y x T_x + T_y x W_x, see ism_setup). */
     double accom_tol_c;   /* cycle 1: coarse criterion (absolute maximum norm, default 1e-5) */
     int accom_max_coarse; /* cycle 1: cap on coarse Gauss-Seidel iterations (default 100000) */
     int stream;           /* single precision: 1 runs the passes that carry neither the correction
@@ -135,9 +137,10 @@ const char *ism_status_str(ism_status s);
  *            does not divide nx (ny), the last coarse column (row) is
  *            narrower (Sec. 3.3: padding, interpolation rectangles of
  *            different sizes; the coarse centre sits at the middle of its
- *            cell); such grids take the ISM and ACM coarse operators and the
- *            correction-scheme cycle (ism_set_options rejects GMG, the deep
- *            ACM V-cycle and cycle 1 there) and ISM_MIXED needs nx % 4 == 0.
+ *            cell); such grids take the ISM and ACM coarse operators, the
+ *            correction-scheme cycle and, with walls only, the accommodative
+ *            cycle 1 (ism_set_options rejects GMG and the deep ACM V-cycle
+ *            there) and ISM_MIXED needs nx % 4 == 0.
  *   h        cell size (used by proj_step only; > 0).
  *   bc       host, 4 ints (ism_bc) for the west, east, south, north faces;
  *            ISM_BC_PERIODIC on both faces of an axis or on neither, and

@@ -16,7 +16,10 @@
 // a Neumann end and 1 at a Dirichlet-0 end, circulant on a periodic axis
 // (whose neighbours then wrap; such an axis has an even number >= 4 of
 // coarse cells, so the nine neighbours are distinct and the four colours
-// independent).
+// independent).  When the grid is not a multiple of m (a narrower last
+// coarse cell, walls only) A_c = W_y x T_x + T_y x W_x with the tridiagonal
+// 1-D operators W = R1 P1 and T = R1 T1 P1 of each axis (ism_pencil.cu),
+// passed in as `tri`.
 #include <math.h>
 #include <string.h>
 
@@ -48,8 +51,14 @@ __device__ __forceinline__ double s_entry(int I, int d, int n, int lo_dir, int h
 }
 
 // coefficient of e[J + dJ][I + dI] (wrapped on a periodic axis) in row (I, J) of A_c
-__device__ __forceinline__ double ac_coef(int I, int J, int dI, int dJ, int ncx, int ncy, int bcmask)
+__device__ __forceinline__ double ac_coef(int I, int J, int dI, int dJ, int ncx, int ncy, int bcmask,
+                                          const double *tri)
 {
+    if (tri) {   // W_x, T_x (3 ncx each), W_y, T_y (3 ncy each): row k as (k-1, k, k+1)
+        const double *Wx = tri, *Tx = tri + 3 * ncx, *Wy = tri + 6 * ncx, *Ty = Wy + 3 * ncy;
+        return __dadd_rn(__dmul_rn(Wy[3 * J + 1 + dJ], Tx[3 * I + 1 + dI]),
+                         __dmul_rn(Ty[3 * J + 1 + dJ], Wx[3 * I + 1 + dI]));
+    }
     const double sx = s_entry(I, dI, ncx, bcmask & 1, bcmask & 2, (bcmask & ISM_PER_X) != 0);
     const double sy = s_entry(J, dJ, ncy, bcmask & 4, bcmask & 8, (bcmask & ISM_PER_Y) != 0);
     double a = __dmul_rn(0.25, __dmul_rn(sx, sy));
@@ -60,7 +69,7 @@ __device__ __forceinline__ double ac_coef(int I, int J, int dI, int dJ, int ncx,
 // row sum over the nine neighbours (dJ = -1..1, dI = -1..1), optionally
 // without the centre
 __device__ __forceinline__ double row_sum(const double *e, int I, int J, int ncx, int ncy, int bcmask,
-                                          bool centre)
+                                          bool centre, const double *tri)
 {
     double s = 0.0;
     for (int dJ = -1; dJ <= 1; ++dJ)
@@ -69,21 +78,34 @@ __device__ __forceinline__ double row_sum(const double *e, int I, int J, int ncx
             if (bcmask & ISM_PER_Y) K = K < 0 ? K + ncy : (K >= ncy ? K - ncy : K);
             if (bcmask & ISM_PER_X) L = L < 0 ? L + ncx : (L >= ncx ? L - ncx : L);
             if ((!centre && dI == 0 && dJ == 0) || K < 0 || K >= ncy || L < 0 || L >= ncx) continue;
-            s = __dadd_rn(s, __dmul_rn(ac_coef(I, J, dI, dJ, ncx, ncy, bcmask), e[(size_t)K * ncx + L]));
+            s = __dadd_rn(s, __dmul_rn(ac_coef(I, J, dI, dJ, ncx, ncy, bcmask, tri), e[(size_t)K * ncx + L]));
         }
     return s;
 }
 
 // One CTA: e = 0, then Gauss-Seidel iterations until the criterion or the
-// cap; the iteration count goes to st->outer.
+// cap; the iteration count goes to st->outer.  SMEM: the iterate and the
+// right-hand side live in dynamic shared memory during the iteration (coarse
+// grids up to AC_SMEM_MAX cells), e is written back at the end.
+constexpr int AC_SMEM_MAX = 12800;             // 2 x 8 B x 12800 = 200 KB
+
+template <bool SMEM>
 __global__ void __launch_bounds__(AC_THREADS, 1)
-k_coarse_gs4(const double *__restrict__ r, double *__restrict__ e, int ncx, int ncy, int bcmask, double tol,
-             int cap, IsmState *st)
+k_coarse_gs4(const double *__restrict__ r_g, double *__restrict__ e_g, int ncx, int ncy, int bcmask, double tol,
+             int cap, IsmState *st, const double *__restrict__ tri)
 {
     if (st->done) return;
+    extern __shared__ double ac_sm[];
     __shared__ double red[32];
     __shared__ int stop;
     const int t = threadIdx.x, nc = ncx * ncy;
+    double *e = SMEM ? ac_sm : e_g;
+    const double *r = r_g;
+    if (SMEM) {
+        double *rs = ac_sm + nc;
+        for (int k = t; k < nc; k += AC_THREADS) rs[k] = r_g[k];
+        r = rs;
+    }
     for (int k = t; k < nc; k += AC_THREADS) e[k] = 0.0;
     __syncthreads();
     int it = 0;
@@ -91,7 +113,7 @@ k_coarse_gs4(const double *__restrict__ r, double *__restrict__ e, int ncx, int 
         double mx = 0.0;
         for (int k = t; k < nc; k += AC_THREADS) {
             const int I = k % ncx, J = k / ncx;
-            const double d = fabs(__dadd_rn(r[k], -row_sum(e, I, J, ncx, ncy, bcmask, true)));
+            const double d = fabs(__dadd_rn(r[k], -row_sum(e, I, J, ncx, ncy, bcmask, true, tri)));
             mx = fmax(mx, d);
         }
         for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(FULLMASK, mx, o));
@@ -109,14 +131,16 @@ k_coarse_gs4(const double *__restrict__ r, double *__restrict__ e, int ncx, int 
             const int hx = (ncx - I0 + 1) / 2, hy = (ncy - J0 + 1) / 2;
             for (int k = t; k < hx * hy; k += AC_THREADS) {
                 const int I = I0 + 2 * (k % hx), J = J0 + 2 * (k / hx);
-                const double s = row_sum(e, I, J, ncx, ncy, bcmask, false);
+                const double s = row_sum(e, I, J, ncx, ncy, bcmask, false, tri);
                 e[(size_t)J * ncx + I] =
-                    __ddiv_rn(__dadd_rn(r[(size_t)J * ncx + I], -s), ac_coef(I, J, 0, 0, ncx, ncy, bcmask));
+                    __ddiv_rn(__dadd_rn(r[(size_t)J * ncx + I], -s), ac_coef(I, J, 0, 0, ncx, ncy, bcmask, tri));
             }
             __syncthreads();
         }
         ++it;
     }
+    if (SMEM)
+        for (int k = t; k < nc; k += AC_THREADS) e_g[k] = e[k];
     if (t == 0) st->outer = it;
 }
 
@@ -200,8 +224,24 @@ ism_status ism_solve_accommodative(ism_ctx *ctx, double tol, int max_sweeps)
                                                                      ctx->nx, ctx->ny, ctx->m, ctx->bcmask,
                                                                      &ctx->st->done);
         ISM_LAUNCH_CHECK(ctx);
-        k_coarse_gs4<<<1, AC_THREADS, 0, ctx->ws>>>(ctx->rc64, ctx->ec64, ctx->ncx, ctx->ncy, ctx->bcmask,
-                                                    ctx->opt.accom_tol_c, ctx->opt.accom_max_coarse, ctx->st);
+        const int nc = ctx->ncx * ctx->ncy;
+        const double *tri = ctx->ragged ? ctx->ac_tri : nullptr;
+        if (nc <= AC_SMEM_MAX) {
+            const size_t smb = 2 * sizeof(double) * (size_t)nc;
+            static bool attr = false;
+            if (!attr) {
+                cudaFuncSetAttribute(k_coarse_gs4<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(2 * sizeof(double) * AC_SMEM_MAX));
+                attr = true;
+            }
+            k_coarse_gs4<true><<<1, AC_THREADS, smb, ctx->ws>>>(ctx->rc64, ctx->ec64, ctx->ncx, ctx->ncy, ctx->bcmask,
+                                                                ctx->opt.accom_tol_c, ctx->opt.accom_max_coarse,
+                                                                ctx->st, tri);
+        } else {
+            k_coarse_gs4<false><<<1, AC_THREADS, 0, ctx->ws>>>(ctx->rc64, ctx->ec64, ctx->ncx, ctx->ncy, ctx->bcmask,
+                                                               ctx->opt.accom_tol_c, ctx->opt.accom_max_coarse,
+                                                               ctx->st, tri);
+        }
         ISM_LAUNCH_CHECK(ctx);
         k_prolong<double><<<dim3((ctx->nx + 127) / 128, ctx->ny), 128, 0, ctx->ws>>>(
             ctx->p64[0], ctx->ec64, ctx->nx, ctx->ny, ctx->m, ctx->ncx, ctx->ncy, ctx->bcmask, ISM_COARSE_ISM,

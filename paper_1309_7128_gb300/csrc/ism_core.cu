@@ -447,7 +447,7 @@ extern "C" void ism_destroy(ism_ctx *ctx)
                     ctx->p64[1], ctx->e32[0], ctx->e32[1], ctx->r32, ctx->rc64, ctx->ec64,
                     ctx->T64, ctx->rc32, ctx->ec32, ctx->T32, ctx->partials, ctx->st,
                     ctx->st_k, ctx->us, ctx->vs, ctx->dp, ctx->rcpart, ctx->roll, ctx->scal,
-                    ctx->tc_block, ctx->G64};
+                    ctx->tc_block, ctx->G64, ctx->ac_tri};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int l = 0; l < 6; ++l) {
@@ -629,9 +629,10 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     if (o->stream < 0 || o->stream > 1) return ISM_ERR_ARG;
     if (o->fault_test < 0 || o->fault_test > 1) return ISM_ERR_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
-    // a narrower last coarse cell: the ISM and ACM operators, correction-scheme cycle
-    if (ctx->ragged && (o->kind == ISM_COARSE_GMG || o->kind == ISM_COARSE_ACMV || o->cycle == 1))
-        return ISM_ERR_ARG;
+    // a narrower last coarse cell: the ISM and ACM operators; the accommodative
+    // cycle with walls only (its coarse coefficients come from the 1-D W, T)
+    if (ctx->ragged && (o->kind == ISM_COARSE_GMG || o->kind == ISM_COARSE_ACMV)) return ISM_ERR_ARG;
+    if (ctx->ragged && o->cycle == 1 && (ctx->bcmask & (ISM_PER_X | ISM_PER_Y))) return ISM_ERR_ARG;
     const int kind_changed = o->kind != ctx->opt.kind;
     EigenHost E;
     if (kind_changed && build_eigen(ctx, o->kind, E) != ISM_OK) return ISM_ERR_ARG;
@@ -646,6 +647,20 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
                 return ISM_ERR_NOMEM;
             }
         }
+    }
+    if (o->cycle == 1 && ctx->ragged && !ctx->ac_tri) {
+        const int ncx = ctx->ncx, ncy = ctx->ncy;
+        std::vector<double> t(6 * (size_t)(ncx + ncy));
+        if (!ism_axis_tridiag(ctx->nx, ctx->m, ctx->bc[0], ctx->bc[1], ISM_COARSE_ISM, t.data(), t.data() + 3 * ncx) ||
+            !ism_axis_tridiag(ctx->ny, ctx->m, ctx->bc[2], ctx->bc[3], ISM_COARSE_ISM, t.data() + 6 * ncx,
+                              t.data() + 6 * ncx + 3 * ncy))
+            return ISM_ERR_ARG;
+        if (cudaMalloc((void **)&ctx->ac_tri, t.size() * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            ctx->ac_tri = nullptr;
+            return ISM_ERR_NOMEM;
+        }
+        ISM_CUDA_TRY(cudaMemcpy(ctx->ac_tri, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
     ctx->opt = *o;
     ctx->opt_gen++;

@@ -80,6 +80,7 @@ struct ism_ctx {
     int max_blocks;
     IsmState *st;              // device control block
     IsmState *st_k;            // device control block for kernel-level entry points
+    double *ac_tri;            // cycle 1 on a grid not a multiple of m: W_x, T_x, W_y, T_y (3 per coarse row)
     IsmState *st_host;         // pinned host copy (selected fields are read back)
 
     // tile plans of the fused sweep pass, per (sweeps K, residual fused)
@@ -159,6 +160,9 @@ struct IsmAxisFactor {
 // (not periodic); kind: ism_coarse_kind (ISM or ACM).  false when a
 // numerical check fails.
 bool ism_axis_factor(int n, int m, int lo, int hi, int kind, IsmAxisFactor &F);
+// The tridiagonal W = R1 P1 and T = R1 T1 P1 of such an axis, row k as
+// (A[k][k-1], A[k][k], A[k][k+1]) at 3k .. 3k+2 of W3, T3 (host, 3 nc each).
+bool ism_axis_tridiag(int n, int m, int lo, int hi, int kind, double *W3, double *T3);
 
 ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarsen, ism_precision prec,
                            void *stream, ism_ctx **out);

@@ -158,14 +158,10 @@ bool invert(std::vector<double> A, int n, std::vector<double> &X)
 
 }  // namespace
 
-bool ism_axis_factor(int n, int m, int lo, int hi, int kind, IsmAxisFactor &F)
+namespace {
+// W = R1 P1 and T = R1 T1 P1 of one axis, accumulated over its fine cells
+bool axis_tri(int n, int m, int lo_dir, int hi_dir, bool constant, Tri &W, Tri &T)
 {
-    const int nc = ncoarse(n, m);
-    if (nc < 2 || lo == ISM_BC_PERIODIC || hi == ISM_BC_PERIODIC) return false;
-    const int lo_dir = lo == ISM_BC_DIRICHLET0, hi_dir = hi == ISM_BC_DIRICHLET0;
-    const bool constant = kind == ISM_COARSE_ACM;
-    // W = R1 P1 and T = R1 T1 P1 accumulated over fine cells
-    Tri W(nc), T(nc);
     for (int i = 0; i < n; ++i) {
         int idx[2], jdx[2];
         double w[2], wj[2];
@@ -186,7 +182,30 @@ bool ism_axis_factor(int n, int m, int lo, int hi, int kind, IsmAxisFactor &F)
         }
         for (int s = 0; s < np; ++s) T.add(K, idx[s], diag * w[s]);
     }
-    if (W.bad || T.bad) return false;
+    return !(W.bad || T.bad);
+}
+}  // namespace
+
+bool ism_axis_tridiag(int n, int m, int lo, int hi, int kind, double *W3, double *T3)
+{
+    const int nc = ncoarse(n, m);
+    if (nc < 2 || lo == ISM_BC_PERIODIC || hi == ISM_BC_PERIODIC) return false;
+    Tri W(nc), T(nc);
+    if (!axis_tri(n, m, lo == ISM_BC_DIRICHLET0, hi == ISM_BC_DIRICHLET0, kind == ISM_COARSE_ACM, W, T)) return false;
+    for (int k = 0; k < nc; ++k) {
+        W3[3 * k] = W.l[k]; W3[3 * k + 1] = W.d[k]; W3[3 * k + 2] = W.u[k];
+        T3[3 * k] = T.l[k]; T3[3 * k + 1] = T.d[k]; T3[3 * k + 2] = T.u[k];
+    }
+    return true;
+}
+
+bool ism_axis_factor(int n, int m, int lo, int hi, int kind, IsmAxisFactor &F)
+{
+    const int nc = ncoarse(n, m);
+    if (nc < 2 || lo == ISM_BC_PERIODIC || hi == ISM_BC_PERIODIC) return false;
+    const int lo_dir = lo == ISM_BC_DIRICHLET0, hi_dir = hi == ISM_BC_DIRICHLET0;
+    Tri W(nc), T(nc);
+    if (!axis_tri(n, m, lo_dir, hi_dir, kind == ISM_COARSE_ACM, W, T)) return false;
 
     // eigenvalues: bracket (-inf, 0], bisection on the pivot count
     double lb = -1.0;

@@ -50,7 +50,8 @@ def _check(fn, outer, missing):
             _check(f, local, missing)
 
 
-@pytest.mark.parametrize("path", ["bench.py", "paper_1309_7128_gb300/timepass.py"])
+@pytest.mark.parametrize("path", ["bench.py", "paper_1309_7128_gb300/timepass.py",
+                                  "paper_1309_7128_gb300/tolc_study.py"])
 def test_functions_read_only_bound_names(path):
     tree = ast.parse(open(os.path.join(ROOT, path)).read())
     module = set(dir(builtins)) | {"__file__", "__name__"}

@@ -92,7 +92,11 @@ def test_deep_acm_vcycle_matches_oracle(nx, ny, m, bc):
 
 
 @pytest.mark.parametrize("nx,ny,m,bc", [(256, 192, 16, (0, 0, 0, 0)), (128, 128, 8, (0, 1, 0, 0)),
-                                         (160, 96, 32, (1, 1, 1, 1))])
+                                         (160, 96, 32, (1, 1, 1, 1)),
+                                         # not multiples of m (narrower last coarse cell): Bench I's 500^2
+                                         (500, 500, 8, (0, 0, 0, 0)), (500, 500, 16, (0, 0, 0, 0)),
+                                         (500, 500, 32, (0, 0, 0, 0)), (150, 90, 16, (0, 1, 0, 0)),
+                                         (200, 120, 32, (1, 1, 1, 1))])
 def test_accommodative_strategy_matches_oracle(nx, ny, m, bc):
     """The paper's accommodative strategy (cycle = 1, FP64): the same number
     of coarse Gauss-Seidel iterations as the oracle (the coarse arithmetic is
@@ -109,8 +113,10 @@ def test_accommodative_strategy_matches_oracle(nx, ny, m, bc):
     assert s == ism.ISM_OK and mx <= tol_f
     assert outer == nc_ref and cycles == nf_ref
     assert rel(host(p), p_ref) <= 1e-10
-    # options: FP64 with the ISM coarse operator only
+    # options: FP64 with the ISM coarse operator only (mixed contexts need nx % 4 == 0)
     for prec, kind in ((ism.ISM_MIXED, 0), (ism.ISM_FP64, ism.ISM_COARSE_ACM)):
+        if prec == ism.ISM_MIXED and nx % 4:
+            continue
         c2 = setup(nx, ny, m, bc, prec=prec)
         o = ism.ism_get_options(c2)
         o.cycle, o.kind = 1, kind
