@@ -123,6 +123,10 @@ typedef struct {
                              (about 0.2 s); the wait runs out, the kernel records the failure, lets
                              its bulk copies finish, frees its tensor memory and returns, and the
                              solve stops with ISM_ERR_CUDA.  The CUDA context stays usable. */
+    int tile_rows;        /* single precision: height of the register-tiled region of the fused pass,
+                             128 (default: 8 warps, two CTAs per SM) or 256 (16 warps, one CTA per
+                             SM; less halo overlap, 1.52x instead of 1.78x the cells at 8 sweeps);
+                             ism_autotune tries both.  The batched solve uses 128. */
 } ism_options;
 
 typedef struct ism_ctx ism_ctx;
@@ -189,8 +193,9 @@ ism_status ism_solve(ism_ctx *ctx, const double *rhs, double *p, double tol,
                      int max_cycles, int *cycles_out, double *relres_out);
 
 /* ism_autotune -- choose the sweeps per cycle and per fused pass (and, for
- * ISM_MIXED, whether the middle passes stream and the refinement's inner
- * stopping factor inner_tol) for this context by timing complete solves of
+ * ISM_MIXED, whether the middle passes stream, the refinement's inner
+ * stopping factor inner_tol and the height of the fused pass's tiled region,
+ * tile_rows) for this context by timing complete solves of
  * rhs (device, nx*ny doubles) from a zero initial guess over a fixed
  * candidate list; keeps the fastest candidate in the context's options and
  * copies it to *best (host, may be NULL).  No counterpart in the paper (its

@@ -254,6 +254,7 @@ static void default_options(ism_options *o, int prec)
     o->accom_max_coarse = 100000;
     o->stream = 0;
     o->fault_test = 0;
+    o->tile_rows = 128;
 }
 
 static const double kPi = 3.14159265358979323846;
@@ -456,7 +457,8 @@ extern "C" void ism_destroy(ism_ctx *ctx)
     }
     for (int K = 0; K <= SMAXK; ++K)
         for (int r = 0; r < 2; ++r)
-            if (ctx->plans[K][r].edge) cudaFree(ctx->plans[K][r].edge);
+            for (int t = 0; t < 2; ++t)
+                if (ctx->plans[t][K][r].edge) cudaFree(ctx->plans[t][K][r].edge);
     if (ctx->st_host) cudaFreeHost(ctx->st_host);
     if (ctx->ev_in) cudaEventDestroy(ctx->ev_in);
     if (ctx->ev_out) cudaEventDestroy(ctx->ev_out);
@@ -468,6 +470,21 @@ extern "C" void ism_destroy(ism_ctx *ctx)
 }
 
 static ism_status make_plans(ism_ctx *ctx);
+
+// Dynamic shared memory of every fused-pass kernel of a region of NW warps.
+template <int NW>
+static void set_sweep_smem()
+{
+    const int smb = (int)sweep_smem_bytes(NW);
+    cudaFuncSetAttribute(k_sweep32<NW, true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<NW, true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<NW, false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<NW, false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<NW, true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<NW, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<NW, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<NW, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+}
 
 
 ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarsen, ism_precision prec,
@@ -578,19 +595,13 @@ ism_status ism_setup_fixed(int nx, int ny, double h, const int bc[4], int coarse
         ism_destroy(ctx);
         return s;
     }
-    // the fused sweep pass uses 80 KB of dynamic shared memory
-    const int smb = (int)sweep_smem_bytes();
+    // the fused sweep pass uses 91 KB (128-row region) or 180 KB (256-row)
+    // of dynamic shared memory
     ism_coarse_tc_prepare();
     restrict_stream_attrs<float>();
     restrict_stream_attrs<double>();
-    cudaFuncSetAttribute(k_sweep32<true, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
-    cudaFuncSetAttribute(k_sweep32<true, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
-    cudaFuncSetAttribute(k_sweep32<false, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
-    cudaFuncSetAttribute(k_sweep32<false, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
-    cudaFuncSetAttribute(k_sweep32<true, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
-    cudaFuncSetAttribute(k_sweep32<true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
-    cudaFuncSetAttribute(k_sweep32<false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
-    cudaFuncSetAttribute(k_sweep32<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    set_sweep_smem<8>();
+    set_sweep_smem<16>();
     if ((s = make_plans(ctx)) != ISM_OK) {
         ism_destroy(ctx);
         return s;
@@ -628,6 +639,7 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     if (!(o->accom_tol_c > 0.0) || o->accom_max_coarse < 1) return ISM_ERR_ARG;
     if (o->stream < 0 || o->stream > 1) return ISM_ERR_ARG;
     if (o->fault_test < 0 || o->fault_test > 1) return ISM_ERR_ARG;
+    if (o->tile_rows != 128 && o->tile_rows != 256) return ISM_ERR_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
     // a narrower last coarse cell: the ISM and ACM operators; the accommodative
     // cycle with walls only (its coarse coefficients come from the 1-D W, T)
@@ -798,15 +810,17 @@ using SweepPlan = ism_ctx::SweepPlan;
 
 static SweepPlan &sweep_plan(ism_ctx *ctx, int K, bool resid)
 {
-    return ctx->plans[K][resid ? 1 : 0];
+    return ctx->plans[ctx->opt.tile_rows == 256 ? 1 : 0][K][resid ? 1 : 0];
 }
 
 static ism_status make_plans(ism_ctx *ctx)
 {
+    for (int shape = 0; shape < 2; ++shape)
     for (int K = 0; K <= SMAXK; ++K)
         for (int r = 0; r < 2; ++r) {
-            SweepPlan &P = ctx->plans[K][r];
-            const int tw = sweep_tile_w(K, r), th = sweep_tile_h(K, r);
+            SweepPlan &P = ctx->plans[shape][K][r];
+            const int nw = shape ? 16 : 8, rh = nw * SRR;
+            const int tw = sweep_tile_w(K, r), th = sweep_tile_h(K, r, nw);
             const int Hc = sweep_halo_cols(K, r), H = sweep_halo(K, r);
             P.gx = (ctx->nx + tw - 1) / tw;
             P.gy = (ctx->ny + th - 1) / th;
@@ -815,7 +829,7 @@ static ism_status make_plans(ism_ctx *ctx)
             P.ix0 = lo(tw, Hc);
             P.iy0 = lo(th, H);
             P.ix1 = P.ix0; while (P.ix1 < P.gx && P.ix1 * tw - Hc + SRW <= ctx->nx - 1) ++P.ix1;
-            P.iy1 = P.iy0; while (P.iy1 < P.gy && P.iy1 * th - H + SRH <= ctx->ny - 1) ++P.iy1;
+            P.iy1 = P.iy0; while (P.iy1 < P.gy && P.iy1 * th - H + rh <= ctx->ny - 1) ++P.iy1;
             if (P.ix1 <= P.ix0 || P.iy1 <= P.iy0) { P.ix1 = P.ix0; P.iy1 = P.iy0; }
             std::vector<int2> e;
             for (int by = 0; by < P.gy; ++by)
@@ -848,24 +862,30 @@ static int ism_sm_count()
 
 // Interior and edge launches of one pass run concurrently: the edge launch
 // goes to a forked stream joined back before the next kernel.
-template <bool PR, bool RE>
+template <int NW, bool PR, bool RE>
 static ism_status launch_sweep_pair(ism_ctx *ctx, const SweepArgs &a, const SweepPlan &P)
 {
-    const size_t sm = sweep_smem_bytes();
+    const size_t sm = sweep_smem_bytes(NW);
     const bool both = P.ix1 > P.ix0 && P.nedge > 0;
     if (both) {
         ISM_CUDA_TRY(cudaEventRecord(ctx->ev_fork, ctx->ws));
         ISM_CUDA_TRY(cudaStreamWaitEvent(ctx->ws2, ctx->ev_fork, 0));
-        k_sweep32<PR, RE, true><<<P.nedge, STHREADS, sm, ctx->ws2>>>(a);
-        k_sweep32<PR, RE, false><<<dim3(P.ix1 - P.ix0, P.iy1 - P.iy0), STHREADS, sm, ctx->ws>>>(a);
+        k_sweep32<NW, PR, RE, true><<<P.nedge, 32 * NW, sm, ctx->ws2>>>(a);
+        k_sweep32<NW, PR, RE, false><<<dim3(P.ix1 - P.ix0, P.iy1 - P.iy0), 32 * NW, sm, ctx->ws>>>(a);
         ISM_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->ws2));
         ISM_CUDA_TRY(cudaStreamWaitEvent(ctx->ws, ctx->ev_join, 0));
     } else if (P.ix1 > P.ix0) {
-        k_sweep32<PR, RE, false><<<dim3(P.ix1 - P.ix0, P.iy1 - P.iy0), STHREADS, sm, ctx->ws>>>(a);
+        k_sweep32<NW, PR, RE, false><<<dim3(P.ix1 - P.ix0, P.iy1 - P.iy0), 32 * NW, sm, ctx->ws>>>(a);
     } else {
-        k_sweep32<PR, RE, true><<<P.nedge, STHREADS, sm, ctx->ws>>>(a);
+        k_sweep32<NW, PR, RE, true><<<P.nedge, 32 * NW, sm, ctx->ws>>>(a);
     }
     return ISM_OK;
+}
+
+template <bool PR, bool RE>
+static ism_status launch_sweep_pair(ism_ctx *ctx, const SweepArgs &a, const SweepPlan &P)
+{
+    return ctx->opt.tile_rows == 256 ? launch_sweep_pair<16, PR, RE>(ctx, a, P) : launch_sweep_pair<8, PR, RE>(ctx, a, P);
 }
 
 // Streaming pass (ism_stream32.cuh): strips of 128 columns, chunks of rows
@@ -907,9 +927,9 @@ static ism_status launch_sweep32(ism_ctx *ctx, SweepArgs a, bool prolong, bool r
     a.H = sweep_halo(a.K, resid);
     a.Hc = sweep_halo_cols(a.K, resid);
     a.TW = sweep_tile_w(a.K, resid);
-    a.TH = sweep_tile_h(a.K, resid);
+    a.TH = sweep_tile_h(a.K, resid, ctx->opt.tile_rows == 256 ? 16 : 8);
     a.gx = P.gx; a.gy = P.gy; a.ix0 = P.ix0; a.iy0 = P.iy0; a.edge_tiles = P.edge;
-    a.pf_ahead = 2 * ism_sm_count();            // one wave of resident CTAs (2 per SM) ahead
+    a.pf_ahead = (ctx->opt.tile_rows == 256 ? 1 : 2) * ism_sm_count();   // one wave of resident CTAs ahead
     a.pgx = P.ix1 - P.ix0;
     a.pn = a.pgx * (P.iy1 - P.iy0);
     if (!resid) a.ctl_mode = -1;
@@ -1580,12 +1600,13 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
                                         {256, 8, 0}, {16, 4, 0},  {32, 4, 1},  {64, 4, 1}, {128, 4, 1}};
     static const int cand_fp64[][3] = {{8, 4, 0}, {16, 4, 0}, {32, 4, 0}, {48, 4, 0}, {64, 4, 0}, {96, 4, 0},
                                        {128, 4, 0}};
-    // then, for the mixed winner, the inner stopping factor of the refinement
+    // then, for the mixed winner, the inner stopping factor of the refinement,
+    // and last the other height of the fused pass's tiled region (tile shape)
     static const double inner_tols[] = {1e-4, 1e-2};
     const int (*cand)[3] = ctx->prec == ISM_MIXED ? cand_mixed : cand_fp64;
     const int ncand = ctx->prec == ISM_MIXED ? (int)(sizeof(cand_mixed) / sizeof(cand_mixed[0]))
                                              : (int)(sizeof(cand_fp64) / sizeof(cand_fp64[0]));
-    const int ntol = ctx->prec == ISM_MIXED ? 2 : 0;
+    const int ntol = ctx->prec == ISM_MIXED ? 3 : 0;
     const ism_options saved = ctx->opt;
     double *p = nullptr;
     if (cudaMalloc((void **)&p, (size_t)ctx->n * 8) != cudaSuccess) { cudaGetLastError(); return ISM_ERR_NOMEM; }
@@ -1600,9 +1621,12 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
             opt.nu = cand[c][0];
             opt.sweeps_per_pass = cand[c][1];
             opt.stream = cand[c][2];
-        } else {
+        } else if (c < ncand + 2) {
             opt = win;
             opt.inner_tol = inner_tols[c - ncand];
+        } else {
+            opt = win;
+            opt.tile_rows = win.tile_rows == 256 ? 128 : 256;
         }
         if ((st = ism_set_options(ctx, &opt)) != ISM_OK) break;
         float ms = 0.f;

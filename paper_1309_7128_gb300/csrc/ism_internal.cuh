@@ -83,8 +83,8 @@ struct ism_ctx {
     double *ac_tri;            // cycle 1 on a grid not a multiple of m: W_x, T_x, W_y, T_y (3 per coarse row)
     IsmState *st_host;         // pinned host copy (selected fields are read back)
 
-    // tile plans of the fused sweep pass, per (sweeps K, residual fused)
-    struct SweepPlan { int gx, gy, ix0, ix1, iy0, iy1, nedge; int2 *edge; } plans[9][2];
+    // tile plans of the fused sweep pass, per (region height 128 | 256, sweeps K, residual fused)
+    struct SweepPlan { int gx, gy, ix0, ix1, iy0, iy1, nedge; int2 *edge; } plans[2][9][2];
 
     // CUDA graphs of a chunk of cycles
     cudaGraphExec_t g_fp64, g_inner;       // chunks of cycles (use_graphs = 1)

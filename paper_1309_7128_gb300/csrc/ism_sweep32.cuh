@@ -53,7 +53,7 @@
 
 constexpr int SNC = 4;                  // columns per thread
 constexpr int SRR = 16;                 // rows per warp
-constexpr int SNW = 8;                  // warps per CTA (a 16-warp, 256-row region was slower at 8192 x 4096)
+constexpr int SNW = 8;                  // warps per CTA of the default region (NW template parameter below)
 constexpr int SRW = 32 * SNC;           // region width 128
 constexpr int SRH = SNW * SRR;          // region height 128
 constexpr int STHREADS = 32 * SNW;      // 256
@@ -83,7 +83,10 @@ struct SweepArgs {
 __host__ __device__ inline int sweep_halo(int K, bool resid) { return 2 * K + (resid ? 1 : 0); }
 __host__ __device__ inline int sweep_halo_cols(int K, bool resid) { return (sweep_halo(K, resid) + 3) & ~3; }
 __host__ __device__ inline int sweep_tile_w(int K, bool resid) { return SRW - 2 * sweep_halo_cols(K, resid); }
-__host__ __device__ inline int sweep_tile_h(int K, bool resid) { return SRH - 2 * sweep_halo(K, resid); }
+__host__ __device__ inline int sweep_tile_h(int K, bool resid, int nw = SNW)
+{
+    return nw * SRR - 2 * sweep_halo(K, resid);
+}
 
 // Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
 __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
@@ -96,6 +99,7 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes)
 // region, clipped to the domain), so that the CTA that runs it about one
 // wave later finds them there instead of in HBM.  Same tile geometry as
 // sweep_tile.
+template <int NW>
 __device__ __forceinline__ void prefetch_tile(const SweepArgs &a, const float *pin, int id)
 {
     if (id >= a.pn) return;
@@ -104,10 +108,10 @@ __device__ __forceinline__ void prefetch_tile(const SweepArgs &a, const float *p
     const int xa = max(x0, 0), xb = min(x0 + SRW, a.nx);
     if (xb <= xa) return;
     const unsigned bytes = (unsigned)(xb - xa) * 4u;       // x0, nx multiples of 4: 16-byte pieces
-    for (int k = threadIdx.x; k < 2 * (SRH + 2); k += STHREADS) {
-        const bool isb = k >= SRH + 2;
-        const int y = y0 - 1 + (isb ? k - (SRH + 2) : k);
-        if ((unsigned)y >= (unsigned)a.ny || (isb && (y < y0 || y >= y0 + SRH))) continue;
+    for (int k = threadIdx.x; k < 2 * ((NW * SRR) + 2); k += (32 * NW)) {
+        const bool isb = k >= (NW * SRR) + 2;
+        const int y = y0 - 1 + (isb ? k - ((NW * SRR) + 2) : k);
+        if ((unsigned)y >= (unsigned)a.ny || (isb && (y < y0 || y >= y0 + (NW * SRR)))) continue;
         prefetch_l2((isb ? a.b : pin) + (size_t)y * a.nx + xa, bytes);
     }
 }
@@ -180,12 +184,13 @@ __device__ __forceinline__ void half_sweep(float (&P)[SRR + 2][SNC], const float
     }
 }
 
+template <int NW>
 __device__ __forceinline__ void exchange_rows(float (&P)[SRR + 2][SNC], float *xch, int buf,
                                               int w, int lane)
 {
     float4 *X = reinterpret_cast<float4 *>(xch);
-    // xch layout: [2 buffers][SNW warps][2 rows][32 lanes] float4
-    const int base = buf * SNW * 2 * 32;
+    // xch layout: [2 buffers][NW warps][2 rows][32 lanes] float4
+    const int base = buf * NW * 2 * 32;
     X[base + (w * 2 + 0) * 32 + lane] = make_float4(P[1][0], P[1][1], P[1][2], P[1][3]);
     X[base + (w * 2 + 1) * 32 + lane] = make_float4(P[SRR][0], P[SRR][1], P[SRR][2], P[SRR][3]);
     __syncthreads();
@@ -193,32 +198,33 @@ __device__ __forceinline__ void exchange_rows(float (&P)[SRR + 2][SNC], float *x
         const float4 v = X[base + ((w - 1) * 2 + 1) * 32 + lane];
         P[0][0] = v.x; P[0][1] = v.y; P[0][2] = v.z; P[0][3] = v.w;
     }
-    if (w < SNW - 1) {
+    if (w < NW - 1) {
         const float4 v = X[base + ((w + 1) * 2 + 0) * 32 + lane];
         P[SRR + 1][0] = v.x; P[SRR + 1][1] = v.y; P[SRR + 1][2] = v.z; P[SRR + 1][3] = v.w;
     }
 }
 
-// G rows needed by a region: its rows span at most SRH/8 + 3 coarse rows (m >= 8);
-// its columns at most SRW/8 + 3 coarse columns (e_c block staged before G)
-constexpr int SGROWS = SRH / 8 + 3;
+// G rows needed by a region of NW warps: its rows span at most 16 NW / 8 + 3
+// coarse rows (m >= 8); its columns at most SRW/8 + 3 coarse columns (e_c
+// block staged before G)
+__host__ __device__ constexpr int sweep_grows(int nw) { return nw * SRR / 8 + 3; }
 constexpr int SGCOLS = SRW / 8 + 3;
-inline size_t sweep_smem_bytes()
+inline size_t sweep_smem_bytes(int nw = SNW)
 {
-    return (size_t)SRH * SRW * 4 + (size_t)2 * SNW * 2 * SRW * 4 + (size_t)SGROWS * SRW * 4 +
-           (size_t)SGROWS * SGCOLS * 4;
+    return (size_t)nw * SRR * SRW * 4 + (size_t)2 * nw * 2 * SRW * 4 + (size_t)sweep_grows(nw) * SRW * 4 +
+           (size_t)sweep_grows(nw) * SGCOLS * 4;
 }
 
 // EDGE: the launch over the tiles whose region touches the domain boundary
 // (listed in edge_tiles); otherwise the launch over the interior tiles.
 // The pass on tile (bx, by) of the problem described by a; one CTA.
-template <bool PROLONG, bool RESID, bool EDGE>
+template <int NW, bool PROLONG, bool RESID, bool EDGE>
 __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, const int by, const int pf_id)
 {
     extern __shared__ __align__(16) float sm[];
-    float *bsm = sm;                       // SRH x SRW (b per thread, colour-pair order)
-    float *xch = sm + SRH * SRW;           // row exchange buffers
-    float *gsm = xch + 2 * SNW * 2 * SRW;  // coarse correction rows G[Jg0 ..] of this region
+    float *bsm = sm;                       // (NW * SRR) x SRW (b per thread, colour-pair order)
+    float *xch = sm + (NW * SRR) * SRW;           // row exchange buffers
+    float *gsm = xch + 2 * NW * 2 * SRW;  // coarse correction rows G[Jg0 ..] of this region
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nx = a.nx, ny = a.ny, H = a.H, Hc = a.Hc, TW = a.TW, TH = a.TH;
     const int x0 = bx * TW - Hc, y0 = by * TH - H;  // region origin, x0 % 4 == 0
@@ -269,14 +275,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
     float P[SRR + 2][SNC];
     const int m = a.m, lm = a.lm, hm = m >> 1;
     const bool acm = a.kind == ISM_COARSE_ACM;
-    // rows of e_c used by region rows y0-1 .. y0+SRH (clamped to the coarse grid)
+    // rows of e_c used by region rows y0-1 .. y0+(NW * SRR) (clamped to the coarse grid)
     int Jg0 = 0, nrow = 0, Ic0 = 0, ncol = 0;
-    float *esm = gsm + SGROWS * SRW;
+    float *esm = gsm + sweep_grows(NW) * SRW;
     if (PROLONG) {
         // along a periodic axis the coarse indices are not clamped: they run
         // over the periodic extension and wrap when e_c is read
         Jg0 = acm ? (y0 - 1) >> lm : ((y0 - 1 - hm + m) >> lm) - 1;
-        int Jg1 = acm ? (y0 + SRH) >> lm : ((y0 + SRH - hm + m) >> lm);
+        int Jg1 = acm ? (y0 + (NW * SRR)) >> lm : ((y0 + (NW * SRR) - hm + m) >> lm);
         if (!per_y) { Jg0 = max(0, Jg0); Jg1 = min(a.ncy - 1, Jg1); }
         nrow = Jg1 - Jg0 + 1;
         // (a) columns Ic0..Ic1: the bilinear neighbours of the loaded columns
@@ -285,7 +291,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         int Ic1 = acm ? xe >> lm : ((xe - hm + m) >> lm);
         if (!per_x) { Ic0 = max(0, Ic0); Ic1 = min(a.ncx - 1, Ic1); }
         ncol = Ic1 - Ic0 + 1;
-        for (int t = threadIdx.x; t < nrow * ncol; t += STHREADS) {
+        for (int t = threadIdx.x; t < nrow * ncol; t += (32 * NW)) {
             const int jr = t / ncol, c = t - jr * ncol;
             const int J = per_y ? wrap_mod(Jg0 + jr, a.ncy) : Jg0 + jr;
             const int I = per_x ? wrap_mod(Ic0 + c, a.ncx) : Ic0 + c;
@@ -339,7 +345,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         const int ncx = a.ncx;
         __syncthreads();
         // (b) G[J][x] = e_c interpolated along x for the region's columns
-        for (int t = threadIdx.x; t < nrow * 32; t += STHREADS) {
+        for (int t = threadIdx.x; t < nrow * 32; t += (32 * NW)) {
             const int jr = t >> 5, l = t & 31, xb = x0 + SNC * l;
             float g[SNC] = {0.f, 0.f, 0.f, 0.f};
             if ((unsigned)xb < (unsigned)nx || per_x) {
@@ -402,7 +408,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         }
     }
 
-    if (!EDGE && pf_id >= 0) prefetch_tile(a, pin, pf_id);
+    if (!EDGE && pf_id >= 0) prefetch_tile<NW>(a, pin, pf_id);
 
     // 2. 2K half-sweeps, red ((x+y) even) first
     const int base = (x0 + y0 + ry0) & 1;      // colour parity of (column 0, row 0) of this warp
@@ -410,7 +416,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         const int par = (s & 1) ^ base;        // active colour c = s & 1: q-parity = c ^ base ^ (r & 1)
         if (par == 0) half_sweep<0, EDGE>(P, bs, lane, idq, rq, colin, er);
         else half_sweep<1, EDGE>(P, bs, lane, idq, rq, colin, er);
-        exchange_rows(P, xch, s & 1, w, lane);
+        exchange_rows<NW>(P, xch, s & 1, w, lane);
     }
 
     // 3. write back the valid tile (rows [H, H+TH), columns [Hc, Hc+TW) of the region)
@@ -470,7 +476,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         //    per-thread sums of every coarse cell in fixed (warp, row-part,
         //    lane) order
         __syncthreads();                                  // xch is reused below
-        float *racc = xch;                                // [SNW][3][32]
+        float *racc = xch;                                // [NW][3][32]
         racc[(w * 3 + 0) * 32 + lane] = acc0;
         racc[(w * 3 + 1) * 32 + lane] = acc1;
         racc[(w * 3 + 2) * 32 + lane] = acc2;
@@ -479,12 +485,12 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         const int gy_lo = by * TH, gy_hi = min(gy_lo + TH, ny);
         const int I0 = gx_lo >> lm, I1 = (gx_hi - 1) >> lm, J0 = gy_lo >> lm, J1 = (gy_hi - 1) >> lm;
         const int nbx = I1 - I0 + 1, nb = nbx * (J1 - J0 + 1);
-        for (int cb = threadIdx.x; cb < nb; cb += STHREADS) {
+        for (int cb = threadIdx.x; cb < nb; cb += (32 * NW)) {
             const int I = I0 + cb % nbx, J = J0 + cb / nbx;
             // lanes whose 4 columns lie in coarse column I
             const int l0 = max(0, (I * m - x0 + 3) >> 2), l1 = min(32, ((I + 1) * m - x0 + 3) >> 2);
             float sacc = 0.f;
-            for (int ww = 0; ww < SNW; ++ww) {
+            for (int ww = 0; ww < NW; ++ww) {
                 const int k = J - ((y0 + ww * SRR) >> lm);
                 if (k < 0 || k > 2) continue;
                 const float *row = racc + (ww * 3 + k) * 32;
@@ -495,31 +501,31 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         }
         // 6. norm partials (per-warp float sums combined in double), then the
         //    fused convergence control in the last CTA to finish
-        __shared__ double red[3][SNW];
+        __shared__ double red[3][NW];
         const double v0 = warp_sum(r2s), v1 = warp_sum(ps), v2 = warp_sum(p2);
         if (lane == 0) { red[0][w] = v0; red[1][w] = v1; red[2][w] = v2; }
         __syncthreads();
         const int nblk = a.gx * a.gy;
         if (threadIdx.x < 3) {
             double t = 0.0;
-            for (int k = 0; k < SNW; ++k) t += red[threadIdx.x][k];
+            for (int k = 0; k < NW; ++k) t += red[threadIdx.x][k];
             a.partials[(size_t)threadIdx.x * nblk + by * a.gx + bx] = t;
         }
         if (a.ctl_mode >= 0) ctl_last_block(a.st, a.partials, nblk, 3, a.ctl_mode, a.cond);
     }
 }
 
-template <bool PROLONG, bool RESID, bool EDGE>
-__global__ void __launch_bounds__(STHREADS, 2) k_sweep32(SweepArgs a)
+template <int NW, bool PROLONG, bool RESID, bool EDGE>
+__global__ void __launch_bounds__(32 * NW, 16 / NW) k_sweep32(SweepArgs a)
 {
     if (a.skip && *a.skip) return;
     if (EDGE) {
         const int2 t = a.edge_tiles[blockIdx.x];
-        sweep_tile<PROLONG, RESID, EDGE>(a, t.x, t.y, -1);
+        sweep_tile<NW, PROLONG, RESID, EDGE>(a, t.x, t.y, -1);
     } else {
         const int id = blockIdx.y * gridDim.x + blockIdx.x;
-        sweep_tile<PROLONG, RESID, EDGE>(a, blockIdx.x + a.ix0, blockIdx.y + a.iy0,
-                                         a.pf_ahead > 0 ? id + a.pf_ahead : -1);
+        sweep_tile<NW, PROLONG, RESID, EDGE>(a, blockIdx.x + a.ix0, blockIdx.y + a.iy0,
+                                             a.pf_ahead > 0 ? id + a.pf_ahead : -1);
     }
 }
 
@@ -532,7 +538,7 @@ __global__ void __launch_bounds__(STHREADS, 2) k_sweep32_batch(const SweepArgs *
     const int4 w = work[blockIdx.x];
     const SweepArgs &a = table[w.x];
     if (a.skip && *a.skip) return;
-    sweep_tile<PROLONG, RESID, EDGE>(a, w.y, w.z, -1);
+    sweep_tile<SNW, PROLONG, RESID, EDGE>(a, w.y, w.z, -1);
 }
 
 // Sum of the 4 partial block sums (fixed order) -> R (ncy x ncx).

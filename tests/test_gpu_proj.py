@@ -241,3 +241,30 @@ def test_shear_cavity_with_the_accommodative_strategy():
         fine.append(c)
     print("accommodative, coarse iterations per step:", coarse[:10], "... fine sweeps:", fine[:10], "...")
     assert max(fine) > 0
+
+
+def test_benchmark_i_500_accommodative_steps_match_the_oracle():
+    """The paper's Benchmark I at its own size, 500 x 500 (not a multiple of
+    m: the last coarse cells are narrower), stepped on the GPU with the
+    accommodative strategy (coarse criterion 1e-5, fine 1e-6, warm start).
+    For each of the first steps the oracle solves the same pressure equation
+    (the step's right-hand side, ism_last_b, from the step's initial guess,
+    the previous increment) with its accommodative solver: the coarse
+    iteration and fine sweep counts are the GPU's exactly."""
+    n, nu, v0, dt, m = 500, 0.1, 0.1, 1.0, 16
+    ctx = setup(n, n, m, (0, 0, 0, 0), prec=ism.ISM_FP64, h=1.0, cycle=1, accom_tol_c=1e-5)
+    ism.check(ism.ism_set_flow(ctx, CAVITY, (v0, 0.0, 0.0, -v0), None, 1.0))
+    ism.check(ism.ism_proj_tol(ctx, 1e-6, 1000000, True))
+    u = torch.zeros((n, n + 1), dtype=torch.float32, device="cuda:0")
+    v = torch.zeros((n + 1, n), dtype=torch.float32, device="cuda:0")
+    p = torch.zeros((n, n), dtype=torch.float32, device="cuda:0")
+    solver = O.OracleAccommodative(n, n, m, (0, 0, 0, 0))
+    dp_prev = np.zeros((n, n))
+    for step in range(3):
+        assert ism.proj_step(ctx, u, v, p, dt, nu) == ism.ISM_OK
+        nc_gpu, nf_gpu, _ = ism.ism_last_counts(ctx)
+        b = host(ism.device_view(ism.ism_last_b(ctx), (n, n)))
+        _, nc_ref, nf_ref, mx = solver.solve(b, p0=dp_prev, tol_f=1e-6, tol_c=1e-5)
+        print(f"step {step}: coarse {nc_gpu} vs {nc_ref}, fine {nf_gpu} vs {nf_ref}")
+        assert (nc_gpu, nf_gpu) == (nc_ref, nf_ref)
+        dp_prev = host(ism.device_view(ism.ism_last_dp(ctx), (n, n)))

@@ -127,11 +127,20 @@ def test_mixed_solve_reaches_tolerance_and_matches_oracle(nx, ny, m, bc, coarse_
 
 
 def test_options_that_need_uniform_coarse_cells_are_rejected():
+    """GMG and the deep ACM V-cycle need uniform coarse cells; the
+    accommodative cycle takes a narrower last coarse cell with walls only."""
     ctx = setup(200, 150, 16)
-    for field, value in (("kind", ism.ISM_COARSE_GMG), ("kind", ism.ISM_COARSE_ACMV), ("cycle", 1)):
+    for field, value in (("kind", ism.ISM_COARSE_GMG), ("kind", ism.ISM_COARSE_ACMV)):
         o = ism.ism_get_options(ctx)
         setattr(o, field, value)
         assert ism.ism_set_options(ctx, o) == ism.ISM_ERR_ARG
+    o = ism.ism_get_options(ctx)
+    o.cycle = 1
+    assert ism.ism_set_options(ctx, o) == ism.ISM_OK
+    ctx = setup(200, 128, 16, (0, 0, 2, 2))          # periodic y, x not a multiple of m
+    o = ism.ism_get_options(ctx)
+    o.cycle = 1
+    assert ism.ism_set_options(ctx, o) == ism.ISM_ERR_ARG
 
 
 def test_batched_ensemble_with_ragged_members():
