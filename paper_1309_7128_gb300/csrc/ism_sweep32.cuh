@@ -184,23 +184,30 @@ __device__ __forceinline__ void half_sweep(float (&P)[SRR + 2][SNC], const float
     }
 }
 
-template <int NW>
-__device__ __forceinline__ void exchange_rows(float (&P)[SRR + 2][SNC], float *xch, int buf,
-                                              int w, int lane)
+// After a half-sweep of colour parity PAR only the cells of that colour in a
+// warp's first and last rows changed, and only those are read across the
+// warp boundary before the next exchange (a cell's vertical neighbour has
+// the other colour): each boundary row passes one float2 per lane, the pair
+// (q, q + 2) with q = PAR for the first (even) row and PAR ^ 1 for the last
+// (odd) row.  Two consecutive exchanges bring both colours of the halo rows
+// up to date.
+template <int NW, int PAR>
+__device__ __forceinline__ void exchange_rows(float (&P)[SRR + 2][SNC], float *xch, int buf, int w, int lane)
 {
-    float4 *X = reinterpret_cast<float4 *>(xch);
-    // xch layout: [2 buffers][NW warps][2 rows][32 lanes] float4
+    constexpr int q0 = PAR, q1 = PAR ^ 1;
+    float2 *X = reinterpret_cast<float2 *>(xch);
+    // xch layout: [2 buffers][NW warps][2 rows][32 lanes] float2
     const int base = buf * NW * 2 * 32;
-    X[base + (w * 2 + 0) * 32 + lane] = make_float4(P[1][0], P[1][1], P[1][2], P[1][3]);
-    X[base + (w * 2 + 1) * 32 + lane] = make_float4(P[SRR][0], P[SRR][1], P[SRR][2], P[SRR][3]);
+    X[base + (w * 2 + 0) * 32 + lane] = make_float2(P[1][q0], P[1][q0 + 2]);
+    X[base + (w * 2 + 1) * 32 + lane] = make_float2(P[SRR][q1], P[SRR][q1 + 2]);
     __syncthreads();
     if (w > 0) {
-        const float4 v = X[base + ((w - 1) * 2 + 1) * 32 + lane];
-        P[0][0] = v.x; P[0][1] = v.y; P[0][2] = v.z; P[0][3] = v.w;
+        const float2 v = X[base + ((w - 1) * 2 + 1) * 32 + lane];
+        P[0][q1] = v.x; P[0][q1 + 2] = v.y;
     }
     if (w < NW - 1) {
-        const float4 v = X[base + ((w + 1) * 2 + 0) * 32 + lane];
-        P[SRR + 1][0] = v.x; P[SRR + 1][1] = v.y; P[SRR + 1][2] = v.z; P[SRR + 1][3] = v.w;
+        const float2 v = X[base + ((w + 1) * 2 + 0) * 32 + lane];
+        P[SRR + 1][q0] = v.x; P[SRR + 1][q0 + 2] = v.y;
     }
 }
 
@@ -414,9 +421,13 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
     const int base = (x0 + y0 + ry0) & 1;      // colour parity of (column 0, row 0) of this warp
     for (int s = 0; s < 2 * a.K; ++s) {
         const int par = (s & 1) ^ base;        // active colour c = s & 1: q-parity = c ^ base ^ (r & 1)
-        if (par == 0) half_sweep<0, EDGE>(P, bs, lane, idq, rq, colin, er);
-        else half_sweep<1, EDGE>(P, bs, lane, idq, rq, colin, er);
-        exchange_rows<NW>(P, xch, s & 1, w, lane);
+        if (par == 0) {
+            half_sweep<0, EDGE>(P, bs, lane, idq, rq, colin, er);
+            exchange_rows<NW, 0>(P, xch, s & 1, w, lane);
+        } else {
+            half_sweep<1, EDGE>(P, bs, lane, idq, rq, colin, er);
+            exchange_rows<NW, 1>(P, xch, s & 1, w, lane);
+        }
     }
 
     // 3. write back the valid tile (rows [H, H+TH), columns [Hc, Hc+TW) of the region)
