@@ -82,7 +82,11 @@ typedef enum {
     ISM_VEL_NOSLIP = 0,    /* wall; tangential velocity wall_u[face] */
     ISM_VEL_FREESLIP = 1,  /* wall; zero tangential stress */
     ISM_VEL_INFLOW = 2,    /* west face only: u = inflow profile */
-    ISM_VEL_OUTFLOW = 3    /* east face only: convective outflow, pressure Dirichlet 0 */
+    ISM_VEL_OUTFLOW = 3,   /* east face only: convective outflow, pressure Dirichlet 0 */
+    ISM_VEL_PERIODIC = 4   /* both faces of an axis (the pressure faces periodic too): the
+                              neighbour across the face is at the other end; the last face of
+                              the axis (u[., nx] or v[ny, .]) is the first face again and the
+                              step keeps the two equal */
 } ism_vel_bc;
 
 /* Solver options (ism_get_options fills the defaults). */
@@ -318,9 +322,12 @@ ism_status ism_time_restrict(ism_ctx *ctx, const void *p, const void *b, void *r
 /* Velocity boundary setup for proj_step.
  *   vel_bc  host, 4 ints (ism_vel_bc).  INFLOW only on the west face,
  *           OUTFLOW only on the east face; the pressure boundary given to
- *           ism_setup must be Dirichlet-0 exactly on OUTFLOW faces and have
- *           no periodic face (the projection step has walls only), else
- *           ISM_ERR_ARG.
+ *           ism_setup must be Dirichlet-0 exactly on OUTFLOW faces and
+ *           periodic exactly on PERIODIC faces, else ISM_ERR_ARG.  (The paper's
+ *           benchmarks have walls, inflow and outflow; Sec. 4.1 states that its
+ *           kernels also take periodic faces.)  proj_step_adjoint, and
+ *           proj_rollout_grad when it forms a gradient, reject periodic faces
+ *           (ISM_ERR_ARG).
  *   wall_u  host, 4 doubles: tangential wall speed of NOSLIP faces.
  *   u_in    device, ny floats: west inflow profile (NULL if no inflow);
  *           read at every proj_step, so the caller may update it.

@@ -605,8 +605,11 @@ void or_prolong_add_f32(int nx, int ny, int m, const int *bc, const double *q, f
 /*                                                                             */
 /* Face kinds (vel_bc[face]): 0 no-slip wall moving tangentially with          */
 /* wall_u[face]; 1 free-slip wall; 2 inflow (west face only, profile u_in[j]); */
-/* 3 convective outflow (east face only, speed conv_u).  The pressure is      */
-/* Dirichlet-0 on outflow faces and Neumann elsewhere.                         */
+/* 3 convective outflow (east face only, speed conv_u); 4 periodic (on both    */
+/* faces of an axis: the neighbour across the face is at the other end, and   */
+/* the last face of the axis, kept equal to the first, is the same face).     */
+/* The pressure is Dirichlet-0 on outflow faces, periodic on periodic faces   */
+/* and Neumann elsewhere.                                                      */
 /* ------------------------------------------------------------------------ */
 
 #define UU(i, j) u[(size_t)(j) * (size_t)(nx + 1) + (size_t)(i)]
@@ -614,6 +617,10 @@ void or_prolong_add_f32(int nx, int ny, int m, const int *bc, const double *q, f
 #define US(i, j) us[(size_t)(j) * (size_t)(nx + 1) + (size_t)(i)]
 #define VS(i, j) vs[(size_t)(j) * (size_t)nx + (size_t)(i)]
 #define PP(i, j) p[(size_t)(j) * (size_t)nx + (size_t)(i)]
+
+#define VEL_PER 4
+
+static int wrapn(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
 
 /* ghost value of a tangential velocity component beyond a face */
 static double tangential_ghost(int kind, double wall_u, double inner)
@@ -632,16 +639,19 @@ void or_predictor(int nx, int ny, double h, double dt, double nu,
                   const double *p, double *us, double *vs)
 {
     double ih = 1.0 / h, ih2 = 1.0 / (h * h);
-    /* x-faces */
+    int px = vel_bc[F_W] == VEL_PER, py = vel_bc[F_S] == VEL_PER;
+    /* x-faces; with x periodic, face 0 is computed like an interior face
+       (west neighbours wrap) and face nx is the same face */
     ROWS_PARALLEL
     for (int j = 0; j < ny; ++j) {
         for (int i = 0; i <= nx; ++i) {
             double uc = UU(i, j);
-            if (i == 0) {
+            if (px && i == nx) continue;
+            if (!px && i == 0) {
                 US(i, j) = (vel_bc[F_W] == 2) ? u_in[j] : 0.0;
                 continue;
             }
-            if (i == nx) {
+            if (!px && i == nx) {
                 if (vel_bc[F_E] == 3) {
                     double pin = PP(nx - 1, j);
                     double gp = (-pin - pin) * ih;                /* ghost -p: Dirichlet 0 */
@@ -651,32 +661,40 @@ void or_predictor(int nx, int ny, double h, double dt, double nu,
                 }
                 continue;
             }
-            double uw = UU(i - 1, j), ue = UU(i + 1, j);
-            double usx = (j > 0) ? UU(i, j - 1) : tangential_ghost(vel_bc[F_S], wall_u[F_S], uc);
-            double unx = (j < ny - 1) ? UU(i, j + 1) : tangential_ghost(vel_bc[F_N], wall_u[F_N], uc);
-            double vbar = 0.25 * (VV(i - 1, j) + VV(i, j) + VV(i - 1, j + 1) + VV(i, j + 1));
+            int im = wrapn(i - 1, nx), ip = px ? wrapn(i + 1, nx) : i + 1, jp = py ? wrapn(j + 1, ny) : j + 1;
+            double uw = UU(im, j), ue = UU(ip, j);
+            double usx = (j > 0) ? UU(i, j - 1) : (py ? UU(i, ny - 1) : tangential_ghost(vel_bc[F_S], wall_u[F_S], uc));
+            double unx = (j < ny - 1) ? UU(i, j + 1) : (py ? UU(i, 0) : tangential_ghost(vel_bc[F_N], wall_u[F_N], uc));
+            double vbar = 0.25 * (VV(im, j) + VV(i, j) + VV(im, jp) + VV(i, jp));
             double adv = uc * (ue - uw) * (0.5 * ih) + vbar * (unx - usx) * (0.5 * ih);
             double lap = (ue + uw + unx + usx - 4.0 * uc) * ih2;
-            double gp = (PP(i, j) - PP(i - 1, j)) * ih;
+            double gp = (PP(i, j) - PP(im, j)) * ih;
             US(i, j) = uc + dt * (-adv + nu * lap - gp);
         }
+        if (px) US(nx, j) = US(0, j);
     }
-    /* y-faces: south and north are walls (zero normal velocity) */
+    /* y-faces: south and north are walls (zero normal velocity) unless y is
+       periodic (then face 0 is computed like an interior face and face ny is
+       the same face) */
     ROWS_PARALLEL
     for (int j = 0; j <= ny; ++j) {
         for (int i = 0; i < nx; ++i) {
             double vc = VV(i, j);
-            if (j == 0 || j == ny) { VS(i, j) = 0.0; continue; }
-            double vsy = VV(i, j - 1), vny = VV(i, j + 1);
-            double vw = (i > 0) ? VV(i - 1, j) : tangential_ghost(vel_bc[F_W], wall_u[F_W], vc);
-            double ve = (i < nx - 1) ? VV(i + 1, j) : tangential_ghost(vel_bc[F_E], wall_u[F_E], vc);
-            double ubar = 0.25 * (UU(i, j - 1) + UU(i + 1, j - 1) + UU(i, j) + UU(i + 1, j));
+            if (py && j == ny) { VS(i, j) = 0.0; continue; }      /* set from face 0 below */
+            if (!py && (j == 0 || j == ny)) { VS(i, j) = 0.0; continue; }
+            int jm = wrapn(j - 1, ny), jp = py ? wrapn(j + 1, ny) : j + 1, ip = px ? wrapn(i + 1, nx) : i + 1;
+            double vsy = VV(i, jm), vny = VV(i, jp);
+            double vw = (i > 0) ? VV(i - 1, j) : (px ? VV(nx - 1, j) : tangential_ghost(vel_bc[F_W], wall_u[F_W], vc));
+            double ve = (i < nx - 1) ? VV(i + 1, j) : (px ? VV(0, j) : tangential_ghost(vel_bc[F_E], wall_u[F_E], vc));
+            double ubar = 0.25 * (UU(i, jm) + UU(ip, jm) + UU(i, j) + UU(ip, j));
             double adv = ubar * (ve - vw) * (0.5 * ih) + vc * (vny - vsy) * (0.5 * ih);
             double lap = (ve + vw + vny + vsy - 4.0 * vc) * ih2;
-            double gp = (PP(i, j) - PP(i, j - 1)) * ih;
+            double gp = (PP(i, j) - PP(i, jm)) * ih;
             VS(i, j) = vc + dt * (-adv + nu * lap - gp);
         }
     }
+    if (py)
+        for (int i = 0; i < nx; ++i) VS(i, ny) = VS(i, 0);
 }
 
 /* b = h (u_e - u_w + v_n - v_s) / dt : right-hand side of A_f dp = b (Eq. 4) */
@@ -691,15 +709,21 @@ void or_divergence(int nx, int ny, double h, double dt, const double *u,
 }
 
 /* v^{n+1} = v* - dt grad dp on every face whose normal velocity is not
-   prescribed; p += dp */
+   prescribed (across a periodic face the gradient takes the cell at the
+   other end, and the last face copies the first); p += dp */
 void or_correct(int nx, int ny, double h, double dt, const int *vel_bc,
                 const double *dp, double *u, double *v, double *p)
 {
     double s = dt / h;
+    int px = vel_bc[F_W] == VEL_PER, py = vel_bc[F_S] == VEL_PER;
     ROWS_PARALLEL
     for (int j = 0; j < ny; ++j) {
         for (int i = 1; i < nx; ++i)
             UU(i, j) -= s * (dp[(size_t)j * nx + i] - dp[(size_t)j * nx + i - 1]);
+        if (px) {
+            UU(0, j) -= s * (dp[(size_t)j * nx] - dp[(size_t)j * nx + nx - 1]);
+            UU(nx, j) = UU(0, j);
+        }
         if (vel_bc[F_E] == 3) {
             double pin = dp[(size_t)j * nx + nx - 1];
             UU(nx, j) -= s * (-pin - pin);
@@ -709,5 +733,10 @@ void or_correct(int nx, int ny, double h, double dt, const int *vel_bc,
     for (int j = 1; j < ny; ++j)
         for (int i = 0; i < nx; ++i)
             VV(i, j) -= s * (dp[(size_t)j * nx + i] - dp[(size_t)(j - 1) * nx + i]);
+    if (py)
+        for (int i = 0; i < nx; ++i) {
+            VV(i, 0) -= s * (dp[i] - dp[(size_t)(ny - 1) * nx + i]);
+            VV(i, ny) = VV(i, 0);
+        }
     for (size_t k = 0; k < (size_t)nx * ny; ++k) p[k] += dp[k];
 }

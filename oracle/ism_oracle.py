@@ -36,7 +36,7 @@ _SO = os.path.join(_HERE, "_liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-VEL_NOSLIP, VEL_FREESLIP, VEL_INFLOW, VEL_OUTFLOW = 0, 1, 2, 3
+VEL_NOSLIP, VEL_FREESLIP, VEL_INFLOW, VEL_OUTFLOW, VEL_PERIODIC = 0, 1, 2, 3, 4
 
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 _fp = np.ctypeslib.ndpointer(dtype=np.float32, flags="C_CONTIGUOUS")
@@ -573,8 +573,9 @@ def correct(u, v, p, dp, h, dt, vel_bc):
 
 
 def pressure_bc(vel_bc):
-    """Dirichlet-0 pressure on outflow faces, Neumann elsewhere."""
-    return tuple(1 if k == VEL_OUTFLOW else 0 for k in vel_bc)
+    """Dirichlet-0 pressure on outflow faces, periodic on periodic faces,
+    Neumann elsewhere."""
+    return tuple(1 if k == VEL_OUTFLOW else (BC_PERIODIC if k == VEL_PERIODIC else 0) for k in vel_bc)
 
 
 def proj_step(u, v, p, h, dt, nu, vel_bc, solver: OracleISM, wall_u=(0, 0, 0, 0),

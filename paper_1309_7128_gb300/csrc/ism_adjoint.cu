@@ -301,6 +301,9 @@ extern "C" ism_status proj_step_adjoint(ism_ctx *ctx, const float *u, const floa
         !isfinite(nu))
         return ISM_ERR_ARG;
     if (!ctx->flow_set) return ISM_ERR_ARG;
+    // the transposed step is written for walls, inflow and outflow faces
+    for (int f = 0; f < 4; ++f)
+        if (ctx->vel_bc[f] == ISM_VEL_PERIODIC) return ISM_ERR_ARG;
     TRY(ism_proj_buffers(ctx));
     TRY(ism_enter(ctx));
     const int nx = ctx->nx, ny = ctx->ny, T = 128;

@@ -37,18 +37,24 @@ __device__ __forceinline__ float tangential_ghost(int kind, float wall, float in
 #define VA(i, j) v[(size_t)(j) * nx + (i)]
 #define PA(i, j) p[(size_t)(j) * nx + (i)]
 
-// x-face predictor; grid (ceil((nx+1)/128), ny)
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// x-face predictor; grid (ceil((nx+1)/128), ny).  Along a periodic x axis
+// face 0 is computed like an interior face (its west neighbours wrap) and
+// face nx, the same face, repeats that computation.
 __global__ void k_predict_u(const float *__restrict__ u, const float *__restrict__ v,
                             const float *__restrict__ p, float *__restrict__ us, FlowArgs f)
 {
     const int nx = f.nx, ny = f.ny;
-    const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i > nx) return;
+    const int j = blockIdx.y, io = blockIdx.x * blockDim.x + threadIdx.x;
+    if (io > nx) return;
+    const bool px = f.vbc[0] == ISM_VEL_PERIODIC, py = f.vbc[2] == ISM_VEL_PERIODIC;
+    const int i = (px && io == nx) ? 0 : io;
     const float uc = UA(i, j);
     float out;
-    if (i == 0) {
+    if (i == 0 && !px) {
         out = (f.vbc[0] == ISM_VEL_INFLOW) ? f.u_in[j] : 0.0f;
-    } else if (i == nx) {
+    } else if (i == nx && !px) {
         if (f.vbc[1] == ISM_VEL_OUTFLOW) {
             const float pin = PA(nx - 1, j);
             const float gp = (-pin - pin) * f.ih;                 // ghost -p: Dirichlet 0
@@ -57,38 +63,44 @@ __global__ void k_predict_u(const float *__restrict__ u, const float *__restrict
             out = 0.0f;
         }
     } else {
-        const float uw = UA(i - 1, j), ue = UA(i + 1, j);
-        const float usx = (j > 0) ? UA(i, j - 1) : tangential_ghost(f.vbc[2], f.wall_u[2], uc);
-        const float unx = (j < ny - 1) ? UA(i, j + 1) : tangential_ghost(f.vbc[3], f.wall_u[3], uc);
-        const float vbar = 0.25f * (VA(i - 1, j) + VA(i, j) + VA(i - 1, j + 1) + VA(i, j + 1));
+        const int im = wrapi(i - 1, nx), ip = px ? wrapi(i + 1, nx) : i + 1, jp = py ? wrapi(j + 1, ny) : j + 1;
+        const float uw = UA(im, j), ue = UA(ip, j);
+        const float usx = (j > 0) ? UA(i, j - 1) : (py ? UA(i, ny - 1) : tangential_ghost(f.vbc[2], f.wall_u[2], uc));
+        const float unx = (j < ny - 1) ? UA(i, j + 1) : (py ? UA(i, 0) : tangential_ghost(f.vbc[3], f.wall_u[3], uc));
+        const float vbar = 0.25f * (VA(im, j) + VA(i, j) + VA(im, jp) + VA(i, jp));
         const float adv = uc * (ue - uw) * (0.5f * f.ih) + vbar * (unx - usx) * (0.5f * f.ih);
         const float lap = (ue + uw + unx + usx - 4.0f * uc) * (f.ih * f.ih);
-        const float gp = (PA(i, j) - PA(i - 1, j)) * f.ih;
+        const float gp = (PA(i, j) - PA(im, j)) * f.ih;
         out = uc + f.dt * (-adv + f.nu * lap - gp);
     }
-    us[(size_t)j * (nx + 1) + i] = out;
+    us[(size_t)j * (nx + 1) + io] = out;
 }
 
-// y-face predictor; grid (ceil(nx/128), ny+1).  South and north faces are walls.
+// y-face predictor; grid (ceil(nx/128), ny+1).  South and north faces are
+// walls, or along a periodic y axis face 0 is computed like an interior face
+// and face ny repeats it.
 __global__ void k_predict_v(const float *__restrict__ u, const float *__restrict__ v,
                             const float *__restrict__ p, float *__restrict__ vs, FlowArgs f)
 {
     const int nx = f.nx, ny = f.ny;
-    const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jo = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nx) return;
+    const bool px = f.vbc[0] == ISM_VEL_PERIODIC, py = f.vbc[2] == ISM_VEL_PERIODIC;
+    const int j = (py && jo == ny) ? 0 : jo;
     float out = 0.0f;
-    if (j > 0 && j < ny) {
+    if (py || (j > 0 && j < ny)) {
+        const int jm = wrapi(j - 1, ny), jp = py ? wrapi(j + 1, ny) : j + 1, ip = px ? wrapi(i + 1, nx) : i + 1;
         const float vc = VA(i, j);
-        const float vsy = VA(i, j - 1), vny = VA(i, j + 1);
-        const float vw = (i > 0) ? VA(i - 1, j) : tangential_ghost(f.vbc[0], f.wall_u[0], vc);
-        const float ve = (i < nx - 1) ? VA(i + 1, j) : tangential_ghost(f.vbc[1], f.wall_u[1], vc);
-        const float ubar = 0.25f * (UA(i, j - 1) + UA(i + 1, j - 1) + UA(i, j) + UA(i + 1, j));
+        const float vsy = VA(i, jm), vny = VA(i, jp);
+        const float vw = (i > 0) ? VA(i - 1, j) : (px ? VA(nx - 1, j) : tangential_ghost(f.vbc[0], f.wall_u[0], vc));
+        const float ve = (i < nx - 1) ? VA(i + 1, j) : (px ? VA(0, j) : tangential_ghost(f.vbc[1], f.wall_u[1], vc));
+        const float ubar = 0.25f * (UA(i, jm) + UA(ip, jm) + UA(i, j) + UA(ip, j));
         const float adv = ubar * (ve - vw) * (0.5f * f.ih) + vc * (vny - vsy) * (0.5f * f.ih);
         const float lap = (ve + vw + vny + vsy - 4.0f * vc) * (f.ih * f.ih);
-        const float gp = (PA(i, j) - PA(i, j - 1)) * f.ih;
+        const float gp = (PA(i, j) - PA(i, jm)) * f.ih;
         out = vc + f.dt * (-adv + f.nu * lap - gp);
     }
-    vs[(size_t)j * nx + i] = out;
+    vs[(size_t)jo * nx + i] = out;
 }
 
 // b = h (u_e - u_w + v_n - v_s) / dt in double; partial sums of b and |b|.  h_dt =
@@ -114,13 +126,14 @@ __global__ void k_divergence(const float *__restrict__ u, const float *__restric
 // v = v* - (dt/h) grad dp on the faces whose normal velocity is free
 // (interior faces and the outflow face with its Dirichlet-0 ghost); p += dp.
 __global__ void k_correct_u(float *__restrict__ u, const float *__restrict__ us,
-                            const double *__restrict__ dp, int nx, int ny, double s, int outflow_e)
+                            const double *__restrict__ dp, int nx, int ny, double s, int outflow_e, int px)
 {
     const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i > nx) return;
     const size_t k = (size_t)j * (nx + 1) + i;
     double val = us[k];
     if (i > 0 && i < nx) val -= s * (dp[(size_t)j * nx + i] - dp[(size_t)j * nx + i - 1]);
+    else if (px) val -= s * (dp[(size_t)j * nx] - dp[(size_t)j * nx + nx - 1]);   // faces 0 and nx: the same face
     else if (i == nx && outflow_e) {
         const double pin = dp[(size_t)j * nx + nx - 1];
         val -= s * (-pin - pin);
@@ -130,13 +143,14 @@ __global__ void k_correct_u(float *__restrict__ u, const float *__restrict__ us,
 
 __global__ void k_correct_v(float *__restrict__ v, const float *__restrict__ vs,
                             const double *__restrict__ dp, float *__restrict__ p, int nx, int ny,
-                            double s)
+                            double s, int py)
 {
     const int j = blockIdx.y, i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nx) return;
     const size_t k = (size_t)j * nx + i;
     double val = vs[k];
     if (j > 0 && j < ny) val -= s * (dp[k] - dp[k - nx]);
+    else if (py) val -= s * (dp[i] - dp[(size_t)(ny - 1) * nx + i]);         // faces 0 and ny: the same face
     v[k] = (float)val;
     if (j < ny) p[k] = (float)((double)p[k] + dp[k]);
 }
@@ -158,12 +172,13 @@ extern "C" ism_status ism_set_flow(ism_ctx *ctx, const int vel_bc[4], const doub
 {
     if (!ctx || !vel_bc || !wall_u) return ISM_ERR_ARG;
     for (int f = 0; f < 4; ++f) {
-        if (vel_bc[f] < ISM_VEL_NOSLIP || vel_bc[f] > ISM_VEL_OUTFLOW) return ISM_ERR_ARG;
+        if (vel_bc[f] < ISM_VEL_NOSLIP || vel_bc[f] > ISM_VEL_PERIODIC) return ISM_ERR_ARG;
         if (vel_bc[f] == ISM_VEL_INFLOW && f != 0) return ISM_ERR_ARG;
         if (vel_bc[f] == ISM_VEL_OUTFLOW && f != 1) return ISM_ERR_ARG;
-        // pressure is Dirichlet-0 exactly on outflow faces; walls only
+        // pressure: Dirichlet-0 exactly on outflow faces, periodic exactly on
+        // periodic faces (ism_setup pairs periodic faces), Neumann elsewhere
         if ((vel_bc[f] == ISM_VEL_OUTFLOW) != (ctx->bc[f] == ISM_BC_DIRICHLET0)) return ISM_ERR_ARG;
-        if (ctx->bc[f] == ISM_BC_PERIODIC) return ISM_ERR_ARG;
+        if ((vel_bc[f] == ISM_VEL_PERIODIC) != (ctx->bc[f] == ISM_BC_PERIODIC)) return ISM_ERR_ARG;
         if (!isfinite(wall_u[f])) return ISM_ERR_ARG;
     }
     if (vel_bc[0] == ISM_VEL_INFLOW && !u_in) return ISM_ERR_ARG;
@@ -270,9 +285,11 @@ extern "C" ism_status proj_step(ism_ctx *ctx, float *u, float *v, float *p, doub
     ISM_CUDA_TRY(cudaMemcpyAsync(ctx->dp, ctx->p64[0], (size_t)ctx->n * 8, cudaMemcpyDeviceToDevice, ctx->ws));
     const double sc = dt / ctx->h;
     k_correct_u<<<dim3((nx + 1 + T - 1) / T, ny), T, 0, ctx->ws>>>(u, ctx->us, ctx->dp, nx, ny, sc,
-                                                                   ctx->vel_bc[1] == ISM_VEL_OUTFLOW);
+                                                                   ctx->vel_bc[1] == ISM_VEL_OUTFLOW,
+                                                                   ctx->vel_bc[0] == ISM_VEL_PERIODIC);
     ISM_LAUNCH_CHECK(ctx);
-    k_correct_v<<<dim3((nx + T - 1) / T, ny + 1), T, 0, ctx->ws>>>(v, ctx->vs, ctx->dp, p, nx, ny, sc);
+    k_correct_v<<<dim3((nx + T - 1) / T, ny + 1), T, 0, ctx->ws>>>(v, ctx->vs, ctx->dp, p, nx, ny, sc,
+                                                                   ctx->vel_bc[2] == ISM_VEL_PERIODIC);
     ISM_LAUNCH_CHECK(ctx);
     TRY(ism_leave(ctx));
     return s;

@@ -21,7 +21,7 @@ ISM_OK, ISM_ERR_ARG, ISM_ERR_NOT_CONVERGED, ISM_ERR_NONFINITE, ISM_ERR_CUDA, ISM
 ISM_BC_NEUMANN, ISM_BC_DIRICHLET0, ISM_BC_PERIODIC = 0, 1, 2
 ISM_FP64, ISM_MIXED = 0, 1
 ISM_COARSE_ISM, ISM_COARSE_ACM, ISM_COARSE_GMG, ISM_COARSE_ACMV = 0, 1, 2, 3
-ISM_VEL_NOSLIP, ISM_VEL_FREESLIP, ISM_VEL_INFLOW, ISM_VEL_OUTFLOW = 0, 1, 2, 3
+ISM_VEL_NOSLIP, ISM_VEL_FREESLIP, ISM_VEL_INFLOW, ISM_VEL_OUTFLOW, ISM_VEL_PERIODIC = 0, 1, 2, 3, 4
 
 
 class IsmOptions(C.Structure):

@@ -229,6 +229,75 @@ def test_full_size_fully_periodic_solve_matches_fft(prec):
     assert rel(p, ex) <= 1e-7
 
 
-def test_projection_step_rejects_periodic_pressure_faces():
+def test_projection_step_pairs_periodic_velocity_and_pressure_faces():
+    """Periodic velocity faces need periodic pressure faces and the other way
+    round; the adjoint step rejects periodic faces."""
     ctx = setup(128, 128, 16, (2, 2, 0, 0))
     assert ism.ism_set_flow(ctx, (0, 0, 0, 0)) == ism.ISM_ERR_ARG
+    assert ism.ism_set_flow(ctx, (4, 4, 0, 0)) == ism.ISM_OK
+    ctx2 = setup(128, 128, 16, (0, 0, 0, 0))
+    assert ism.ism_set_flow(ctx2, (4, 4, 0, 0)) == ism.ISM_ERR_ARG
+    import torch
+    u = torch.zeros((128, 129), dtype=torch.float32, device="cuda:0")
+    v = torch.zeros((129, 128), dtype=torch.float32, device="cuda:0")
+    g = [torch.zeros_like(t) for t in (u, v, torch.zeros((128, 128), dtype=torch.float32, device="cuda:0"))]
+    assert ism.proj_step_adjoint(ctx, u, v, 0.01, 0.01, *g) == ism.ISM_ERR_ARG
+
+
+def _tg(n):
+    h = 2 * np.pi / n
+    xf, xc = np.arange(n + 1) * h, (np.arange(n) + 0.5) * h
+    u = np.sin(xf)[None, :] * np.cos(xc)[:, None]
+    v = -np.cos(xc)[None, :] * np.sin(xf)[:, None]
+    p = (np.cos(2 * xc)[None, :] + np.cos(2 * xc)[:, None]) / 4
+    u[:, n] = u[:, 0]
+    v[n, :] = v[0, :]
+    return u, v, p, h
+
+
+@pytest.mark.parametrize("prec", [ism.ISM_FP64, ism.ISM_MIXED])
+@pytest.mark.parametrize("case", ["box", "channel"])
+def test_periodic_projection_steps_match_oracle(prec, case):
+    """Projection steps with periodic faces against the oracle's steps: the
+    Taylor-Green vortex in a fully periodic box, and a channel periodic in x
+    between no-slip walls (north wall moving) with a random start; single
+    precision velocities, one rounding per stored value and step."""
+    import torch
+    from synth.inputs import random_field
+    if case == "box":
+        n = 128
+        u0, v0, p0, h = _tg(n)
+        nx = ny = n
+        vel, wall = (4, 4, 4, 4), (0, 0, 0, 0)
+        nu, dt, m = 0.05, 0.002, 16
+    else:
+        nx, ny, h = 192, 64, 1.0 / 64
+        vel, wall = (4, 4, 0, 0), (0, 0, 0, 0.5)
+        u0 = 0.2 * random_field(nx + 1, ny, 50)
+        v0 = 0.2 * random_field(nx, ny + 1, 51)
+        u0[:, nx] = u0[:, 0]
+        v0[0, :] = 0.0
+        v0[ny, :] = 0.0
+        p0 = np.zeros((ny, nx))
+        nu, dt, m = 0.02, 1e-4, 16
+    f32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)      # noqa: E731
+    u0, v0, p0 = f32(u0), f32(v0), f32(p0)
+    bc = O.pressure_bc(vel)
+    ctx = setup(nx, ny, m, bc, prec=prec, h=h)
+    ism.check(ism.ism_set_flow(ctx, vel, wall, None, 1.0))
+    ism.check(ism.ism_proj_tol(ctx, 1e-10, 100000, False))
+    ud = torch.tensor(u0, dtype=torch.float32, device="cuda:0")
+    vd = torch.tensor(v0, dtype=torch.float32, device="cuda:0")
+    pd = torch.tensor(p0, dtype=torch.float32, device="cuda:0")
+    u, v, p = u0.copy(), v0.copy(), p0.copy()
+    s = O.OracleISM(nx, ny, m, bc)
+    for _ in range(3):
+        assert ism.proj_step(ctx, ud, vd, pd, dt, nu) == ism.ISM_OK
+        O.proj_step(u, v, p, h, dt, nu, vel, s, wall_u=wall, tol=1e-12)
+    ug, vg, pg = host(ud), host(vd), host(pd)
+    assert np.array_equal(ug[:, nx], ug[:, 0])
+    if vel[2] == 4:
+        assert np.array_equal(vg[ny, :], vg[0, :])
+    assert np.abs(ug - u).max() <= 1e-5 * np.abs(u).max()
+    assert np.abs(vg - v).max() <= 1e-5 * np.abs(v).max()
+    assert np.abs(pg - p).max() <= 1e-4 * np.abs(p).max()
