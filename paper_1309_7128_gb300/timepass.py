@@ -9,7 +9,9 @@ the mean device time of one pass measured with CUDA events on the library's
 work stream: `tiled` is the fused K-sweep register-tiled pass (the one
 bench.py reports in its roofline), `stream` the streaming K-sweep pass
 (option stream = 1, K in 1, 2, 4), `restrict` the residual + restriction
-pass.  The first form times the tiled pass on an N x N grid.
+pass, `coarse` the exact coarse solve (ism_coarse_solve, single precision;
+--tc 1 on the tensor cores, 0 on the CUDA cores; host-launched calls).  The
+first form times the tiled pass on an N x N grid.
 """
 import argparse
 import sys
@@ -28,7 +30,8 @@ def main():
         ap = argparse.ArgumentParser()
         ap.add_argument("--nx", type=int, default=2048)
         ap.add_argument("--ny", type=int, default=2048)
-        ap.add_argument("--pass", dest="kind", choices=["tiled", "stream", "restrict"], default="tiled")
+        ap.add_argument("--pass", dest="kind", choices=["tiled", "stream", "restrict", "coarse"], default="tiled")
+        ap.add_argument("--tc", type=int, default=1)
         ap.add_argument("--k", type=int, default=8)
         ap.add_argument("--reps", type=int, default=4)
         ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
@@ -42,6 +45,25 @@ def main():
     g = torch.Generator(device="cuda").manual_seed(0)
     p = torch.zeros((ny, nx), dtype=dt, device="cuda")
     b = torch.randn((ny, nx), dtype=dt, device="cuda", generator=g)
+    if args.kind == "coarse":
+        o = ism.ism_get_options(ctx)
+        o.coarse_tc = args.tc
+        ism.check(ism.ism_set_options(ctx, o), "ism_set_options")
+        ncx, ncy = ism_ceil(nx, 32), ism_ceil(ny, 32)
+        rc = torch.randn((ncy, ncx), dtype=dt, device="cuda", generator=g)
+        rc -= rc.mean()
+        ec = torch.zeros_like(rc)
+        ism.check(ism.ism_coarse_solve(ctx, rc, ec), "ism_coarse_solve")        # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.reps):
+            ism.check(ism.ism_coarse_solve(ctx, rc, ec), "ism_coarse_solve")
+        e1.record()
+        e1.synchronize()
+        us = 1000.0 * e0.elapsed_time(e1) / args.reps
+        print(f"coarse solve {ncx}x{ncy} tc={args.tc} reps={args.reps}: {us:.2f} us per call (host-launched)")
+        return
     if args.kind == "restrict":
         rc = torch.zeros((ism_ceil(ny, 32), ism_ceil(nx, 32)), dtype=dt, device="cuda")
         s, us = ism.ism_time_restrict(ctx, p, b, rc, args.reps)

@@ -2,11 +2,12 @@
 cannot allocate device memory when they need a residual (real-time loops
 that cannot take cudaMalloc's implicit synchronisation, hosts whose device
 memory belongs to their own arena), against the context-based
-ism_residual_restrict, on two calls in a row through the C ABI.  Named to be
-collected last."""
+ism_residual_restrict and the oracle's residual and block sums, on two calls
+in a row through the C ABI.  Named to be collected last."""
 import numpy as np
 import pytest
 
+import oracle as O
 from synth.inputs import random_field
 from tests.gpu_util import dev64, ensure_built, host, ism, setup, torch
 
@@ -36,6 +37,12 @@ def test_noalloc_matches_context_entry_point_twice(nx, ny, m, bc):
         nh = host(norms)
         assert abs(nh[0] - rnorm) <= 1e-12 * rnorm, call
         assert abs(nh[1] - psum) <= 1e-12 * float(p.abs().sum()), call
+        # and against the oracle's residual and block sums of the same fields
+        ph, bh = host(p), host(b)
+        r = O.residual(ph, bh, bc)
+        ref = O.restrict(r, m)
+        np.testing.assert_allclose(host(rc), ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+        assert abs(nh[0] - np.linalg.norm(r)) <= 1e-12 * np.linalg.norm(r), call
 
 
 def test_noalloc_rejects_oversized_coarse_grid():
