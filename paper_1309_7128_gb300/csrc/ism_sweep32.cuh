@@ -116,12 +116,22 @@ __device__ __forceinline__ void prefetch_tile(const SweepArgs &a, const float *p
     }
 }
 
-// b in shared memory: per region row two planes of 32 float2, plane 0 holding
-// (b_q0, b_q2) and plane 1 (b_q1, b_q3) of each lane's columns 4l+q, so the
-// two cells of one colour are one conflict-free 8-byte load.
-__device__ __forceinline__ const float2 *bplane(const float *row, int qp, int lane)
+// b in shared memory, per pair of region rows (2k, 2k + 1) of a warp: two
+// float4 per lane, A = (row 2k plane 0, row 2k + 1 plane 1) and
+// B = (row 2k plane 1, row 2k + 1 plane 0), plane 0 holding (b_q0, b_q2) and
+// plane 1 (b_q1, b_q3) of the lane's columns 4l + q.  A half-sweep of colour
+// parity PAR needs plane PAR of the even row and plane PAR ^ 1 of the odd
+// row: one conflict-free 16-byte load (A or B) serves both rows.
+__device__ __forceinline__ float2 *bslot(float *bs, int r, int qp, int lane)
 {
-    return reinterpret_cast<const float2 *>(row + qp * 64) + lane;
+    const int h = r & 1;
+    return reinterpret_cast<float2 *>(bs + (r >> 1) * 2 * SRW + (qp ^ h) * 128 + lane * 4 + h * 2);
+}
+
+template <int PAR>
+__device__ __forceinline__ float4 bpair(const float *bs, int k, int lane)
+{
+    return *reinterpret_cast<const float4 *>(bs + k * 2 * SRW + PAR * 128 + lane * 4);
 }
 
 // Divisor contribution of the south / north faces for global row y.
@@ -154,10 +164,12 @@ __device__ __forceinline__ void half_sweep(float (&P)[SRR + 2][SNC], const float
                                            const float (&idq)[SNC], const float (&rq)[SNC],
                                            const bool colin, const EdgeRows &er)
 {
+    float4 bb2 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int r = 0; r < SRR; ++r) {
         const int qp = PAR ^ (r & 1);            // which pair of columns has the active colour
-        const float2 bb = *bplane(bs + r * SRW, qp, lane);
+        if ((r & 1) == 0) bb2 = bpair<PAR>(bs, r >> 1, lane);
+        const float2 bb = (r & 1) ? make_float2(bb2.z, bb2.w) : make_float2(bb2.x, bb2.y);
         if (qp == 0) {
             const float left = __shfl_up_sync(FULLMASK, P[r + 1][3], 1);
             float s0 = ((left + P[r + 1][1]) + P[r][0]) + P[r + 2][0];
@@ -320,9 +332,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         for (int r = 0; r < SRR; ++r) {
             float4 v = *reinterpret_cast<const float4 *>(bsrc + (size_t)r * nx);
             v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f;
-            float2 *row = reinterpret_cast<float2 *>(bs + r * SRW);
-            row[lane] = make_float2(v.x, v.z);
-            row[32 + lane] = make_float2(v.y, v.w);
+            *bslot(bs, r, 0, lane) = make_float2(v.x, v.z);
+            *bslot(bs, r, 1, lane) = make_float2(v.y, v.w);
         }
     } else {
 #pragma unroll
@@ -342,9 +353,8 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (rowin && colin) v = *reinterpret_cast<const float4 *>(a.b + (size_t)y * nx + cxl);
             if (!edge) { v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f; }
-            float2 *row = reinterpret_cast<float2 *>(bs + r * SRW);
-            row[lane] = make_float2(v.x, v.z);
-            row[32 + lane] = make_float2(v.y, v.w);
+            *bslot(bs, r, 0, lane) = make_float2(v.x, v.z);
+            *bslot(bs, r, 1, lane) = make_float2(v.y, v.w);
         }
     }
     if (PROLONG) {
@@ -465,7 +475,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
             const float right = __shfl_down_sync(FULLMASK, P[r + 1][0], 1);
             const int rr = ry0 + r, y = y0 + rr;
             const bool ok = colvalid && rr >= H && rr < H + TH && (unsigned)y < (unsigned)ny;
-            const float2 b02 = *bplane(bs + r * SRW, 0, lane), b13 = *bplane(bs + r * SRW, 1, lane);
+            const float2 b02 = *bslot(bs, r, 0, lane), b13 = *bslot(bs, r, 1, lane);
             const float bq[SNC] = {b02.x, b13.x, b02.y, b13.y};
             const float ra = row_adj(y, ny, a.bcmask);
             float rowsum = 0.f;
