@@ -103,8 +103,13 @@ typedef struct {
     int use_graphs;       /* 0: plain launches; 1: CUDA graphs of check_every cycles; 2 (default):
                              the whole solve as one graph with device-side while loops */
     int coarse_tc;        /* mixed: 1 (default) runs the single-precision coarse solve on the tensor
-                             cores (tcgen05, TF32 operands, FP32 accumulation) when ncx, ncy <= 64;
-                             0 on the CUDA cores in FP32.  Ignored by the FP64 path. */
+                             cores (tcgen05, TF32 operands, FP32 accumulation) when ncx, ncy <= 256:
+                             up to 64 x 64 one CTA runs the whole product chain, above that four
+                             launches of a tiled GEMM (128 x 32 blocks) do; 2 takes the tiled
+                             launches on every coarse grid up to 256 x 256; 0 runs it on the CUDA
+                             cores in FP32, as do 1 and 2 above 256.  The batched ensemble uses the
+                             tensor cores only when every problem's coarse grid is <= 64 x 64.
+                             Ignored by the FP64 path. */
     int cycle;            /* 0 (default): the correction-scheme cycle above.  1: the paper's
                              accommodative strategy (Sec. 4.3.1), FP64 contexts with the ISM coarse
                              operator only: Gauss-Seidel on the coarse equations until max |r_c| <=
@@ -316,6 +321,13 @@ ism_status ism_time_pass(ism_ctx *ctx, void *p, const void *b, int sweeps, int r
  * work stream).  Synchronises. */
 ism_status ism_time_restrict(ism_ctx *ctx, const void *p, const void *b, void *rc, int reps,
                              double *us_per_pass);
+
+/* Measurement helper: *us_per_solve the mean device time of one exact coarse
+ * solve ec = A_c^+ rc (device arrays as in ism_coarse_solve, in the context's
+ * precision; the engine the options select: the tensor-core kernels under
+ * coarse_tc, else the CUDA cores), timed like ism_time_pass over `reps`
+ * solves captured in one graph.  Synchronises. */
+ism_status ism_time_coarse(ism_ctx *ctx, const void *rc, void *ec, int reps, double *us_per_solve);
 
 /* ---------------- projection time step (Sec. 2.2-2.3, Eq. 3-4) ---------- */
 

@@ -331,7 +331,7 @@ static void pass_work(const std::vector<ism_ctx *> &cs, int K, bool resid, std::
 static bool batch_uses_tc(const std::vector<ism_ctx *> &cs)
 {
     for (ism_ctx *c : cs)
-        if (!c->opt.coarse_tc || !ism_coarse_tc_supported(c)) return false;
+        if (!c->opt.coarse_tc || !ism_coarse_tc_small(c)) return false;
     return true;
 }
 

@@ -308,9 +308,14 @@ __global__ void __launch_bounds__(CT_THREADS, 1) k_coarse_tc_batch(const CoarseT
 
 }  // namespace
 
-bool ism_coarse_tc_supported(const ism_ctx *ctx)
+bool ism_coarse_tc_small(const ism_ctx *ctx)
 {
     return ctx->tc_block && ctx->ncx <= CT_MAXC && ctx->ncy <= CT_MAXC;
+}
+
+bool ism_coarse_tc_supported(const ism_ctx *ctx)
+{
+    return ism_coarse_tc_small(ctx) || ctx->tct_block != nullptr;
 }
 
 void ism_coarse_tc_prepare()
@@ -319,6 +324,7 @@ void ism_coarse_tc_prepare()
     cudaFuncSetAttribute(k_coarse_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
     cudaFuncSetAttribute(k_coarse_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
     cudaFuncSetAttribute(k_coarse_tc_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+    ism_coarse_tct_prepare();
 }
 
 static CoarseTcArgs coarse_tc_args(ism_ctx *ctx, const float *rc, float *ec, float *rcpart, const int *skip)
@@ -343,7 +349,7 @@ ism_status ism_coarse_tc_batch_table(ism_ctx *const *ctxs, int n, void **table, 
     size_t sm = 0;
     for (int d = 0; d < n; ++d) {
         ism_ctx *c = ctxs[d];
-        if (!ism_coarse_tc_supported(c)) return ISM_ERR_ARG;
+        if (!ism_coarse_tc_small(c)) return ISM_ERR_ARG;
         t[d] = coarse_tc_args(c, c->rcpart, c->ec32, c->rcpart, &c->st->inner_done);
         t[d].consumed = &c->st->skip_init;
         sm = std::max(sm, (size_t)t[d].L.bytes);
@@ -369,7 +375,9 @@ ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, con
                                 const std::vector<double> &Minv)
 {
     const int ncx = ctx->ncx, ncy = ctx->ncy;
-    if (ncx > CT_MAXC || ncy > CT_MAXC) return ISM_OK;   // CUDA-core path only
+    const ism_status st = ism_coarse_tct_upload(ctx, Qx, QxT, Qy, QyT);
+    if (st != ISM_OK) return st;
+    if (ncx > CT_MAXC || ncy > CT_MAXC) return ISM_OK;   // tiled chain (or CUDA cores) only
     const TcLayout L = tc_layout(ncx, ncy);
     std::vector<unsigned char> h(L.cbytes, 0);
     auto put_h = [&](uint32_t base, int row, int k, int K, double v) {
@@ -407,6 +415,9 @@ ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, con
 ism_status ism_launch_coarse_tc(ism_ctx *ctx, const float *rc, bool from_parts, float *ec, float *rcpart,
                                 const int *skip)
 {
+    // coarse_tc 1 takes the single-CTA kernel where it fits, 2 the tiled chain always
+    if (ctx->opt.coarse_tc == 2 || !ism_coarse_tc_small(ctx))
+        return ism_launch_coarse_tct(ctx, rc, from_parts, ec, rcpart, skip);
     const CoarseTcArgs a = coarse_tc_args(ctx, rc, ec, rcpart, skip);
     if (from_parts) k_coarse_tc<true><<<1, CT_THREADS, a.L.bytes, ctx->ws>>>(a);
     else k_coarse_tc<false><<<1, CT_THREADS, a.L.bytes, ctx->ws>>>(a);

@@ -448,7 +448,7 @@ extern "C" void ism_destroy(ism_ctx *ctx)
                     ctx->p64[1], ctx->e32[0], ctx->e32[1], ctx->r32, ctx->rc64, ctx->ec64,
                     ctx->T64, ctx->rc32, ctx->ec32, ctx->T32, ctx->partials, ctx->st,
                     ctx->st_k, ctx->us, ctx->vs, ctx->dp, ctx->rcpart, ctx->roll, ctx->scal,
-                    ctx->tc_block, ctx->G64, ctx->ac_tri};
+                    ctx->tc_block, ctx->tct_block, ctx->G64, ctx->ac_tri};
     for (void *b : bufs)
         if (b) cudaFree(b);
     for (int l = 0; l < 6; ++l) {
@@ -630,7 +630,7 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     if (o->kind == ISM_COARSE_ACMV && ctx->prec != ISM_FP64) return ISM_ERR_ARG;
     if (o->max_outer < 1 || o->inner_max < 1 || o->check_every < 1 || o->check_every > 4096) return ISM_ERR_ARG;
     if (o->use_graphs < 0 || o->use_graphs > 2) return ISM_ERR_ARG;
-    if (o->coarse_tc < 0 || o->coarse_tc > 1) return ISM_ERR_ARG;
+    if (o->coarse_tc < 0 || o->coarse_tc > 2) return ISM_ERR_ARG;
     if (o->cycle < 0 || o->cycle > 1) return ISM_ERR_ARG;
     if (o->cycle == 1 && (ctx->prec != ISM_FP64 || o->kind != ISM_COARSE_ISM)) return ISM_ERR_ARG;
     // the four-colour coarse Gauss-Seidel needs an even coarse count along a periodic axis
@@ -1579,6 +1579,23 @@ extern "C" ism_status ism_time_pass(ism_ctx *ctx, void *p, const void *b, int sw
     };
     TRY(ism_enter(ctx));
     ism_status st = time_graph(ctx, reps, pass, us_per_pass);
+    ism_status s2 = ism_leave(ctx);
+    ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
+    return st != ISM_OK ? st : s2;
+}
+
+extern "C" ism_status ism_time_coarse(ism_ctx *ctx, const void *rc, void *ec, int reps, double *us_per_solve)
+{
+    if (!ctx || !rc || !ec || reps < 1 || !us_per_solve) return ISM_ERR_ARG;
+    auto solve = [&](int) -> ism_status {
+        if (ctx->prec == ISM_FP64)
+            return launch_coarse<double, false>(ctx, (const double *)rc, (double *)ec, ctx->T64, nullptr);
+        if (ctx->opt.coarse_tc && ism_coarse_tc_supported(ctx))
+            return ism_launch_coarse_tc(ctx, (const float *)rc, false, (float *)ec, nullptr, nullptr);
+        return launch_coarse<float, false>(ctx, (const float *)rc, (float *)ec, ctx->T32, nullptr);
+    };
+    TRY(ism_enter(ctx));
+    ism_status st = time_graph(ctx, reps, solve, us_per_solve);
     ism_status s2 = ism_leave(ctx);
     ISM_CUDA_TRY(cudaStreamSynchronize(ctx->ws));
     return st != ISM_OK ? st : s2;

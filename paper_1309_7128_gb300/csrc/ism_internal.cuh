@@ -76,6 +76,8 @@ struct ism_ctx {
     double *lvl_r[6], *lvl_e[6];   // deep V-cycle (ISM_COARSE_ACMV): residual / correction of levels 1..L-1
     void *tc_block;            // tensor-core coarse solve: constant operand tiles (TF32), or NULL
     size_t tc_bytes;
+    void *tct_block;           // tiled tensor-core coarse solve: chunked operand tiles and intermediates, or NULL
+    size_t tct_bytes;
     double *partials;          // ISM_NQ * max_blocks
     int max_blocks;
     IsmState *st;              // device control block
@@ -188,7 +190,11 @@ ism_status ism_proj_buffers(ism_ctx *ctx);
 // Tensor-core coarse solve of the single-precision cycle (ism_coarse_tc.cu):
 // rc -> ec (ncy x ncx); from_parts: rc holds 4 partial block sums per coarse
 // cell; rcpart (or NULL) is cleared afterwards.
+// ism_coarse_tc_supported: either kernel applies (coarse grids up to
+// 256 x 256); ism_coarse_tc_small: the single-CTA kernel (up to 64 x 64),
+// the only one of the batched ensemble.
 bool ism_coarse_tc_supported(const ism_ctx *ctx);
+bool ism_coarse_tc_small(const ism_ctx *ctx);
 void ism_coarse_tc_prepare();   // kernel attributes (called by ism_setup, outside any capture)
 // Lay out the constant operands of E = Qy [(QyT R Qx) . Minv] QxT as TF32
 // tiles on the device.
@@ -197,6 +203,14 @@ ism_status ism_coarse_tc_upload(ism_ctx *ctx, const std::vector<double> &Qx, con
                                 const std::vector<double> &Minv);
 ism_status ism_launch_coarse_tc(ism_ctx *ctx, const float *rc, bool from_parts, float *ec, float *rcpart,
                                 const int *skip);
+// The tiled chain of ism_coarse_tct.cu: four launches of a 128 x 32-block
+// tcgen05 GEMM over chunked K-major TF32 tiles (coarse grids up to 256 x 256).
+bool ism_coarse_tct_fits(int ncx, int ncy);
+void ism_coarse_tct_prepare();
+ism_status ism_coarse_tct_upload(ism_ctx *ctx, const std::vector<double> &Qx, const std::vector<double> &QxT,
+                                 const std::vector<double> &Qy, const std::vector<double> &QyT);
+ism_status ism_launch_coarse_tct(ism_ctx *ctx, const float *rc, bool from_parts, float *ec, float *rcpart,
+                                 const int *skip);
 // Batched ensemble: a device table of per-problem arguments (owned by the
 // caller, cudaFree) and the shared memory the launch needs; one CTA per
 // problem, problems outside an inner solve skip.

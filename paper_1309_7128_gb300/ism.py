@@ -66,6 +66,7 @@ _SIGS = {
     "ism_set_warm_start": (_I, [_VP, _VP]),
     "ism_time_pass": (_I, [_VP, _VP, _VP, _I, _I, C.POINTER(C.c_double)]),
     "ism_time_restrict": (_I, [_VP, _VP, _VP, _VP, _I, C.POINTER(C.c_double)]),
+    "ism_time_coarse": (_I, [_VP, _VP, _VP, _I, C.POINTER(C.c_double)]),
     "ism_autotune": (_I, [_VP, _VP, _D, _I, C.POINTER(IsmOptions)]),
     "ism_residual_restrict_noalloc": (_I, [_I, _I, _I, C.POINTER(C.c_int), _VP, _VP, _VP, _VP, _VP]),
     "ism_solve_batched": (_I, [_I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _D, _I,
@@ -212,6 +213,13 @@ def ism_time_restrict(ctx, p, b, rc, reps):
     """Returns (status, mean device microseconds per residual + restriction pass)."""
     us = C.c_double(0.0)
     s = lib().ism_time_restrict(ctx.handle, _ptr(p), _ptr(b), _ptr(rc), int(reps), C.byref(us))
+    return s, us.value
+
+
+def ism_time_coarse(ctx, rc, ec, reps):
+    """Returns (status, mean device microseconds per exact coarse solve)."""
+    us = C.c_double(0.0)
+    s = lib().ism_time_coarse(ctx.handle, _ptr(rc), _ptr(ec), int(reps), C.byref(us))
     return s, us.value
 
 

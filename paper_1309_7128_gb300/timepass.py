@@ -10,7 +10,8 @@ work stream: `tiled` is the fused K-sweep register-tiled pass (the one
 bench.py reports in its roofline), `stream` the streaming K-sweep pass
 (option stream = 1, K in 1, 2, 4), `restrict` the residual + restriction
 pass, `coarse` the exact coarse solve (ism_coarse_solve, single precision;
---tc 1 on the tensor cores, 0 on the CUDA cores; host-launched calls).  The
+--tc 1 on the tensor cores, 2 the tiled tensor-core chain on every size, 0 on
+the CUDA cores; host-launched calls, then the same number in one graph).  The
 first form times the tiled pass on an N x N grid.
 """
 import argparse
@@ -62,7 +63,10 @@ def main():
         e1.record()
         e1.synchronize()
         us = 1000.0 * e0.elapsed_time(e1) / args.reps
-        print(f"coarse solve {ncx}x{ncy} tc={args.tc} reps={args.reps}: {us:.2f} us per call (host-launched)")
+        s, usg = ism.ism_time_coarse(ctx, rc, ec, args.reps)
+        ism.check(s, "ism_time_coarse")
+        print(f"coarse solve {ncx}x{ncy} tc={args.tc} reps={args.reps}: {us:.2f} us per call (host-launched), "
+              f"{usg:.2f} us per solve (graph of {args.reps})")
         return
     if args.kind == "restrict":
         rc = torch.zeros((ism_ceil(ny, 32), ism_ceil(nx, 32)), dtype=dt, device="cuda")

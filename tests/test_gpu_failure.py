@@ -27,11 +27,12 @@ def _built():
 
 
 @pytest.mark.parametrize("use_graphs", [2, 0])
-def test_coarse_wait_that_runs_out_ends_the_solve_with_a_status(use_graphs):
+@pytest.mark.parametrize("coarse_tc", [1, 2])
+def test_coarse_wait_that_runs_out_ends_the_solve_with_a_status(use_graphs, coarse_tc):
     nx = ny = 256
     m = 32                                   # 8 x 8 coarse grid: the tensor-core coarse solve
-    b = smooth_rhs(nx, ny, 3)
-    ctx = setup(nx, ny, m, prec=ism.ISM_MIXED, coarse_tc=1, fault_test=1, use_graphs=use_graphs)
+    b = smooth_rhs(nx, ny, 3)                # (coarse_tc 1: one CTA; 2: the tiled chain)
+    ctx = setup(nx, ny, m, prec=ism.ISM_MIXED, coarse_tc=coarse_tc, fault_test=1, use_graphs=use_graphs)
     p0 = np.zeros((ny, nx))
     p = dev64(p0)
     t0 = time.perf_counter()
@@ -51,7 +52,7 @@ def test_coarse_wait_that_runs_out_ends_the_solve_with_a_status(use_graphs):
     assert rel(host(p), p_ex) <= 1e-9
 
     # a fresh context and plain torch work on the same device
-    ctx2 = setup(nx, ny, m, prec=ism.ISM_MIXED, coarse_tc=1)
+    ctx2 = setup(nx, ny, m, prec=ism.ISM_MIXED, coarse_tc=coarse_tc)
     p = dev64(p0)
     s, _, rr = ism.ism_solve(ctx2, dev64(b), p, 1e-8, 100000)
     assert s == ism.ISM_OK and rr <= 1e-8

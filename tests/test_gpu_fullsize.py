@@ -72,7 +72,7 @@ def test_fp64_full_size_takes_the_oracle_cycle_count(oracle_cavity2048):
     assert rel(host(p), o["p8"]) <= 1e-12
 
 
-@pytest.mark.parametrize("coarse_tc", [1, 0])
+@pytest.mark.parametrize("coarse_tc", [1, 0, 2])
 def test_mixed_full_size_matches_the_converged_oracle(oracle_cavity2048, coarse_tc):
     o = oracle_cavity2048
     n, m = 2048, 32

@@ -86,9 +86,12 @@ def test_coarse_solve(nx, ny, m, bc, kind):
     if not any(bc):
         rc -= rc.mean()
     ref = O.OracleISM(nx, ny, m, bc, kind=kind).coarse_solve(rc)
-    # FP64; FP32 on the CUDA cores; TF32 on the tensor cores (tcgen05): four
-    # chained products of operands rounded to 2^-11 relative
-    for prec, tcflag, tol in ((ism.ISM_FP64, 0, 1e-11), (ism.ISM_MIXED, 0, 2e-5), (ism.ISM_MIXED, 1, 1e-2)):
+    # FP64; FP32 on the CUDA cores; on the tensor cores (tcgen05): coarse_tc 1
+    # runs the single-CTA kernel on these coarse grids, four chained products
+    # of operands rounded to TF32 (2^-11 relative); coarse_tc 2 the tiled
+    # chain of four launches in split TF32 (about FP32 rounding)
+    for prec, tcflag, tol in ((ism.ISM_FP64, 0, 1e-11), (ism.ISM_MIXED, 0, 2e-5), (ism.ISM_MIXED, 1, 1e-2),
+                              (ism.ISM_MIXED, 2, 5e-5)):
         ctx = setup(nx, ny, m, bc, prec=prec, kind=KINDS[kind], coarse_tc=tcflag)
         mk = dev64 if prec == ism.ISM_FP64 else dev32
         ec = mk(np.zeros_like(rc))
@@ -139,30 +142,72 @@ def test_full_size_single_cycle_fp32():
     np.testing.assert_allclose(host(pd), ref.astype(np.float64), rtol=0, atol=2e-6 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("nx,ny,m", [(2048, 2048, 32), (2048, 2048, 16), (160, 96, 32), (1024, 512, 8),
-                                    (512, 256, 8)])
-def test_coarse_solve_tensor_cores_tf32_error(nx, ny, m):
-    """The tcgen05 TF32 coarse solve against the FP64 oracle: on coarse grids
-    up to 64 x 64 the error is that of TF32 operands (well below 1e-2 of the
-    solution's scale and far above FP32 rounding, so the tensor-core path is
-    the one that ran); larger coarse grids fall back to the FP32 CUDA-core
-    path and give its result exactly."""
-    ncx, ncy = nx // m, ny // m
+def _launches(ctx):
+    return ism.ism_last_counts(ctx)[2]
+
+
+@pytest.mark.parametrize("nx,ny,m,tcflag", [
+    (2048, 2048, 32, 1),    # 64 x 64: one CTA
+    (2048, 2048, 32, 2),    # the same grid through the tiled chain
+    (160, 96, 32, 1),
+    (160, 96, 32, 2),       # 5 x 3: one partly filled block
+    (512, 256, 8, 1),
+    (2048, 2048, 16, 1),    # 128 x 128: tiled chain
+    (1024, 512, 8, 1),      # 128 x 64
+    (8192, 4096, 32, 1),    # 256 x 128: the jet's coarse grid
+    (2304, 2560, 16, 1),    # 144 x 160: two 128-row blocks
+    (3000, 2200, 32, 1),    # 94 x 69, ragged last coarse cells (1-D pencils)
+    (8192, 8192, 32, 2),    # 256 x 256: the largest grid of the tiled chain
+])
+def test_coarse_solve_tensor_cores_against_oracle(nx, ny, m, tcflag):
+    """The tcgen05 coarse solves against the FP64 oracle.  The single-CTA
+    kernel (coarse grids up to 64 x 64 under coarse_tc 1) carries the error of
+    TF32 operands: well below 1e-2 of the solution's scale and far above FP32
+    rounding.  The tiled chain (above 64 x 64, or coarse_tc 2) computes in
+    split TF32 and stays within a few FP32 roundings, like the CUDA-core
+    kernels, but differs from them bit for bit.  The launch counts show which
+    engine ran: 2 launches on the CUDA cores, 1 for the single CTA, 4 for the
+    chain."""
+    ncx, ncy = -(-nx // m), -(-ny // m)
     rc = random_field(ncx, ncy, 9)
     rc -= rc.mean()
     ref = O.OracleISM(nx, ny, m, (0, 0, 0, 0)).coarse_solve(rc)
     ref -= ref.mean()
-    errs = {}
-    for tcflag in (0, 1):
-        ctx = setup(nx, ny, m, prec=ism.ISM_MIXED, coarse_tc=tcflag)
+    errs, outs, nl = {}, {}, {}
+    for flag in (0, tcflag):
+        ctx = setup(nx, ny, m, prec=ism.ISM_MIXED, coarse_tc=flag)
         ec = dev32(np.zeros_like(rc))
+        l0 = _launches(ctx)
         ism.check(ism.ism_coarse_solve(ctx, dev32(rc), ec))
+        nl[flag] = _launches(ctx) - l0
         got = host(ec)
+        outs[flag] = got.copy()
         got -= got.mean()
-        errs[tcflag] = np.abs(got - ref).max() / np.abs(ref).max()
-    print(f"{nx}x{ny}/{m}: max error FP32 {errs[0]:.2e}, TF32 tensor cores {errs[1]:.2e}")
-    assert errs[0] <= 2e-5
-    if ncx <= 64 and ncy <= 64:
-        assert 2e-5 < errs[1] <= 1e-2
+        errs[flag] = np.abs(got - ref).max() / np.abs(ref).max()
+    print(f"{nx}x{ny}/{m} ({ncx}x{ncy}) tc={tcflag}: max error FP32 {errs[0]:.2e}, tensor cores {errs[tcflag]:.2e}")
+    assert errs[0] <= 2e-5 and nl[0] == 2
+    if tcflag == 1 and ncx <= 64 and ncy <= 64:
+        assert nl[tcflag] == 1
+        assert 2e-5 < errs[tcflag] <= 1e-2
     else:
-        assert errs[1] == errs[0]
+        assert nl[tcflag] == 4
+        assert errs[tcflag] <= 5e-5
+        assert not np.array_equal(outs[tcflag], outs[0])
+
+
+def test_coarse_solve_above_the_tensor_core_limit_takes_the_cuda_cores():
+    """512 x 128 coarse cells (beyond 256 along x): coarse_tc 1 and 2 fall back
+    to the FP32 CUDA-core kernels (2 launches) and give their result bit for
+    bit."""
+    nx, ny, m = 16384, 4096, 32
+    rc = random_field(nx // m, ny // m, 9)
+    rc -= rc.mean()
+    outs = []
+    for flag in (0, 1, 2):
+        ctx = setup(nx, ny, m, prec=ism.ISM_MIXED, coarse_tc=flag)
+        ec = dev32(np.zeros_like(rc))
+        l0 = _launches(ctx)
+        ism.check(ism.ism_coarse_solve(ctx, dev32(rc), ec))
+        assert _launches(ctx) - l0 == 2
+        outs.append(host(ec))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])

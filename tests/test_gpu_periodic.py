@@ -144,7 +144,7 @@ def test_fp64_solve_matches_oracle(nx, ny, m, bc, kind):
 
 
 @pytest.mark.parametrize("nx,ny,m,bc", SOLVE_CASES)
-@pytest.mark.parametrize("coarse_tc", [0, 1])
+@pytest.mark.parametrize("coarse_tc", [0, 1, 2])
 def test_mixed_solve_reaches_tolerance_and_matches_oracle(nx, ny, m, bc, coarse_tc):
     """The mixed path runs the fused pass with the correction and the
     residual folded in, so the wrapped loads of the boundary tiles carry the

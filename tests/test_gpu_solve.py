@@ -214,15 +214,17 @@ def test_full_size_mixed_and_fp64_agree():
     assert rel(pm, pd) <= 1e-7
 
 
-@pytest.mark.parametrize("nx,ny,m,bc", [(2048, 2048, 32, (0, 0, 0, 0)), (512, 256, 16, (0, 1, 0, 0)),
-                                         (160, 96, 32, (1, 1, 1, 1))])
-def test_mixed_coarse_on_tensor_cores_matches_cuda_cores(nx, ny, m, bc):
+@pytest.mark.parametrize("nx,ny,m,bc,tcflag", [(2048, 2048, 32, (0, 0, 0, 0), 1), (512, 256, 16, (0, 1, 0, 0), 1),
+                                                (160, 96, 32, (1, 1, 1, 1), 1), (2048, 2048, 16, (0, 0, 0, 0), 1),
+                                                (4096, 2048, 16, (0, 1, 0, 0), 1), (512, 256, 16, (0, 1, 0, 0), 2)])
+def test_mixed_coarse_on_tensor_cores_matches_cuda_cores(nx, ny, m, bc, tcflag):
     """The single-precision cycle with its coarse solve on the tensor cores
-    (TF32) reaches the same FP64 tolerance as with the FP32 CUDA-core coarse
-    solve, to the same solution, within a few cycles."""
+    (TF32; one CTA up to 64 x 64 coarse cells, the tiled chain above that and
+    under coarse_tc 2) reaches the same FP64 tolerance as with the FP32
+    CUDA-core coarse solve, to the same solution, within a few cycles."""
     b = smooth_rhs(nx, ny, 4) + (1e-6 if any(bc) else 0.0)
     s0, p0, c0, r0, _, _ = gpu_solve(b, nx, ny, m, bc, ism.ISM_MIXED, coarse_tc=0)
-    s1, p1, c1, r1, _, _ = gpu_solve(b, nx, ny, m, bc, ism.ISM_MIXED, coarse_tc=1)
+    s1, p1, c1, r1, _, _ = gpu_solve(b, nx, ny, m, bc, ism.ISM_MIXED, coarse_tc=tcflag)
     print(f"{nx}x{ny}/{m}: cycles CUDA cores {c0}, tensor cores {c1}")
     assert s0 == ism.ISM_OK and s1 == ism.ISM_OK and r0 <= 1e-8 and r1 <= 1e-8
     assert rel(p1, p0) <= 1e-8
