@@ -203,9 +203,9 @@ ism_status ism_solve(ism_ctx *ctx, const double *rhs, double *p, double tol,
 
 /* ism_autotune -- choose the sweeps per cycle and per fused pass (and, for
  * ISM_MIXED, whether the middle passes stream, the refinement's inner
- * stopping factor inner_tol and the height of the fused pass's tiled region,
- * tile_rows) for this context by timing complete solves of
- * rhs (device, nx*ny doubles) from a zero initial guess over a fixed
+ * stopping factor inner_tol, the height of the fused pass's tiled region,
+ * tile_rows, and the coarse engine, coarse_tc) for this context by timing
+ * complete solves of rhs (device, nx*ny doubles) from a zero initial guess over a fixed
  * candidate list; keeps the fastest candidate in the context's options and
  * copies it to *best (host, may be NULL).  No counterpart in the paper (its
  * tile size and coarse tolerance were tuned by hand, Sec. 4.1, 4.3.1).
@@ -432,8 +432,11 @@ ism_status proj_rollout_grad(ism_ctx *ctx, const float *u0, const float *v0, con
  * unfinished problems (a finished problem drops out), so one set of
  * launches advances every problem by one cycle; per problem the arithmetic
  * and the decisions are those of ism_solve.  The coarse solves run on the
- * tensor cores (one CTA per problem) when every context has coarse_tc set and
- * a coarse grid of at most 64 x 64, else on the CUDA cores.  The graph is
+ * tensor cores when every context has coarse_tc set and a coarse grid of at
+ * most 256 x 256: one CTA per problem when every coarse grid is at most
+ * 64 x 64 and no context asks for the chain (coarse_tc 2), else the tiled
+ * split-TF32 chain, four launches over all problems' blocks; otherwise on the
+ * CUDA cores.  The graph is
  * built on the first call with a given list of contexts and reused while the
  * list is unchanged and no member's options were set since.
  *   ctxs   host, n distinct contexts.  rhs, p: host arrays of n device pointers
@@ -448,8 +451,8 @@ ism_status ism_solve_batched(int n, ism_ctx *const *ctxs, const double *const *r
 
 /* ism_autotune_batched -- choose the sweeps per cycle of a batched ensemble
  * (nu in {16, 32, 64, 128}, 8 sweeps per fused pass, the same for every
- * problem as ism_solve_batched requires) and whether its coarse solves run on
- * the tensor cores (coarse_tc), by timing ism_solve_batched on the given
+ * problem as ism_solve_batched requires) and the engine of its coarse solves
+ * (coarse_tc 0, 1 or 2), by timing ism_solve_batched on the given
  * right-hand sides; p: host array of n device iterates, overwritten
  * (zero initial guesses).  Sets the winner in every context (on failure the
  * options are restored) and returns it in *nu_out (host, may be NULL).  No

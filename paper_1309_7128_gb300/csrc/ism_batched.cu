@@ -61,8 +61,11 @@ struct Plan {
     // 1 = plain pass geometry, 2 = residual pass geometry
     std::vector<SweepArgs *> tab;   // per pass q (q < npass = nu / K)
     SweepArgs *tab_init = nullptr;  // the init pass (K = 0, residual)
-    void *ctc = nullptr;            // tensor-core coarse solve: per-problem arguments, or NULL
+    int engine = 0;                 // coarse solves: 0 CUDA cores, 1 single-CTA tensor-core kernel, 2 tiled chain
+    void *ctc = nullptr;            // engine 1: per-problem arguments; engine 2: arguments and work list
     size_t ctc_smem = 0;
+    size_t ctct_smem[4] = {};
+    int ctct_nwork = 0;
     int4 *work_in[3] = {}, *work_ed[3] = {};
     int nwork_in[3] = {}, nwork_ed[3] = {};
     int maxncx = 1;
@@ -327,12 +330,19 @@ static void pass_work(const std::vector<ism_ctx *> &cs, int K, bool resid, std::
     }
 }
 
-// Tensor cores for the coarse solves when every problem allows them.
-static bool batch_uses_tc(const std::vector<ism_ctx *> &cs)
+// Engine of the coarse solves: the tensor cores when every problem has
+// coarse_tc set and a coarse grid they take -- the single-CTA kernel when all
+// are <= 64 x 64 and none asks for the chain (coarse_tc 2), else the tiled
+// split-TF32 chain -- and the CUDA cores otherwise.
+static int batch_engine(const std::vector<ism_ctx *> &cs)
 {
-    for (ism_ctx *c : cs)
-        if (!c->opt.coarse_tc || !ism_coarse_tc_small(c)) return false;
-    return true;
+    bool small = true, chain = false;
+    for (ism_ctx *c : cs) {
+        if (!c->opt.coarse_tc || !ism_coarse_tc_supported(c)) return 0;
+        small = small && ism_coarse_tc_small(c);
+        chain = chain || c->opt.coarse_tc == 2;
+    }
+    return small && !chain ? 1 : 2;
 }
 
 static ism_status build_plan(Plan *P, const std::vector<ism_ctx *> &cs)
@@ -372,7 +382,9 @@ static ism_status build_plan(Plan *P, const std::vector<ism_ctx *> &cs)
         cudaGetLastError();
         return ISM_ERR_NOMEM;
     }
-    if (batch_uses_tc(cs)) TRY(ism_coarse_tc_batch_table(cs.data(), P->n, &P->ctc, &P->ctc_smem));
+    P->engine = batch_engine(cs);
+    if (P->engine == 1) TRY(ism_coarse_tc_batch_table(cs.data(), P->n, &P->ctc, &P->ctc_smem));
+    if (P->engine == 2) TRY(ism_coarse_tct_batch_table(cs.data(), P->n, &P->ctc, &P->ctct_nwork, P->ctct_smem));
     const int npass = P->nu / P->K;
     P->tab.assign(npass, nullptr);
     for (int q = 0; q < npass; ++q) {
@@ -463,9 +475,12 @@ static ism_status body(ism_ctx *c0, Plan *P, unsigned long long cond, long long 
     count += 2;
     TRY((launch_pass<false, true>(c0, P->tab_init, P->work_in[0], P->nwork_in[0], P->work_ed[0],
                                   P->nwork_ed[0], count)));
-    if (P->ctc) {
+    if (P->engine == 1) {
         TRY(ism_launch_coarse_tc_batch(c0->ws, P->ctc, P->n, P->ctc_smem));
         count -= 1;
+    } else if (P->engine == 2) {
+        TRY(ism_launch_coarse_tct_batch(c0->ws, P->ctc, P->n, P->ctct_nwork, P->ctct_smem));
+        count += 2;
     } else {
         k_b_coarse1<<<P->ncrows, 256, csm, c0->ws>>>(P->dom, P->crows);
         k_b_coarse2<<<P->ncrows, 256, csm, c0->ws>>>(P->dom, P->crows);
@@ -526,7 +541,7 @@ static ism_status build_graph(ism_ctx *c0, Plan *P)
 static bool plan_matches(const Plan *P, const std::vector<ism_ctx *> &cs)
 {
     if (!P || (int)cs.size() != P->n || cs[0]->opt.nu != P->nu || cs[0]->opt.sweeps_per_pass != P->K) return false;
-    if ((P->ctc != nullptr) != batch_uses_tc(cs)) return false;
+    if (P->engine != batch_engine(cs)) return false;
     for (size_t d = 0; d < cs.size(); ++d)
         if (cs[d]->uid != P->uids[d] || cs[d]->opt_gen != P->gens[d]) return false;
     return true;

@@ -46,6 +46,7 @@
 // an mbarrier phase that nothing completes.
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ism_kernels.cuh"
@@ -119,6 +120,7 @@ struct TctArgs {
     void *out, *outlo;        // OUT 0, 1: chunked tile, hi and lo parts; OUT 2: E (ncy x ncx)
     const float *minv;        // OUT 1: Minv (ncy x ncx)
     float *rcpart;            // OUT 2: partial block sums to clear, or NULL
+    int *consumed;            // OUT 2: set to 1 once the solve has used R (batched: first restriction), or NULL
     const int *skip;
     IsmState *st;
     int K;                    // padded K of this product (a multiple of 32, <= 256)
@@ -153,10 +155,11 @@ __device__ __forceinline__ void tf32_split(float x, uint32_t &hi, uint32_t &lo)
 //            a B operand (NP rows, K = KY); 2: D into E, then clear rcpart.
 // A and B in hi and lo parts, three MMAs per K step; OUT 0 and 1 write the
 // hi and lo parts of the next operand.
+// (cta, ncta): this CTA's index among the problem's CTAs and their number,
+// which share the clearing of the partial block sums.
 template <int BSRC, int OUT>
-__global__ void __launch_bounds__(TT_THREADS) k_coarse_tct(TctArgs a)
+__device__ __forceinline__ void tct_body(const TctArgs &a, int n0, int m0, int cta, int ncta)
 {
-    if (a.skip && *a.skip) return;
     constexpr int NS = TT_STAGES, NPART = 2;
     constexpr uint32_t SB = tct_stage_bytes(BSRC);
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -165,7 +168,6 @@ __global__ void __launch_bounds__(TT_THREADS) k_coarse_tct(TctArgs a)
     __shared__ uint32_t tslot;
     __shared__ int s_issued;
     const int t = threadIdx.x, nch = a.K >> 5, S = nch < NS ? nch : NS;
-    const int n0 = blockIdx.x * TT_N, m0 = blockIdx.y * 128;
     unsigned char *ring = smem, *sBall = smem + S * SB;
 
     // chunk c into stage c % S: the A part(s), and for BSRC 0 the B part(s)
@@ -355,10 +357,32 @@ __global__ void __launch_bounds__(TT_THREADS) k_coarse_tct(TctArgs a)
     if (t < 32) tc::tmem_dealloc(tmem, 32);
     if (OUT == 2 && all && a.rcpart) {
         float4 *rp = reinterpret_cast<float4 *>(a.rcpart);
-        const size_t ncell = (size_t)a.ncx * a.ncy, stride = (size_t)gridDim.x * gridDim.y * TT_THREADS;
-        for (size_t i = ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * TT_THREADS + t; i < ncell; i += stride)
-            rp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const size_t ncell = (size_t)a.ncx * a.ncy, stride = (size_t)ncta * TT_THREADS;
+        for (size_t i = (size_t)cta * TT_THREADS + t; i < ncell; i += stride) rp[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    if (OUT == 2 && all && a.consumed && cta == 0 && t == 0) *a.consumed = 1;
+}
+
+template <int BSRC, int OUT>
+__global__ void __launch_bounds__(TT_THREADS) k_coarse_tct(TctArgs a)
+{
+    if (a.skip && *a.skip) return;
+    tct_body<BSRC, OUT>(a, blockIdx.x * TT_N, blockIdx.y * 128, blockIdx.y * gridDim.x + blockIdx.x,
+                        gridDim.x * gridDim.y);
+}
+
+// Batched ensemble: one launch per product over the blocks of every problem;
+// work[b] = (problem, block column, block row, index of the block within the
+// problem), tab[problem] that problem's arguments; problems outside an
+// inner solve return at once.
+template <int BSRC, int OUT>
+__global__ void __launch_bounds__(TT_THREADS) k_coarse_tct_batch(const TctArgs *__restrict__ tab,
+                                                                 const int4 *__restrict__ work)
+{
+    const int4 w = work[blockIdx.x];
+    const TctArgs a = tab[w.x];
+    if (a.skip && *a.skip) return;
+    tct_body<BSRC, OUT>(a, w.y * TT_N, w.z * 128, w.w, (a.NP / TT_N) * (a.MP / 128));
 }
 
 template <int BSRC, int OUT>
@@ -366,6 +390,37 @@ void set_tct_smem()
 {
     cudaFuncSetAttribute(k_coarse_tct<BSRC, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)tct_smem(BSRC, TT_MAXC));
+    cudaFuncSetAttribute(k_coarse_tct_batch<BSRC, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tct_smem(BSRC, TT_MAXC));
+}
+
+// The arguments of the four products for one context (rc, ec, rcpart as in
+// ism_launch_coarse_tct).
+void tct_chain_args(ism_ctx *ctx, const float *rc, float *ec, float *rcpart, const int *skip, TctArgs p[4])
+{
+    const TctLayout L = tct_layout(ctx->ncx, ctx->ncy);
+    unsigned char *blk = static_cast<unsigned char *>(ctx->tct_block);
+    TctArgs a;
+    memset(&a, 0, sizeof(a));
+    a.skip = skip;
+    a.st = ctx->st;
+    a.ncx = L.ncx; a.ncy = L.ncy; a.MP = L.MP; a.KY = L.KY; a.NP = L.NP;
+    // T1 = Qy^T R (B = R^T built in shared memory)
+    p[0] = a;
+    p[0].A = blk + L.qyt; p[0].Alo = p[0].A + L.lo_ay; p[0].R = rc; p[0].K = L.KY;
+    p[0].out = blk + L.t1; p[0].outlo = blk + L.t1 + L.lo_t1; p[0].fault_test = ctx->opt.fault_test;
+    // T2 .* Minv = (T1 Qx) .* Minv, stored transposed as the next B operand
+    p[1] = a;
+    p[1].A = blk + L.t1; p[1].Alo = p[1].A + L.lo_t1; p[1].B = blk + L.qx2; p[1].Blo = p[1].B + L.lo_bx;
+    p[1].K = L.NP; p[1].out = blk + L.bufB; p[1].outlo = blk + L.bufB + L.lo_b; p[1].minv = ctx->Minv32;
+    // T3 = Qy (T2 .* Minv), over T1
+    p[2] = a;
+    p[2].A = blk + L.qy; p[2].Alo = p[2].A + L.lo_ay; p[2].B = blk + L.bufB; p[2].Blo = p[2].B + L.lo_b;
+    p[2].K = L.KY; p[2].out = blk + L.t1; p[2].outlo = blk + L.t1 + L.lo_t1;
+    // E = T3 Qx^T; the partial block sums are cleared for the next restriction
+    p[3] = a;
+    p[3].A = blk + L.t1; p[3].Alo = p[3].A + L.lo_t1; p[3].B = blk + L.qx4; p[3].Blo = p[3].B + L.lo_bx;
+    p[3].K = L.NP; p[3].out = ec; p[3].rcpart = rcpart;
 }
 
 }  // namespace
@@ -430,39 +485,60 @@ ism_status ism_launch_coarse_tct(ism_ctx *ctx, const float *rc, bool from_parts,
 {
     if (!ctx->tct_block) return ISM_ERR_ARG;
     const TctLayout L = tct_layout(ctx->ncx, ctx->ncy);
-    unsigned char *blk = static_cast<unsigned char *>(ctx->tct_block);
-    TctArgs a;
-    memset(&a, 0, sizeof(a));
-    a.skip = skip;
-    a.st = ctx->st;
-    a.ncx = L.ncx; a.ncy = L.ncy; a.MP = L.MP; a.KY = L.KY; a.NP = L.NP;
+    TctArgs p[4];
+    tct_chain_args(ctx, rc, ec, rcpart, skip, p);
     const dim3 grid(L.NP / TT_N, L.MP / 128);
     cudaStream_t s = ctx->ws;
-
-    // T1 = Qy^T R (B = R^T built in shared memory)
-    TctArgs p = a;
-    p.A = blk + L.qyt; p.Alo = p.A + L.lo_ay; p.R = rc; p.K = L.KY;
-    p.out = blk + L.t1; p.outlo = blk + L.t1 + L.lo_t1; p.fault_test = ctx->opt.fault_test;
-    if (from_parts) k_coarse_tct<1, 0><<<grid, TT_THREADS, tct_smem(1, p.K), s>>>(p);
-    else k_coarse_tct<2, 0><<<grid, TT_THREADS, tct_smem(2, p.K), s>>>(p);
+    if (from_parts) k_coarse_tct<1, 0><<<grid, TT_THREADS, tct_smem(1, p[0].K), s>>>(p[0]);
+    else k_coarse_tct<2, 0><<<grid, TT_THREADS, tct_smem(2, p[0].K), s>>>(p[0]);
     ISM_LAUNCH_CHECK(ctx);
-    // T2 .* Minv = (T1 Qx) .* Minv, stored transposed as the next B operand
-    p = a;
-    p.A = blk + L.t1; p.Alo = p.A + L.lo_t1; p.B = blk + L.qx2; p.Blo = p.B + L.lo_bx; p.K = L.NP;
-    p.out = blk + L.bufB; p.outlo = blk + L.bufB + L.lo_b; p.minv = ctx->Minv32;
-    k_coarse_tct<0, 1><<<grid, TT_THREADS, tct_smem(0, p.K), s>>>(p);
+    k_coarse_tct<0, 1><<<grid, TT_THREADS, tct_smem(0, p[1].K), s>>>(p[1]);
     ISM_LAUNCH_CHECK(ctx);
-    // T3 = Qy (T2 .* Minv), over T1
-    p = a;
-    p.A = blk + L.qy; p.Alo = p.A + L.lo_ay; p.B = blk + L.bufB; p.Blo = p.B + L.lo_b; p.K = L.KY;
-    p.out = blk + L.t1; p.outlo = blk + L.t1 + L.lo_t1;
-    k_coarse_tct<0, 0><<<grid, TT_THREADS, tct_smem(0, p.K), s>>>(p);
+    k_coarse_tct<0, 0><<<grid, TT_THREADS, tct_smem(0, p[2].K), s>>>(p[2]);
     ISM_LAUNCH_CHECK(ctx);
-    // E = T3 Qx^T; the partial block sums are cleared for the next restriction
-    p = a;
-    p.A = blk + L.t1; p.Alo = p.A + L.lo_t1; p.B = blk + L.qx4; p.Blo = p.B + L.lo_bx; p.K = L.NP;
-    p.out = ec; p.rcpart = rcpart;
-    k_coarse_tct<0, 2><<<grid, TT_THREADS, tct_smem(0, p.K), s>>>(p);
+    k_coarse_tct<0, 2><<<grid, TT_THREADS, tct_smem(0, p[3].K), s>>>(p[3]);
     ISM_LAUNCH_CHECK(ctx);
     return ISM_OK;
+}
+
+ism_status ism_coarse_tct_batch_table(ism_ctx *const *ctxs, int n, void **table, int *nwork, size_t smem[4])
+{
+    std::vector<TctArgs> t((size_t)4 * n);
+    std::vector<int4> work;
+    for (int q = 0; q < 4; ++q) smem[q] = 0;
+    for (int d = 0; d < n; ++d) {
+        ism_ctx *c = ctxs[d];
+        if (!c->tct_block) return ISM_ERR_ARG;
+        TctArgs p[4];
+        tct_chain_args(c, c->rcpart, c->ec32, c->rcpart, &c->st->inner_done, p);
+        p[3].consumed = &c->st->skip_init;
+        for (int q = 0; q < 4; ++q) {
+            t[(size_t)q * n + d] = p[q];
+            smem[q] = std::max(smem[q], (size_t)tct_smem(q == 0 ? 1 : 0, p[q].K));
+        }
+        const int gx = p[0].NP / TT_N, gy = p[0].MP / 128;
+        for (int by = 0; by < gy; ++by)
+            for (int bx = 0; bx < gx; ++bx) work.push_back(make_int4(d, bx, by, by * gx + bx));
+    }
+    const size_t tb = t.size() * sizeof(TctArgs), wb = work.size() * sizeof(int4);
+    if (cudaMalloc(table, tb + wb) != cudaSuccess) {
+        cudaGetLastError();
+        *table = nullptr;
+        return ISM_ERR_NOMEM;
+    }
+    ISM_CUDA_TRY(cudaMemcpy(*table, t.data(), tb, cudaMemcpyHostToDevice));
+    ISM_CUDA_TRY(cudaMemcpy(static_cast<unsigned char *>(*table) + tb, work.data(), wb, cudaMemcpyHostToDevice));
+    *nwork = (int)work.size();
+    return ISM_OK;
+}
+
+ism_status ism_launch_coarse_tct_batch(cudaStream_t s, const void *table, int n, int nwork, const size_t smem[4])
+{
+    const TctArgs *t = static_cast<const TctArgs *>(table);
+    const int4 *w = reinterpret_cast<const int4 *>(t + (size_t)4 * n);
+    k_coarse_tct_batch<1, 0><<<nwork, TT_THREADS, smem[0], s>>>(t, w);
+    k_coarse_tct_batch<0, 1><<<nwork, TT_THREADS, smem[1], s>>>(t + n, w);
+    k_coarse_tct_batch<0, 0><<<nwork, TT_THREADS, smem[2], s>>>(t + 2 * (size_t)n, w);
+    k_coarse_tct_batch<0, 2><<<nwork, TT_THREADS, smem[3], s>>>(t + 3 * (size_t)n, w);
+    return cudaGetLastError() == cudaSuccess ? ISM_OK : ISM_ERR_CUDA;
 }

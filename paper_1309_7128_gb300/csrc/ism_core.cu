@@ -1618,12 +1618,20 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
     static const int cand_fp64[][3] = {{8, 4, 0}, {16, 4, 0}, {32, 4, 0}, {48, 4, 0}, {64, 4, 0}, {96, 4, 0},
                                        {128, 4, 0}};
     // then, for the mixed winner, the inner stopping factor of the refinement,
-    // and last the other height of the fused pass's tiled region (tile shape)
+    // the other height of the fused pass's tiled region (tile shape), and
+    // last the other coarse engines (CUDA cores, the single-CTA tensor-core
+    // kernel, the tiled split-TF32 chain: TF32 error costs cycles on some
+    // grids, and the chain's four launches cost time on small ones)
     static const double inner_tols[] = {1e-4, 1e-2};
     const int (*cand)[3] = ctx->prec == ISM_MIXED ? cand_mixed : cand_fp64;
     const int ncand = ctx->prec == ISM_MIXED ? (int)(sizeof(cand_mixed) / sizeof(cand_mixed[0]))
                                              : (int)(sizeof(cand_fp64) / sizeof(cand_fp64[0]));
-    const int ntol = ctx->prec == ISM_MIXED ? 3 : 0;
+    const int ntol = ctx->prec == ISM_MIXED ? 5 : 0;
+    // the engine coarse_tc = k selects (0 CUDA cores, 1 single CTA, 2 chain)
+    auto engine = [&](int k) {
+        if (k == 0 || !ism_coarse_tc_supported(ctx)) return 0;
+        return (k == 1 && ism_coarse_tc_small(ctx)) ? 1 : 2;
+    };
     const ism_options saved = ctx->opt;
     double *p = nullptr;
     if (cudaMalloc((void **)&p, (size_t)ctx->n * 8) != cudaSuccess) { cudaGetLastError(); return ISM_ERR_NOMEM; }
@@ -1633,6 +1641,7 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
     ism_options opt = saved, win = saved;
     float best_ms = 1e30f;
     ism_status st = ISM_OK;
+    int tc0 = 0;                                  // coarse engine of the winner before the last steps
     for (int c = 0; c < ncand + ntol && st == ISM_OK; ++c) {
         if (c < ncand) {
             opt.nu = cand[c][0];
@@ -1641,9 +1650,15 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
         } else if (c < ncand + 2) {
             opt = win;
             opt.inner_tol = inner_tols[c - ncand];
-        } else {
+        } else if (c == ncand + 2) {
             opt = win;
             opt.tile_rows = win.tile_rows == 256 ? 128 : 256;
+        } else {
+            if (c == ncand + 3) tc0 = win.coarse_tc;
+            opt = win;
+            opt.coarse_tc = (tc0 + (c - ncand - 2)) % 3;
+            if (engine(opt.coarse_tc) == engine(tc0)) continue;                  // the same engine
+            if (c == ncand + 4 && engine(opt.coarse_tc) == engine((tc0 + 1) % 3)) continue;
         }
         if ((st = ism_set_options(ctx, &opt)) != ISM_OK) break;
         float ms = 0.f;

@@ -211,6 +211,12 @@ ism_status ism_coarse_tct_upload(ism_ctx *ctx, const std::vector<double> &Qx, co
                                  const std::vector<double> &Qy, const std::vector<double> &QyT);
 ism_status ism_launch_coarse_tct(ism_ctx *ctx, const float *rc, bool from_parts, float *ec, float *rcpart,
                                  const int *skip);
+// Batched ensemble: one device block (owned by the caller, cudaFree) holding
+// the four products' per-problem arguments and the list of every problem's
+// CTAs (*nwork entries), and the shared memory of each product's launch;
+// problems outside an inner solve skip.
+ism_status ism_coarse_tct_batch_table(ism_ctx *const *ctxs, int n, void **table, int *nwork, size_t smem[4]);
+ism_status ism_launch_coarse_tct_batch(cudaStream_t s, const void *table, int n, int nwork, const size_t smem[4]);
 // Batched ensemble: a device table of per-problem arguments (owned by the
 // caller, cudaFree) and the shared memory the launch needs; one CTA per
 // problem, problems outside an inner solve skip.

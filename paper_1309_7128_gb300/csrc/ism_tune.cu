@@ -101,8 +101,10 @@ extern "C" ism_status ism_autotune_batched(int n, ism_ctx *const *ctxs, const do
                                            double *const *p, double tol, int *nu_out)
 {
     if (n < 1 || !ctxs || !rhs || !p || !(tol > 0.0)) return ISM_ERR_ARG;
-    // (nu, coarse solve on the tensor cores or the CUDA cores)
-    static const int cand[][2] = {{16, 1}, {32, 1}, {64, 1}, {128, 1}, {16, 0}, {32, 0}, {64, 0}, {128, 0}};
+    // (nu, coarse engine: 1 the tensor cores, single-CTA kernel where every
+    // coarse grid allows it; 2 the tiled split-TF32 chain; 0 the CUDA cores)
+    static const int cand[][2] = {{16, 1}, {32, 1}, {64, 1}, {128, 1}, {16, 2}, {32, 2},
+                                  {64, 2}, {128, 2}, {16, 0}, {32, 0}, {64, 0}, {128, 0}};
     std::vector<ism_options> saved(n);
     for (int d = 0; d < n; ++d) {
         if (!ctxs[d] || !rhs[d] || !p[d]) return ISM_ERR_ARG;

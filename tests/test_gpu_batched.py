@@ -114,20 +114,43 @@ def test_batched_many_passes_per_cycle(nu):
 
 
 def test_batched_tensor_core_and_cuda_core_coarse_agree():
-    """The ensemble with its coarse solves on the tensor cores (TF32, one CTA
-    per problem) and on the CUDA cores (FP32): both reach 1e-8 per problem
-    and agree to the refinement tolerance."""
+    """The ensemble with its coarse solves on the tensor cores (coarse_tc 1:
+    TF32, one CTA per problem; 2: the tiled split-TF32 chain over all
+    problems' blocks) and on the CUDA cores (FP32): all reach 1e-8 per problem
+    and agree to the refinement tolerance; the chain, accurate to about FP32
+    rounding, takes the CUDA-core cycle counts within one cycle."""
     shapes = batch_shapes(8, seed=5, lo=128, hi=512)
     out = {}
-    for tcflag in (0, 1):
+    for tcflag in (0, 1, 2):
         ctxs, rhs, ps, bs = make_batch(shapes, [16] * 8, [(0, 0, 0, 0)] * 7 + [(0, 1, 0, 0)], seed0=300,
                                        coarse_tc=tcflag)
         s, cyc, rr = ism.ism_solve_batched(ctxs, rhs, ps, 1e-8, 100000)
         assert s == ism.ISM_OK and all(r <= 1e-8 for r in rr)
         out[tcflag] = ([host(p) for p in ps], cyc)
-    for a, b in zip(out[0][0], out[1][0]):
-        assert rel(b, a) <= 1e-8
-    print("cycles CUDA cores", out[0][1], "tensor cores", out[1][1])
+    for tcflag in (1, 2):
+        for a, b in zip(out[0][0], out[tcflag][0]):
+            assert rel(b, a) <= 1e-8
+    assert all(abs(a - b) <= 1 for a, b in zip(out[0][1], out[2][1]))
+    print("cycles CUDA cores", out[0][1], "tensor cores", out[1][1], "chain", out[2][1])
+
+
+def test_batched_chain_on_coarse_grids_above_64():
+    """Problems whose coarse grids exceed 64 x 64 (128 x 64, 96 x 96, 144 x 80
+    at 16h) take the tiled chain under coarse_tc 1, batched like the rest:
+    each result equals its single-problem solve (which takes the same chain)
+    and the smallest the oracle's solution."""
+    shapes = [(2048, 1024), (1536, 1536), (2304, 1280), (256, 256)]
+    ctxs, rhs, ps, bs = make_batch(shapes, [16] * 4, [(0, 0, 0, 0), (0, 1, 0, 0), (0, 0, 0, 0), (0, 0, 0, 0)],
+                                   seed0=700, coarse_tc=1)
+    s, cyc, rr = ism.ism_solve_batched(ctxs, rhs, ps, 1e-8, 100000)
+    assert s == ism.ISM_OK and all(r <= 1e-8 for r in rr)
+    for k, (nx, ny) in enumerate(shapes):
+        q = dev64(np.zeros((ny, nx)))
+        s1, c1, r1 = ism.ism_solve(ctxs[k], rhs[k], q, 1e-8, 100000)
+        assert s1 == ism.ISM_OK and abs(c1 - cyc[k]) <= 2
+        assert rel(host(ps[k]), host(q)) <= 1e-9
+    p_ex, _, _ = O.OracleISM(256, 256, 16, nu=ism.ism_get_options(ctxs[3]).nu).solve(bs[3], tol=1e-11)
+    assert rel(host(ps[3]), p_ex) <= 1e-9
 
 
 def test_autotune_batched_sets_a_common_nu():
@@ -136,6 +159,8 @@ def test_autotune_batched_sets_a_common_nu():
     s, nu = ism.ism_autotune_batched(ctxs, rhs, ps, 1e-8)
     assert s == ism.ISM_OK and nu in (16, 32, 64, 128)
     assert all(ism.ism_get_options(c).nu == nu for c in ctxs)
+    tcs = {ism.ism_get_options(c).coarse_tc for c in ctxs}
+    assert len(tcs) == 1 and tcs <= {0, 1, 2}
     for p in ps:
         p.zero_()
     s, cyc, rr = ism.ism_solve_batched(ctxs, rhs, ps, 1e-8, 100000)

@@ -239,8 +239,9 @@ def test_autotune_picks_a_working_candidate(prec):
     s, o = ism.ism_autotune(ctx, dev64(b), 1e-8, 100000)
     assert s == ism.ISM_OK and o.nu % o.sweeps_per_pass == 0
     cur = ism.ism_get_options(ctx)
-    assert (cur.nu, cur.sweeps_per_pass, cur.stream, cur.inner_tol) == (o.nu, o.sweeps_per_pass, o.stream,
-                                                                        o.inner_tol)
+    assert (cur.nu, cur.sweeps_per_pass, cur.stream, cur.inner_tol, cur.tile_rows, cur.coarse_tc) == \
+        (o.nu, o.sweeps_per_pass, o.stream, o.inner_tol, o.tile_rows, o.coarse_tc)
+    assert o.coarse_tc in (0, 1, 2)
     p_ex, _, _ = O.OracleISM(nx, ny, 32, nu=o.nu).solve(b, tol=1e-11)
     p = dev64(np.zeros((ny, nx)))
     s, c, r = ism.ism_solve(ctx, dev64(b), p, 1e-8, 100000)
