@@ -1617,16 +1617,17 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
                                         {256, 8, 0}, {16, 4, 0},  {32, 4, 1},  {64, 4, 1}, {128, 4, 1}};
     static const int cand_fp64[][3] = {{8, 4, 0}, {16, 4, 0}, {32, 4, 0}, {48, 4, 0}, {64, 4, 0}, {96, 4, 0},
                                        {128, 4, 0}};
-    // then, for the mixed winner, the inner stopping factor of the refinement,
-    // the other height of the fused pass's tiled region (tile shape), and
-    // last the other coarse engines (CUDA cores, the single-CTA tensor-core
-    // kernel, the tiled split-TF32 chain: TF32 error costs cycles on some
-    // grids, and the chain's four launches cost time on small ones)
+    // then, for the three fastest mixed candidates, the inner stopping factor
+    // of the refinement (it interacts with nu: a longer cycle reaches a
+    // tighter inner tolerance in fewer cycles); for the winner the other
+    // height of the fused pass's tiled region (tile shape), and last the other
+    // coarse engines (CUDA cores, the single-CTA tensor-core kernel, the tiled
+    // split-TF32 chain: TF32 error costs cycles on some grids, and the chain's
+    // four launches cost time on small ones)
     static const double inner_tols[] = {1e-4, 1e-2};
     const int (*cand)[3] = ctx->prec == ISM_MIXED ? cand_mixed : cand_fp64;
     const int ncand = ctx->prec == ISM_MIXED ? (int)(sizeof(cand_mixed) / sizeof(cand_mixed[0]))
                                              : (int)(sizeof(cand_fp64) / sizeof(cand_fp64[0]));
-    const int ntol = ctx->prec == ISM_MIXED ? 5 : 0;
     // the engine coarse_tc = k selects (0 CUDA cores, 1 single CTA, 2 chain)
     auto engine = [&](int k) {
         if (k == 0 || !ism_coarse_tc_supported(ctx)) return 0;
@@ -1638,42 +1639,65 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    ism_options opt = saved, win = saved;
-    float best_ms = 1e30f;
     ism_status st = ISM_OK;
-    int tc0 = 0;                                  // coarse engine of the winner before the last steps
-    for (int c = 0; c < ncand + ntol && st == ISM_OK; ++c) {
-        if (c < ncand) {
-            opt.nu = cand[c][0];
-            opt.sweeps_per_pass = cand[c][1];
-            opt.stream = cand[c][2];
-        } else if (c < ncand + 2) {
-            opt = win;
-            opt.inner_tol = inner_tols[c - ncand];
-        } else if (c == ncand + 2) {
-            opt = win;
-            opt.tile_rows = win.tile_rows == 256 ? 128 : 256;
-        } else {
-            if (c == ncand + 3) tc0 = win.coarse_tc;
-            opt = win;
-            opt.coarse_tc = (tc0 + (c - ncand - 2)) % 3;
-            if (engine(opt.coarse_tc) == engine(tc0)) continue;                  // the same engine
-            if (c == ncand + 4 && engine(opt.coarse_tc) == engine((tc0 + 1) % 3)) continue;
-        }
-        if ((st = ism_set_options(ctx, &opt)) != ISM_OK) break;
-        float ms = 0.f;
-        for (int rep = 0; rep < 2 && st == ISM_OK; ++rep) {     // first run builds the graph
+    // time of a complete solve under `o` (the first run builds the graph and
+    // is not counted), 1e30 if it does not converge
+    auto time_opt = [&](const ism_options &o) -> float {
+        if ((st = ism_set_options(ctx, &o)) != ISM_OK) return 1e30f;
+        float ms = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
             cudaMemsetAsync(p, 0, (size_t)ctx->n * 8, ctx->user_stream);
             cudaEventRecord(e0, ctx->user_stream);
             int cyc = 0;
             double rel = 0.0;
-            ism_status s = ism_solve(ctx, rhs, p, tol, max_cycles, &cyc, &rel);
+            const ism_status s = ism_solve(ctx, rhs, p, tol, max_cycles, &cyc, &rel);
             cudaEventRecord(e1, ctx->user_stream);
             cudaEventSynchronize(e1);
-            if (s != ISM_OK) { ms = 1e30f; break; }
+            if (s != ISM_OK) return 1e30f;
             cudaEventElapsedTime(&ms, e0, e1);
         }
-        if (ms < best_ms) { best_ms = ms; win = opt; }
+        return ms;
+    };
+    std::vector<std::pair<float, ism_options>> first;
+    for (int c = 0; c < ncand && st == ISM_OK; ++c) {
+        ism_options o = saved;
+        o.nu = cand[c][0];
+        o.sweeps_per_pass = cand[c][1];
+        o.stream = cand[c][2];
+        first.push_back({time_opt(o), o});
+    }
+    std::stable_sort(first.begin(), first.end(),
+                     [](const std::pair<float, ism_options> &x, const std::pair<float, ism_options> &y) {
+                         return x.first < y.first;
+                     });
+    float best_ms = first.empty() ? 1e30f : first[0].first;
+    ism_options win = first.empty() ? saved : first[0].second;
+    if (ctx->prec == ISM_MIXED && st == ISM_OK) {
+        auto consider = [&](const ism_options &o) {
+            const float ms = time_opt(o);
+            if (ms < best_ms) { best_ms = ms; win = o; }
+        };
+        const int top = std::min<int>(3, (int)first.size());
+        for (int k = 0; k < top && st == ISM_OK; ++k)
+            for (double it : inner_tols) {
+                if (first[k].first >= 1e29f || st != ISM_OK) continue;
+                ism_options o = first[k].second;
+                o.inner_tol = it;
+                consider(o);
+            }
+        if (st == ISM_OK) {
+            ism_options o = win;
+            o.tile_rows = win.tile_rows == 256 ? 128 : 256;
+            consider(o);
+        }
+        const ism_options w0 = win;
+        for (int d = 1; d <= 2 && st == ISM_OK; ++d) {
+            ism_options o = w0;
+            o.coarse_tc = (w0.coarse_tc + d) % 3;
+            if (engine(o.coarse_tc) == engine(w0.coarse_tc)) continue;                 // the same engine
+            if (d == 2 && engine(o.coarse_tc) == engine((w0.coarse_tc + 1) % 3)) continue;
+            consider(o);
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
