@@ -238,7 +238,7 @@ def set_graphs(ism, ctx, use_graphs):
     ism.check(ism.ism_set_options(ctx, o), "ism_set_options")
 
 
-def tune(ism, ctx, rhs, args, prec):
+def tune(ism, ctx, rhs, args, prec, p0=None):
     if args.no_autotune:
         o = ism.ism_get_options(ctx)
         if prec == ism.ISM_MIXED:
@@ -247,7 +247,7 @@ def tune(ism, ctx, rhs, args, prec):
             o.nu = args.nu_fp64
         ism.check(ism.ism_set_options(ctx, o), "ism_set_options")
         return options_dict(ism, ctx, False)
-    s, _ = ism.ism_autotune(ctx, rhs, TOL, 1_000_000)
+    s, _ = ism.ism_autotune_from(ctx, rhs, p0, TOL, 1_000_000)
     ism.check(s, "ism_autotune")
     return options_dict(ism, ctx, True)
 
@@ -317,13 +317,17 @@ def run_jet(args, ism, dev, world, rank):
     p = torch.zeros((JET_NY, JET_NX), dtype=torch.float32, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    # warm-up: W - 1 steps, tune on the last right-hand side, one more step
-    # (builds the solve graphs of the tuned options)
-    for _ in range(args.warmup - 1):
+    # warm-up: W - 1 steps, tune on the last one's solve (its right-hand side,
+    # started from the increment it was warm-started with, as the timed steps
+    # are), one more step (builds the solve graphs of the tuned options)
+    for _ in range(args.warmup - 2):
         ism.check(ism.proj_step(ctx, u, v, p, dt, JET_NU), "proj_step (warm-up)")
     torch.cuda.synchronize()
+    dp_tune = ism.device_view(ism.ism_last_dp(ctx), (JET_NY, JET_NX)).clone()
+    ism.check(ism.proj_step(ctx, u, v, p, dt, JET_NU), "proj_step (warm-up)")
+    torch.cuda.synchronize()
     rhs_tune = ism.device_view(ism.ism_last_b(ctx), (JET_NY, JET_NX)).clone()
-    opt_m = tune(ism, ctx, rhs_tune, args, ism.ISM_MIXED)
+    opt_m = tune(ism, ctx, rhs_tune, args, ism.ISM_MIXED, dp_tune)
     set_graphs(ism, ctx, args.use_graphs)
     ism.check(ism.proj_step(ctx, u, v, p, dt, JET_NU), "proj_step (warm-up)")
     torch.cuda.synchronize()

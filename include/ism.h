@@ -214,6 +214,14 @@ ism_status ism_solve(ism_ctx *ctx, const double *rhs, double *p, double tol,
 ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, int max_cycles,
                         ism_options *best);
 
+/* ism_autotune_from -- ism_autotune with every timed solve started from the
+ * initial guess p0 (device, nx*ny doubles, not modified; NULL: zero, which is
+ * ism_autotune).  A time stepper whose solves start from the previous step's
+ * increment tunes on such a solve: a warm start needs fewer cycles, and the
+ * fastest options differ from those of a cold one. */
+ism_status ism_autotune_from(ism_ctx *ctx, const double *rhs, const double *p0, double tol,
+                             int max_cycles, ism_options *best);
+
 /* Coarsening factor m of a context (0 for NULL). */
 int ism_coarsening(const ism_ctx *ctx);
 

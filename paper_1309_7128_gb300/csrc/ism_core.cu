@@ -1606,6 +1606,12 @@ extern "C" ism_status ism_time_coarse(ism_ctx *ctx, const void *rc, void *ec, in
 extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, int max_cycles,
                                    ism_options *best)
 {
+    return ism_autotune_from(ctx, rhs, nullptr, tol, max_cycles, best);
+}
+
+extern "C" ism_status ism_autotune_from(ism_ctx *ctx, const double *rhs, const double *p0, double tol,
+                                        int max_cycles, ism_options *best)
+{
     if (!ctx || !rhs || !(tol > 0.0) || max_cycles < 1) return ISM_ERR_ARG;
     // a cycle costs a fixed part (coarse solve, fused prolongation and residual,
     // control) plus one part per pass, and the total sweeps of a solve are
@@ -1646,7 +1652,8 @@ extern "C" ism_status ism_autotune(ism_ctx *ctx, const double *rhs, double tol, 
         if ((st = ism_set_options(ctx, &o)) != ISM_OK) return 1e30f;
         float ms = 1e30f;
         for (int rep = 0; rep < 2; ++rep) {
-            cudaMemsetAsync(p, 0, (size_t)ctx->n * 8, ctx->user_stream);
+            if (p0) cudaMemcpyAsync(p, p0, (size_t)ctx->n * 8, cudaMemcpyDeviceToDevice, ctx->user_stream);
+            else cudaMemsetAsync(p, 0, (size_t)ctx->n * 8, ctx->user_stream);
             cudaEventRecord(e0, ctx->user_stream);
             int cyc = 0;
             double rel = 0.0;

@@ -11,7 +11,12 @@
 //     needs either the left or the right one, never both),
 // i.e. five instructions per cell update.  After each half-sweep the first
 // and last rows of every warp are exchanged through shared memory
-// (double-buffered, one barrier per half-sweep).
+// (double-buffered, one barrier per half-sweep).  The right-hand side b of
+// the region is staged once per pass in tensor memory (TMEM, tcgen05.st),
+// ordered so that one tcgen05.ld of four columns gives the b values of two
+// rows of a half-sweep: the shared-memory pipe, which the shuffles and the
+// row exchange also use, is left to them (TMEM has its own data path; with b
+// in shared memory the pass was 6-11% slower, results bit-identical).
 //
 // K sweeps run on the region before it is written back.  Values at the
 // region edge are stale (shuffles wrap to the lane itself, the outermost
@@ -50,6 +55,7 @@
 #pragma once
 
 #include "ism_kernels.cuh"
+#include "ism_tc.cuh"
 
 constexpr int SNC = 4;                  // columns per thread
 constexpr int SRR = 16;                 // rows per warp
@@ -116,22 +122,37 @@ __device__ __forceinline__ void prefetch_tile(const SweepArgs &a, const float *p
     }
 }
 
-// b in shared memory, per pair of region rows (2k, 2k + 1) of a warp: two
-// float4 per lane, A = (row 2k plane 0, row 2k + 1 plane 1) and
-// B = (row 2k plane 1, row 2k + 1 plane 0), plane 0 holding (b_q0, b_q2) and
-// plane 1 (b_q1, b_q3) of the lane's columns 4l + q.  A half-sweep of colour
-// parity PAR needs plane PAR of the even row and plane PAR ^ 1 of the odd
-// row: one conflict-free 16-byte load (A or B) serves both rows.
-__device__ __forceinline__ float2 *bslot(float *bs, int r, int qp, int lane)
+// b in tensor memory (TMEM): warp w owns 64 columns of TMEM lane quarter
+// w % 4 (lane l of the warp = TMEM lane 32 (w % 4) + l), from column
+// 64 (w / 4).  Column PAR 32 + 2 r + j holds, for region row r of the warp,
+// b at column 4l + qp + 2j with qp = PAR ^ (r & 1): the two cells row r
+// updates in a half-sweep of colour parity PAR.  A half-sweep reads its
+// rows' values in pairs of rows (four consecutive columns).
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, float v0, float v1, float v2, float v3, float v4, float v5,
+                                         float v6, float v7)
 {
-    const int h = r & 1;
-    return reinterpret_cast<float2 *>(bs + (r >> 1) * 2 * SRW + (qp ^ h) * 128 + lane * 4 + h * 2);
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                 :: "r"(taddr), "r"(__float_as_uint(v0)), "r"(__float_as_uint(v1)), "r"(__float_as_uint(v2)),
+                    "r"(__float_as_uint(v3)), "r"(__float_as_uint(v4)), "r"(__float_as_uint(v5)),
+                    "r"(__float_as_uint(v6)), "r"(__float_as_uint(v7))
+                 : "memory");
 }
 
-template <int PAR>
-__device__ __forceinline__ float4 bpair(const float *bs, int k, int lane)
+__device__ __forceinline__ float4 tmem_ld4(uint32_t taddr)
 {
-    return *reinterpret_cast<const float4 *>(bs + k * 2 * SRW + PAR * 128 + lane * 4);
+    uint32_t r0, r1, r2, r3;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3) :: "memory");
+    return make_float4(__uint_as_float(r0), __uint_as_float(r1), __uint_as_float(r2), __uint_as_float(r3));
+}
+
+// Rows r0..r0+3 of b (one float4 per row: the thread's 4 columns) into TMEM.
+__device__ __forceinline__ void b_store4(uint32_t tb, int r0, const float4 (&v)[4])
+{
+    // PAR 0: even row (b0, b2), odd row (b1, b3); PAR 1: even (b1, b3), odd (b0, b2)
+    tmem_st8(tb + 2 * r0, v[0].x, v[0].z, v[1].y, v[1].w, v[2].x, v[2].z, v[3].y, v[3].w);
+    tmem_st8(tb + 32 + 2 * r0, v[0].y, v[0].w, v[1].x, v[1].z, v[2].y, v[2].w, v[3].x, v[3].z);
 }
 
 // Divisor contribution of the south / north faces for global row y.
@@ -160,7 +181,7 @@ __device__ __forceinline__ float edge_inv(const EdgeRows &er, const float (&rq)[
 // Half-sweep of colour parity PAR over the warp's rows; EDGE selects the
 // boundary-aware update (out-of-domain cells are never updated).
 template <int PAR, bool EDGE>
-__device__ __forceinline__ void half_sweep(float (&P)[SRR + 2][SNC], const float *bs, const int lane,
+__device__ __forceinline__ void half_sweep(float (&P)[SRR + 2][SNC], const uint32_t tb, const int lane,
                                            const float (&idq)[SNC], const float (&rq)[SNC],
                                            const bool colin, const EdgeRows &er)
 {
@@ -168,7 +189,7 @@ __device__ __forceinline__ void half_sweep(float (&P)[SRR + 2][SNC], const float
 #pragma unroll
     for (int r = 0; r < SRR; ++r) {
         const int qp = PAR ^ (r & 1);            // which pair of columns has the active colour
-        if ((r & 1) == 0) bb2 = bpair<PAR>(bs, r >> 1, lane);
+        if ((r & 1) == 0) bb2 = tmem_ld4(tb + PAR * 32 + 2 * r);
         const float2 bb = (r & 1) ? make_float2(bb2.z, bb2.w) : make_float2(bb2.x, bb2.y);
         if (qp == 0) {
             const float left = __shfl_up_sync(FULLMASK, P[r + 1][3], 1);
@@ -230,7 +251,7 @@ __host__ __device__ constexpr int sweep_grows(int nw) { return nw * SRR / 8 + 3;
 constexpr int SGCOLS = SRW / 8 + 3;
 inline size_t sweep_smem_bytes(int nw = SNW)
 {
-    return (size_t)nw * SRR * SRW * 4 + (size_t)2 * nw * 2 * SRW * 4 + (size_t)sweep_grows(nw) * SRW * 4 +
+    return (size_t)2 * nw * 2 * SRW * 4 + (size_t)sweep_grows(nw) * SRW * 4 +
            (size_t)sweep_grows(nw) * SGCOLS * 4;
 }
 
@@ -241,8 +262,7 @@ template <int NW, bool PROLONG, bool RESID, bool EDGE>
 __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, const int by, const int pf_id)
 {
     extern __shared__ __align__(16) float sm[];
-    float *bsm = sm;                       // (NW * SRR) x SRW (b per thread, colour-pair order)
-    float *xch = sm + (NW * SRR) * SRW;           // row exchange buffers
+    float *xch = sm;                       // row exchange buffers
     float *gsm = xch + 2 * NW * 2 * SRW;  // coarse correction rows G[Jg0 ..] of this region
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nx = a.nx, ny = a.ny, H = a.H, Hc = a.Hc, TW = a.TW, TH = a.TH;
@@ -253,7 +273,15 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
     const int in = ((a.curp ? *a.curp : 0) + a.q) & 1;
     const float *__restrict__ pin = in ? a.e1 : a.e0;
     float *__restrict__ pout = in ? a.e0 : a.e1;
-    float *bs = bsm + ry0 * SRW;           // this warp's b rows (two colour planes per row)
+    // TMEM for b: NW x 16 columns (64 per warp; warps w and w + 4 share a
+    // lane quarter).  At most 256 columns per SM (two CTAs of 8 warps or one
+    // of 16, as registers allow), of 512, so the allocation never waits long.
+    __shared__ uint32_t tslot;
+    if (w == 0) tc::tmem_alloc(&tslot, (uint32_t)(NW * 16));
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = tslot + ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(64 * (w >> 2));
     // nx % 4 == 0 and cx % 4 == 0: a thread's 4 columns are all in or all out
     const bool per_x = EDGE && (a.bcmask & ISM_PER_X), per_y = EDGE && (a.bcmask & ISM_PER_Y);
     const bool coldom = (unsigned)cx < (unsigned)nx;
@@ -329,11 +357,14 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         }
         const float *bsrc = a.b + (size_t)(y0 + ry0) * nx + cx;
 #pragma unroll
-        for (int r = 0; r < SRR; ++r) {
-            float4 v = *reinterpret_cast<const float4 *>(bsrc + (size_t)r * nx);
-            v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f;
-            *bslot(bs, r, 0, lane) = make_float2(v.x, v.z);
-            *bslot(bs, r, 1, lane) = make_float2(v.y, v.w);
+        for (int r0 = 0; r0 < SRR; r0 += 4) {
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                v[k] = *reinterpret_cast<const float4 *>(bsrc + (size_t)(r0 + k) * nx);
+                v[k].x *= 0.25f; v[k].y *= 0.25f; v[k].z *= 0.25f; v[k].w *= 0.25f;
+            }
+            b_store4(tb, r0, v);
         }
     } else {
 #pragma unroll
@@ -346,15 +377,17 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
             P[r][0] = v.x; P[r][1] = v.y; P[r][2] = v.z; P[r][3] = v.w;
         }
 #pragma unroll
-        for (int r = 0; r < SRR; ++r) {
-            int y = y0 + ry0 + r;
-            bool rowin = (unsigned)y < (unsigned)ny;
-            if (per_y && !rowin) { y = wrap_mod(y, ny); rowin = true; }
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (rowin && colin) v = *reinterpret_cast<const float4 *>(a.b + (size_t)y * nx + cxl);
-            if (!edge) { v.x *= 0.25f; v.y *= 0.25f; v.z *= 0.25f; v.w *= 0.25f; }
-            *bslot(bs, r, 0, lane) = make_float2(v.x, v.z);
-            *bslot(bs, r, 1, lane) = make_float2(v.y, v.w);
+        for (int r0 = 0; r0 < SRR; r0 += 4) {
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                int y = y0 + ry0 + r0 + k;
+                bool rowin = (unsigned)y < (unsigned)ny;
+                if (per_y && !rowin) { y = wrap_mod(y, ny); rowin = true; }
+                v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (rowin && colin) v[k] = *reinterpret_cast<const float4 *>(a.b + (size_t)y * nx + cxl);
+            }
+            b_store4(tb, r0, v);
         }
     }
     if (PROLONG) {
@@ -426,16 +459,17 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
     }
 
     if (!EDGE && pf_id >= 0) prefetch_tile<NW>(a, pin, pf_id);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 
     // 2. 2K half-sweeps, red ((x+y) even) first
     const int base = (x0 + y0 + ry0) & 1;      // colour parity of (column 0, row 0) of this warp
     for (int s = 0; s < 2 * a.K; ++s) {
         const int par = (s & 1) ^ base;        // active colour c = s & 1: q-parity = c ^ base ^ (r & 1)
         if (par == 0) {
-            half_sweep<0, EDGE>(P, bs, lane, idq, rq, colin, er);
+            half_sweep<0, EDGE>(P, tb, lane, idq, rq, colin, er);
             exchange_rows<NW, 0>(P, xch, s & 1, w, lane);
         } else {
-            half_sweep<1, EDGE>(P, bs, lane, idq, rq, colin, er);
+            half_sweep<1, EDGE>(P, tb, lane, idq, rq, colin, er);
             exchange_rows<NW, 1>(P, xch, s & 1, w, lane);
         }
     }
@@ -469,14 +503,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         const int r1 = ((Jw + 1) << lm) - yw, r2 = ((Jw + 2) << lm) - yw;
         float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
         float r2s = 0.f, ps = 0.f, p2 = 0.f;
+        float4 bA = make_float4(0.f, 0.f, 0.f, 0.f), bB = bA;
 #pragma unroll
         for (int r = 0; r < SRR; ++r) {
+            if ((r & 1) == 0) {
+                bA = tmem_ld4(tb + 2 * r);          // row r: (b0, b2), row r + 1: (b1, b3)
+                bB = tmem_ld4(tb + 32 + 2 * r);     // row r: (b1, b3), row r + 1: (b0, b2)
+            }
             const float left = __shfl_up_sync(FULLMASK, P[r + 1][3], 1);
             const float right = __shfl_down_sync(FULLMASK, P[r + 1][0], 1);
             const int rr = ry0 + r, y = y0 + rr;
             const bool ok = colvalid && rr >= H && rr < H + TH && (unsigned)y < (unsigned)ny;
-            const float2 b02 = *bslot(bs, r, 0, lane), b13 = *bslot(bs, r, 1, lane);
-            const float bq[SNC] = {b02.x, b13.x, b02.y, b13.y};
+            const float bq[SNC] = {(r & 1) ? bB.z : bA.x, (r & 1) ? bA.z : bB.x, (r & 1) ? bB.w : bA.y,
+                                   (r & 1) ? bA.w : bB.y};
             const float ra = row_adj(y, ny, a.bcmask);
             float rowsum = 0.f;
 #pragma unroll
@@ -534,6 +573,9 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
         }
         if (a.ctl_mode >= 0) ctl_last_block(a.st, a.partials, nblk, 3, a.ctl_mode, a.cond);
     }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (w == 0) tc::tmem_dealloc(tslot, (uint32_t)(NW * 16));
 }
 
 template <int NW, bool PROLONG, bool RESID, bool EDGE>

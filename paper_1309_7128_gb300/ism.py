@@ -68,6 +68,7 @@ _SIGS = {
     "ism_time_restrict": (_I, [_VP, _VP, _VP, _VP, _I, C.POINTER(C.c_double)]),
     "ism_time_coarse": (_I, [_VP, _VP, _VP, _I, C.POINTER(C.c_double)]),
     "ism_autotune": (_I, [_VP, _VP, _D, _I, C.POINTER(IsmOptions)]),
+    "ism_autotune_from": (_I, [_VP, _VP, _VP, _D, _I, C.POINTER(IsmOptions)]),
     "ism_residual_restrict_noalloc": (_I, [_I, _I, _I, C.POINTER(C.c_int), _VP, _VP, _VP, _VP, _VP]),
     "ism_solve_batched": (_I, [_I, C.POINTER(_VP), C.POINTER(_VP), C.POINTER(_VP), _D, _I,
                                C.POINTER(C.c_int), C.POINTER(C.c_double)]),
@@ -176,6 +177,15 @@ def ism_autotune(ctx, rhs, tol=1e-8, max_cycles=100000):
     """Returns (status, chosen IsmOptions)."""
     o = IsmOptions()
     s = lib().ism_autotune(ctx.handle, _ptr(rhs), float(tol), int(max_cycles), C.byref(o))
+    return s, o
+
+
+def ism_autotune_from(ctx, rhs, p0, tol=1e-8, max_cycles=100000):
+    """ism_autotune with every timed solve started from p0 (device, or None
+    for zero).  Returns (status, chosen IsmOptions)."""
+    o = IsmOptions()
+    s = lib().ism_autotune_from(ctx.handle, _ptr(rhs), _ptr(p0) if p0 is not None else None, float(tol),
+                                int(max_cycles), C.byref(o))
     return s, o
 
 

@@ -248,6 +248,32 @@ def test_autotune_picks_a_working_candidate(prec):
     assert s == ism.ISM_OK and r <= 1e-8 and rel(host(p), p_ex) <= 1e-9
 
 
+def test_autotune_from_a_warm_start():
+    """ism_autotune_from times solves started from a given guess (here the
+    solution of a nearby right-hand side, as a time stepper's previous
+    increment): the guess is not modified, the options it keeps solve that
+    problem from that guess to the tolerance, and the result matches the
+    oracle."""
+    nx = ny = 256
+    b0 = smooth_rhs(nx, ny, 9)
+    b = b0 + 0.05 * smooth_rhs(nx, ny, 10)
+    ctx = setup(nx, ny, 32, (0, 0, 0, 0), prec=ism.ISM_MIXED)
+    p0 = dev64(np.zeros((ny, nx)))
+    s, _, _ = ism.ism_solve(ctx, dev64(b0), p0, 1e-8, 100000)
+    assert s == ism.ISM_OK
+    keep = host(p0).copy()
+    s, o = ism.ism_autotune_from(ctx, dev64(b), p0, 1e-8, 100000)
+    assert s == ism.ISM_OK and o.nu % o.sweeps_per_pass == 0
+    assert np.array_equal(host(p0), keep)
+    cur = ism.ism_get_options(ctx)
+    assert (cur.nu, cur.inner_tol, cur.coarse_tc) == (o.nu, o.inner_tol, o.coarse_tc)
+    q = dev64(keep)
+    s, c, r = ism.ism_solve(ctx, dev64(b), q, 1e-8, 100000)
+    assert s == ism.ISM_OK and r <= 1e-8
+    p_ex, _, _ = O.OracleISM(nx, ny, 32, nu=o.nu).solve(b, tol=1e-11)
+    assert rel(host(q), p_ex) <= 1e-9
+
+
 @pytest.mark.parametrize("nx,ny,expect", [(512, 512, (16, 32)), (144, 96, (16,)), (96, 64, (16, 32))])
 def test_setup_chooses_coarsening(nx, ny, expect):
     """coarsen = 0: the library times solves with 16h and 32h (those that
