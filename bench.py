@@ -220,7 +220,7 @@ def events():
 def options_dict(ism, ctx, autotuned):
     o = ism.ism_get_options(ctx)
     return {"nu": o.nu, "sweeps_per_pass": o.sweeps_per_pass, "stream": o.stream, "inner_tol": o.inner_tol,
-            "coarse_tc": o.coarse_tc, "tile_rows": o.tile_rows, "autotuned": autotuned}
+            "coarse_tc": o.coarse_tc, "tile_rows": o.tile_rows, "packed": o.packed, "autotuned": autotuned}
 
 
 def jet_context(ism, prec, prof):

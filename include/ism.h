@@ -136,6 +136,12 @@ typedef struct {
                              128 (default: 8 warps, two CTAs per SM) or 256 (16 warps, one CTA per
                              SM; less halo overlap, 1.52x instead of 1.78x the cells at 8 sweeps);
                              ism_autotune tries both.  The batched solve uses 128. */
+    int packed;           /* single precision: 1 updates the two same-colour cells of a row of the
+                             fused pass's interior tiles with packed FP32 pair instructions (fewer
+                             instructions, longer latency; results bit-identical); 0 with scalar
+                             ones; 2 (default) packed when a pass runs at least four waves of
+                             resident CTAs.  ism_autotune tries 0 and 1.  The batched solve uses
+                             scalar updates. */
 } ism_options;
 
 typedef struct ism_ctx ism_ctx;

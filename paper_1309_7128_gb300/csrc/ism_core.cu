@@ -255,6 +255,7 @@ static void default_options(ism_options *o, int prec)
     o->stream = 0;
     o->fault_test = 0;
     o->tile_rows = 128;
+    o->packed = 2;
 }
 
 static const double kPi = 3.14159265358979323846;
@@ -484,6 +485,10 @@ static void set_sweep_smem()
     cudaFuncSetAttribute(k_sweep32<NW, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
     cudaFuncSetAttribute(k_sweep32<NW, false, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
     cudaFuncSetAttribute(k_sweep32<NW, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<NW, true, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<NW, true, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<NW, false, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
+    cudaFuncSetAttribute(k_sweep32<NW, false, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb);
 }
 
 
@@ -640,6 +645,7 @@ extern "C" ism_status ism_set_options(ism_ctx *ctx, const ism_options *o)
     if (o->stream < 0 || o->stream > 1) return ISM_ERR_ARG;
     if (o->fault_test < 0 || o->fault_test > 1) return ISM_ERR_ARG;
     if (o->tile_rows != 128 && o->tile_rows != 256) return ISM_ERR_ARG;
+    if (o->packed < 0 || o->packed > 2) return ISM_ERR_ARG;
     if (!(o->inner_tol > 0.0 && o->inner_tol < 1.0) || !(o->floor_mult >= 0.0)) return ISM_ERR_ARG;
     // a narrower last coarse cell: the ISM and ACM operators; the accommodative
     // cycle with walls only (its coarse coefficients come from the 1-D W, T)
@@ -867,15 +873,24 @@ static ism_status launch_sweep_pair(ism_ctx *ctx, const SweepArgs &a, const Swee
 {
     const size_t sm = sweep_smem_bytes(NW);
     const bool both = P.ix1 > P.ix0 && P.nedge > 0;
+    const dim3 gin(P.ix1 - P.ix0, P.iy1 - P.iy0);
+    // packed pair updates in the interior launch: option packed 1, or 2
+    // (automatic) when the launch runs at least four waves of resident CTAs
+    const bool pk = ctx->opt.packed == 1 ||
+                    (ctx->opt.packed == 2 && (long long)gin.x * gin.y >= 4LL * (16 / NW) * ism_sm_count());
+    auto interior = [&]() {
+        if (pk) k_sweep32<NW, PR, RE, false, true><<<gin, 32 * NW, sm, ctx->ws>>>(a);
+        else k_sweep32<NW, PR, RE, false, false><<<gin, 32 * NW, sm, ctx->ws>>>(a);
+    };
     if (both) {
         ISM_CUDA_TRY(cudaEventRecord(ctx->ev_fork, ctx->ws));
         ISM_CUDA_TRY(cudaStreamWaitEvent(ctx->ws2, ctx->ev_fork, 0));
         k_sweep32<NW, PR, RE, true><<<P.nedge, 32 * NW, sm, ctx->ws2>>>(a);
-        k_sweep32<NW, PR, RE, false><<<dim3(P.ix1 - P.ix0, P.iy1 - P.iy0), 32 * NW, sm, ctx->ws>>>(a);
+        interior();
         ISM_CUDA_TRY(cudaEventRecord(ctx->ev_join, ctx->ws2));
         ISM_CUDA_TRY(cudaStreamWaitEvent(ctx->ws, ctx->ev_join, 0));
     } else if (P.ix1 > P.ix0) {
-        k_sweep32<NW, PR, RE, false><<<dim3(P.ix1 - P.ix0, P.iy1 - P.iy0), 32 * NW, sm, ctx->ws>>>(a);
+        interior();
     } else {
         k_sweep32<NW, PR, RE, true><<<P.nedge, 32 * NW, sm, ctx->ws>>>(a);
     }
@@ -1695,6 +1710,13 @@ extern "C" ism_status ism_autotune_from(ism_ctx *ctx, const double *rhs, const d
         if (st == ISM_OK) {
             ism_options o = win;
             o.tile_rows = win.tile_rows == 256 ? 128 : 256;
+            consider(o);
+        }
+        // scalar or packed pair updates in the interior tiles, explicitly
+        const ism_options w1 = win;
+        for (int pk = 0; pk <= 1 && st == ISM_OK; ++pk) {
+            ism_options o = w1;
+            o.packed = pk;
             consider(o);
         }
         const ism_options w0 = win;

@@ -17,6 +17,11 @@
 // rows of a half-sweep: the shared-memory pipe, which the shuffles and the
 // row exchange also use, is left to them (TMEM has its own data path; with b
 // in shared memory the pass was 6-11% slower, results bit-identical).
+// Interior tiles hold -b/4 there, the edge tiles b.  The interior launch may
+// update the two cells of a row with packed FP32 pair instructions
+// (add.rn.f32x2, fma.rn.f32x2): each lane rounds like the scalar op, so the
+// results are bit-identical; fewer instructions help when a pass runs many
+// waves of tiles (issue-bound), the longer latency hurts when it runs few.
 //
 // K sweeps run on the region before it is written back.  Values at the
 // region edge are stale (shuffles wrap to the lane itself, the outermost
@@ -138,6 +143,17 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, float v0, float v1, flo
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float4 &lo, float4 &hi)
+{
+    uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7) : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3), "+r"(r4), "+r"(r5), "+r"(r6), "+r"(r7) :: "memory");
+    lo = make_float4(__uint_as_float(r0), __uint_as_float(r1), __uint_as_float(r2), __uint_as_float(r3));
+    hi = make_float4(__uint_as_float(r4), __uint_as_float(r5), __uint_as_float(r6), __uint_as_float(r7));
+}
+
 __device__ __forceinline__ float4 tmem_ld4(uint32_t taddr)
 {
     uint32_t r0, r1, r2, r3;
@@ -180,36 +196,81 @@ __device__ __forceinline__ float edge_inv(const EdgeRows &er, const float (&rq)[
 
 // Half-sweep of colour parity PAR over the warp's rows; EDGE selects the
 // boundary-aware update (out-of-domain cells are never updated).
-template <int PAR, bool EDGE>
+// Packed FP32 pairs (sm_100+): one instruction for the two same-colour
+// cells of a row; each lane of the pair rounds exactly like the scalar op.
+__device__ __forceinline__ float2 add2(float2 a, float2 b)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c)
+{
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\t"
+        "mov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+template <int PAR, bool EDGE, bool PK>
 __device__ __forceinline__ void half_sweep(float (&P)[SRR + 2][SNC], const uint32_t tb, const int lane,
                                            const float (&idq)[SNC], const float (&rq)[SNC],
                                            const bool colin, const EdgeRows &er)
 {
-    float4 bb2 = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 bb2 = make_float4(0.f, 0.f, 0.f, 0.f), bb3 = bb2;
 #pragma unroll
     for (int r = 0; r < SRR; ++r) {
         const int qp = PAR ^ (r & 1);            // which pair of columns has the active colour
-        if ((r & 1) == 0) bb2 = tmem_ld4(tb + PAR * 32 + 2 * r);
+        if ((r & 3) == 0) tmem_ld8(tb + PAR * 32 + 2 * r, bb2, bb3);
+        else if ((r & 3) == 2) bb2 = bb3;
         const float2 bb = (r & 1) ? make_float2(bb2.z, bb2.w) : make_float2(bb2.x, bb2.y);
         if (qp == 0) {
             const float left = __shfl_up_sync(FULLMASK, P[r + 1][3], 1);
-            float s0 = ((left + P[r + 1][1]) + P[r][0]) + P[r + 2][0];
-            float s2 = ((P[r + 1][1] + P[r + 1][3]) + P[r][2]) + P[r + 2][2];
-            if (!EDGE) {
-                P[r + 1][0] = fmaf(s0, 0.25f, -bb.x);
-                P[r + 1][2] = fmaf(s2, 0.25f, -bb.y);
+            if (!EDGE && PK) {
+                float2 t = add2(make_float2(left, P[r + 1][1]), make_float2(P[r + 1][1], P[r + 1][3]));
+                t = add2(t, make_float2(P[r][0], P[r][2]));
+                t = add2(t, make_float2(P[r + 2][0], P[r + 2][2]));
+                t = fma2(t, make_float2(0.25f, 0.25f), bb);          // bb holds -b / 4
+                P[r + 1][0] = t.x;
+                P[r + 1][2] = t.y;
+            } else if (!EDGE) {
+                const float s0 = ((left + P[r + 1][1]) + P[r][0]) + P[r + 2][0];
+                const float s2 = ((P[r + 1][1] + P[r + 1][3]) + P[r][2]) + P[r + 2][2];
+                P[r + 1][0] = fmaf(s0, 0.25f, bb.x);
+                P[r + 1][2] = fmaf(s2, 0.25f, bb.y);
             } else if (colin && r >= er.rlo && r < er.rhi) {
+                const float s0 = ((left + P[r + 1][1]) + P[r][0]) + P[r + 2][0];
+                const float s2 = ((P[r + 1][1] + P[r + 1][3]) + P[r][2]) + P[r + 2][2];
                 P[r + 1][0] = (s0 - bb.x) * edge_inv(er, rq, r, 0);
                 P[r + 1][2] = (s2 - bb.y) * edge_inv(er, rq, r, 2);
             }
         } else {
             const float right = __shfl_down_sync(FULLMASK, P[r + 1][0], 1);
-            float s1 = ((P[r + 1][0] + P[r + 1][2]) + P[r][1]) + P[r + 2][1];
-            float s3 = ((P[r + 1][2] + right) + P[r][3]) + P[r + 2][3];
-            if (!EDGE) {
-                P[r + 1][1] = fmaf(s1, 0.25f, -bb.x);
-                P[r + 1][3] = fmaf(s3, 0.25f, -bb.y);
+            if (!EDGE && PK) {
+                float2 t = add2(make_float2(P[r + 1][0], P[r + 1][2]), make_float2(P[r + 1][2], right));
+                t = add2(t, make_float2(P[r][1], P[r][3]));
+                t = add2(t, make_float2(P[r + 2][1], P[r + 2][3]));
+                t = fma2(t, make_float2(0.25f, 0.25f), bb);          // bb holds -b / 4
+                P[r + 1][1] = t.x;
+                P[r + 1][3] = t.y;
+            } else if (!EDGE) {
+                const float s1 = ((P[r + 1][0] + P[r + 1][2]) + P[r][1]) + P[r + 2][1];
+                const float s3 = ((P[r + 1][2] + right) + P[r][3]) + P[r + 2][3];
+                P[r + 1][1] = fmaf(s1, 0.25f, bb.x);
+                P[r + 1][3] = fmaf(s3, 0.25f, bb.y);
             } else if (colin && r >= er.rlo && r < er.rhi) {
+                const float s1 = ((P[r + 1][0] + P[r + 1][2]) + P[r][1]) + P[r + 2][1];
+                const float s3 = ((P[r + 1][2] + right) + P[r][3]) + P[r + 2][3];
                 P[r + 1][1] = (s1 - bb.x) * edge_inv(er, rq, r, 1);
                 P[r + 1][3] = (s3 - bb.y) * edge_inv(er, rq, r, 3);
             }
@@ -234,14 +295,15 @@ __device__ __forceinline__ void exchange_rows(float (&P)[SRR + 2][SNC], float *x
     X[base + (w * 2 + 0) * 32 + lane] = make_float2(P[1][q0], P[1][q0 + 2]);
     X[base + (w * 2 + 1) * 32 + lane] = make_float2(P[SRR][q1], P[SRR][q1 + 2]);
     __syncthreads();
-    if (w > 0) {
-        const float2 v = X[base + ((w - 1) * 2 + 1) * 32 + lane];
-        P[0][q1] = v.x; P[0][q1 + 2] = v.y;
-    }
-    if (w < NW - 1) {
-        const float2 v = X[base + ((w + 1) * 2 + 0) * 32 + lane];
-        P[SRR + 1][q0] = v.x; P[SRR + 1][q0 + 2] = v.y;
-    }
+    // the first and last warps read their own slots instead of a missing
+    // neighbour's and keep their outer halo rows (no branches)
+    const bool up = w > 0, dn = w < NW - 1;
+    const float2 vu = X[base + ((up ? w - 1 : w) * 2 + 1) * 32 + lane];
+    const float2 vd = X[base + ((dn ? w + 1 : w) * 2 + 0) * 32 + lane];
+    P[0][q1] = up ? vu.x : P[0][q1];
+    P[0][q1 + 2] = up ? vu.y : P[0][q1 + 2];
+    P[SRR + 1][q0] = dn ? vd.x : P[SRR + 1][q0];
+    P[SRR + 1][q0 + 2] = dn ? vd.y : P[SRR + 1][q0 + 2];
 }
 
 // G rows needed by a region of NW warps: its rows span at most 16 NW / 8 + 3
@@ -257,8 +319,10 @@ inline size_t sweep_smem_bytes(int nw = SNW)
 
 // EDGE: the launch over the tiles whose region touches the domain boundary
 // (listed in edge_tiles); otherwise the launch over the interior tiles.
+// PK (interior tiles): the two same-colour cells of a row in packed FP32
+// pairs (fewer instructions, longer latency; bit-identical results).
 // The pass on tile (bx, by) of the problem described by a; one CTA.
-template <int NW, bool PROLONG, bool RESID, bool EDGE>
+template <int NW, bool PROLONG, bool RESID, bool EDGE, bool PK = false>
 __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, const int by, const int pf_id)
 {
     extern __shared__ __align__(16) float sm[];
@@ -362,7 +426,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 v[k] = *reinterpret_cast<const float4 *>(bsrc + (size_t)(r0 + k) * nx);
-                v[k].x *= 0.25f; v[k].y *= 0.25f; v[k].z *= 0.25f; v[k].w *= 0.25f;
+                v[k].x *= -0.25f; v[k].y *= -0.25f; v[k].z *= -0.25f; v[k].w *= -0.25f;
             }
             b_store4(tb, r0, v);
         }
@@ -463,14 +527,19 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
 
     // 2. 2K half-sweeps, red ((x+y) even) first
     const int base = (x0 + y0 + ry0) & 1;      // colour parity of (column 0, row 0) of this warp
-    for (int s = 0; s < 2 * a.K; ++s) {
-        const int par = (s & 1) ^ base;        // active colour c = s & 1: q-parity = c ^ base ^ (r & 1)
-        if (par == 0) {
-            half_sweep<0, EDGE>(P, tb, lane, idq, rq, colin, er);
-            exchange_rows<NW, 0>(P, xch, s & 1, w, lane);
-        } else {
-            half_sweep<1, EDGE>(P, tb, lane, idq, rq, colin, er);
-            exchange_rows<NW, 1>(P, xch, s & 1, w, lane);
+    if (base == 0) {
+        for (int s = 0; s < a.K; ++s) {
+            half_sweep<0, EDGE, PK>(P, tb, lane, idq, rq, colin, er);
+            exchange_rows<NW, 0>(P, xch, 0, w, lane);
+            half_sweep<1, EDGE, PK>(P, tb, lane, idq, rq, colin, er);
+            exchange_rows<NW, 1>(P, xch, 1, w, lane);
+        }
+    } else {
+        for (int s = 0; s < a.K; ++s) {
+            half_sweep<1, EDGE, PK>(P, tb, lane, idq, rq, colin, er);
+            exchange_rows<NW, 1>(P, xch, 0, w, lane);
+            half_sweep<0, EDGE, PK>(P, tb, lane, idq, rq, colin, er);
+            exchange_rows<NW, 0>(P, xch, 1, w, lane);
         }
     }
 
@@ -524,7 +593,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
                 const float rt = q == SNC - 1 ? right : P[r + 1][q + 1];
                 const float pc = P[r + 1][q];
                 const float sn = ((lf + rt) + P[r][q]) + P[r + 2][q];
-                const float bb = EDGE ? bq[q] : 4.0f * bq[q];
+                const float bb = EDGE ? bq[q] : -4.0f * bq[q];
                 const float res = EDGE ? bb - (sn - (idq[q] + ra) * pc) : bb - fmaf(-4.0f, pc, sn);
                 if (ok) { rowsum += res; r2s = fmaf(res, res, r2s); ps += pc; p2 = fmaf(pc, pc, p2); }
             }
@@ -578,7 +647,7 @@ __device__ __forceinline__ void sweep_tile(const SweepArgs &a, const int bx, con
     if (w == 0) tc::tmem_dealloc(tslot, (uint32_t)(NW * 16));
 }
 
-template <int NW, bool PROLONG, bool RESID, bool EDGE>
+template <int NW, bool PROLONG, bool RESID, bool EDGE, bool PK = false>
 __global__ void __launch_bounds__(32 * NW, 16 / NW) k_sweep32(SweepArgs a)
 {
     if (a.skip && *a.skip) return;
@@ -587,7 +656,7 @@ __global__ void __launch_bounds__(32 * NW, 16 / NW) k_sweep32(SweepArgs a)
         sweep_tile<NW, PROLONG, RESID, EDGE>(a, t.x, t.y, -1);
     } else {
         const int id = blockIdx.y * gridDim.x + blockIdx.x;
-        sweep_tile<NW, PROLONG, RESID, EDGE>(a, blockIdx.x + a.ix0, blockIdx.y + a.iy0,
+        sweep_tile<NW, PROLONG, RESID, EDGE, PK>(a, blockIdx.x + a.ix0, blockIdx.y + a.iy0,
                                              a.pf_ahead > 0 ? id + a.pf_ahead : -1);
     }
 }

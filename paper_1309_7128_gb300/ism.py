@@ -30,7 +30,7 @@ class IsmOptions(C.Structure):
                 ("floor_mult", C.c_double), ("check_every", C.c_int), ("use_graphs", C.c_int),
                 ("coarse_tc", C.c_int), ("cycle", C.c_int), ("accom_tol_c", C.c_double),
                 ("accom_max_coarse", C.c_int),
-                ("stream", C.c_int), ("fault_test", C.c_int), ("tile_rows", C.c_int)]
+                ("stream", C.c_int), ("fault_test", C.c_int), ("tile_rows", C.c_int), ("packed", C.c_int)]
 
 
 class IsmError(RuntimeError):

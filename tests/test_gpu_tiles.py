@@ -86,3 +86,43 @@ def test_tile_rows_option_is_validated_and_tuned():
     s, best = ism.ism_autotune(ctx, dev64(smooth_rhs(256, 256, 9)), 1e-8, 100000)
     assert s == ism.ISM_OK and best.tile_rows in (128, 256)
     assert ism.ism_get_options(ctx).tile_rows == best.tile_rows
+
+
+@pytest.mark.parametrize("nx,ny,m,bc", [(160, 96, 32, (0, 0, 0, 0)), (1000, 744, 16, (1, 0, 0, 1)),
+                                         (512, 256, 16, (2, 2, 0, 1)), (4096, 4096, 32, (0, 0, 0, 0))])
+@pytest.mark.parametrize("tile_rows", [128, 256])
+def test_packed_pair_updates_are_bit_identical(nx, ny, m, bc, tile_rows):
+    """Option packed: the interior tiles' packed FP32 pair updates round each
+    lane like the scalar updates, so K sweeps and whole mixed solves give the
+    same bits with packed 0, 1 and 2 (automatic: packed on the 4096^2 grid,
+    which runs more than four waves of tiles); the sweeps also match the
+    oracle's float sweeps."""
+    p = random_field(nx, ny, 3).astype(np.float32)
+    b = random_field(nx, ny, 4).astype(np.float32)
+    rhs = smooth_rhs(nx, ny, 6) + (1e-6 if any(x == 1 for x in bc) else 0.0)
+    outs, sols = [], []
+    for pk in (0, 1, 2):
+        ctx = setup(nx, ny, m, bc, prec=ism.ISM_MIXED, tile_rows=tile_rows, packed=pk)
+        pd = dev32(p)
+        ism.check(ism.ism_smooth(ctx, pd, dev32(b), 8))
+        outs.append(host(pd))
+        q = dev64(np.zeros((ny, nx)))
+        s, cyc, rr = ism.ism_solve(ctx, dev64(rhs), q, 1e-8, 100000)
+        assert s == ism.ISM_OK and rr <= 1e-8
+        sols.append((cyc, host(q)))
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+    assert all(c == sols[0][0] and np.array_equal(x, sols[0][1]) for c, x in sols[1:])
+    if nx * ny <= 1000 * 744:
+        ref = np.ascontiguousarray(p.copy())
+        bca = np.asarray(bc, dtype=np.int32)
+        for _ in range(8):
+            O.lib().or_rbgs_sweep_f32(nx, ny, bca, ref, np.ascontiguousarray(b))
+        np.testing.assert_allclose(outs[0], ref.astype(np.float64), rtol=0, atol=2e-6 * np.abs(ref).max())
+
+
+def test_packed_option_is_validated():
+    ctx = setup(64, 64, 16, prec=ism.ISM_MIXED)
+    o = ism.ism_get_options(ctx)
+    assert o.packed == 2
+    o.packed = 3
+    assert ism.ism_set_options(ctx, o) == ism.ISM_ERR_ARG
