@@ -1633,6 +1633,9 @@ extern "C" ism_status ism_autotune_from(ism_ctx *ctx, const double *rhs, const d
     // nearly independent of nu: larger nu amortises the fixed part.  Mixed
     // candidates {nu, sweeps per pass, stream}: the streaming middle passes
     // (stream = 1, 4 sweeps per pass) win on grids larger than L2.
+    // (K = 6, whose 104 x 104 valid tile wastes fewer cells than the 96 x 96
+    // of K = 8, measured slower per sweep on 8192 x 4096 and 2048^2 grids and
+    // is not offered.)
     static const int cand_mixed[][3] = {{8, 4, 0},   {8, 8, 0},   {16, 8, 0},  {24, 8, 0}, {32, 8, 0},
                                         {48, 8, 0},  {64, 8, 0},  {96, 8, 0},  {128, 8, 0}, {192, 8, 0},
                                         {256, 8, 0}, {16, 4, 0},  {32, 4, 1},  {64, 4, 1}, {128, 4, 1}};

@@ -36,7 +36,7 @@ def test_smooth_fp64(nx, ny, m, bc):
 
 @pytest.mark.parametrize("nx,ny,m", SHAPES)
 @pytest.mark.parametrize("bc", ALL_BCS)
-@pytest.mark.parametrize("sweeps", [1, 4, 7])
+@pytest.mark.parametrize("sweeps", [1, 4, 6, 7])
 def test_smooth_fused_fp32(nx, ny, m, bc, sweeps):
     """Fused multi-sweep pass (temporal blocking) against the oracle's float
     sweeps: the same operations in the same order, so agreement is at the
