@@ -242,7 +242,7 @@ def tune(ism, ctx, rhs, args, prec, p0=None):
     if args.no_autotune:
         o = ism.ism_get_options(ctx)
         if prec == ism.ISM_MIXED:
-            o.nu, o.sweeps_per_pass = args.nu, args.sweeps_per_pass
+            o.nu, o.sweeps_per_pass, o.inner_tol = args.nu, args.sweeps_per_pass, args.inner_tol
         else:
             o.nu = args.nu_fp64
         ism.check(ism.ism_set_options(ctx, o), "ism_set_options")
@@ -1008,6 +1008,7 @@ def main():
                     help="use --nu / --sweeps-per-pass / --nu-fp64 instead of ism_autotune")
     ap.add_argument("--nu", type=int, default=64)
     ap.add_argument("--sweeps-per-pass", type=int, default=8)
+    ap.add_argument("--inner-tol", type=float, default=1e-3, help="with --no-autotune: the mixed inner_tol")
     ap.add_argument("--nu-fp64", type=int, default=32)
     ap.add_argument("--use-graphs", type=int, default=2, choices=[0, 1, 2],
                     help="2: one graph per solve with device-side loops (default); 1: graphs of "

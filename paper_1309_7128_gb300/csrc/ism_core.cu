@@ -1641,9 +1641,10 @@ extern "C" ism_status ism_autotune_from(ism_ctx *ctx, const double *rhs, const d
                                         {256, 8, 0}, {16, 4, 0},  {32, 4, 1},  {64, 4, 1}, {128, 4, 1}};
     static const int cand_fp64[][3] = {{8, 4, 0}, {16, 4, 0}, {32, 4, 0}, {48, 4, 0}, {64, 4, 0}, {96, 4, 0},
                                        {128, 4, 0}};
-    // then, for the three fastest mixed candidates, the inner stopping factor
+    // then, for the five fastest mixed candidates, the inner stopping factor
     // of the refinement (it interacts with nu: a longer cycle reaches a
-    // tighter inner tolerance in fewer cycles); for the winner the other
+    // tighter inner tolerance in fewer cycles, and candidates that tie at the
+    // default factor can differ by 20% at another); for the winner the other
     // height of the fused pass's tiled region (tile shape), and last the other
     // coarse engines (CUDA cores, the single-CTA tensor-core kernel, the tiled
     // split-TF32 chain: TF32 error costs cycles on some grids, and the chain's
@@ -1702,7 +1703,7 @@ extern "C" ism_status ism_autotune_from(ism_ctx *ctx, const double *rhs, const d
             const float ms = time_opt(o);
             if (ms < best_ms) { best_ms = ms; win = o; }
         };
-        const int top = std::min<int>(3, (int)first.size());
+        const int top = std::min<int>(5, (int)first.size());
         for (int k = 0; k < top && st == ISM_OK; ++k)
             for (double it : inner_tols) {
                 if (first[k].first >= 1e29f || st != ISM_OK) continue;
