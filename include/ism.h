@@ -103,12 +103,13 @@ typedef struct {
     int use_graphs;       /* 0: plain launches; 1: CUDA graphs of check_every cycles; 2 (default):
                              the whole solve as one graph with device-side while loops */
     int coarse_tc;        /* mixed: 1 (default) runs the single-precision coarse solve on the tensor
-                             cores (tcgen05, TF32 operands, FP32 accumulation) when ncx, ncy <= 256:
-                             up to 64 x 64 one CTA runs the whole product chain, above that four
-                             launches of a tiled GEMM (128 x 32 blocks) do; 2 takes the tiled
-                             launches on every coarse grid up to 256 x 256; 0 runs it on the CUDA
-                             cores in FP32, as do 1 and 2 above 256.  The batched ensemble uses the
-                             tensor cores only when every problem's coarse grid is <= 64 x 64.
+                             cores (tcgen05, FP32 accumulation) when ncx, ncy <= 256: up to 64 x 64
+                             one CTA runs the whole product chain with TF32 operands, above that
+                             four launches of a tiled GEMM (128 x 32 blocks) do, in split TF32
+                             (operands as hi + lo TF32 parts, about FP32 accuracy); 2 takes the
+                             tiled launches on every coarse grid up to 256 x 256; 0 runs it on the
+                             CUDA cores in FP32, as do 1 and 2 above 256.  The batched ensemble
+                             picks its engine from the same setting (see ism_solve_batched).
                              Ignored by the FP64 path. */
     int cycle;            /* 0 (default): the correction-scheme cycle above.  1: the paper's
                              accommodative strategy (Sec. 4.3.1), FP64 contexts with the ISM coarse

@@ -21,7 +21,8 @@
 // difference.
 //
 // Limits: ncx, ncy <= 64 (all operand tiles resident, <= 177 KB of shared
-// memory); larger coarse grids take the CUDA-core path.
+// memory); larger coarse grids, up to 256 x 256, take the tiled split-TF32
+// chain of ism_coarse_tct.cu, and beyond that the CUDA-core path.
 #include <math.h>
 #include <string.h>
 
